@@ -1,0 +1,233 @@
+/*
+ * tacchi.h -- C ABI of the GB300 elastomer simulator and tactile renderer.
+ *
+ * The library simulates the elastomer of an optical tactile sensor pressed by
+ * a rigid indenter with the Material Point Method (Tacchi, arXiv 2301.08343,
+ * Sec. III-A) and renders the deformed top surface into a tactile image
+ * (Sec. III-B).  Every step of the computation runs in the library's own
+ * CUDA kernels for sm_103a on one GPU.
+ *
+ * Conventions for every call:
+ *   - A call returns a tacchi_status; TACCHI_OK is 0, errors are negative.
+ *   - Work is queued asynchronously on the stream given at creation.
+ *     Errors detected on the device (a particle leaving the grid, NaN,
+ *     det F <= 0, a bounded wait running out) are recorded in a device error
+ *     word and reported by the next call that synchronises (tacchi_sync,
+ *     tacchi_get_state, and heightmap/render calls with host outputs).
+ *     Once reported they stay set ("sticky") until tacchi_set_state or
+ *     tacchi_clear_error.
+ *   - The library copies everything it is given; the caller owns its
+ *     buffers.  "dev" pointers must be device memory of the context's device;
+ *     "host" pointers are ordinary host memory; a pointer documented as
+ *     "host or dev" may be either (the library checks which).
+ *   - Positions in state buffers are in grid-cell units measured from grid
+ *     node 0: x_world = origin_m + u * dx_m (see tacchi_info).  F is carried
+ *     as F - I for precision near the rest state.
+ *   - Arrays of per-particle quantities are structure-of-arrays: component c
+ *     of particle p is at [c * n_particles + p]; 3x3 matrices are row-major,
+ *     entry (r, c) is component r * 3 + c.
+ */
+#ifndef TACCHI_H
+#define TACCHI_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tacchi_ctx *tacchi_handle; /* opaque, library-owned */
+
+typedef enum {
+  TACCHI_OK = 0,
+  TACCHI_ERR_INVALID_ARG = -1, /* a size, pointer or parameter is out of range */
+  TACCHI_ERR_OOM = -2,         /* device or host allocation failed */
+  TACCHI_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+  TACCHI_ERR_NUMERICAL = -4,   /* NaN/Inf or det F <= 0 seen on the device */
+  TACCHI_ERR_OUT_OF_GRID = -5, /* a particle's stencil reached the padding band */
+  TACCHI_ERR_TIMEOUT = -6,     /* a bounded device-side wait gave up */
+  TACCHI_ERR_STATE = -7,       /* call not valid in the current state */
+  TACCHI_ERR_CFL = -8          /* a particle moved a cell or more in one substep */
+} tacchi_status;
+
+/* Elastomer block and material (Sec. IV-B: block size, Young's modulus and
+ * Poisson's ratio; the paper gives no density, so it is a parameter).
+ * The block occupies [0, extent_m[0]] x [0, extent_m[1]] x [0, extent_m[2]]
+ * in the world frame; its bottom face z = 0 is the sensor base. */
+typedef struct {
+  double extent_m[3];  /* block size (m); each must be a whole multiple of dx_m */
+  double dx_m;         /* grid node interval Delta X (m) */
+  double E_pa;         /* Young's modulus (Pa), > 0 */
+  double nu;           /* Poisson's ratio, in (-1, 0.5) */
+  double density;      /* kg/m^3, > 0 */
+  uint64_t seed;       /* seed of the jittered particle lattice */
+  int jitter;          /* 1: jitter each particle in its sub-cell; 0: centres */
+  int pad_side;        /* grid cells around the block in x and y (0 -> 4; >= 3) */
+  int pad_bottom;      /* grid cells below the base (0 -> 3; >= 3) */
+  int pad_top;         /* grid cells above the top face (0 -> 4; >= 3) */
+  double gravity[3];   /* m/s^2, applied on the grid; the paper uses none */
+  int free_base;       /* 0: base held fixed (Eq. 10); 1: no base condition */
+  int block[3];        /* particle-sort block in cells (0 -> library default) */
+} tacchi_elastomer_desc;
+
+typedef enum {
+  TACCHI_INDENTER_NONE = 0,
+  TACCHI_INDENTER_SPHERE = 1,    /* params[0] = radius; pose = centre */
+  TACCHI_INDENTER_CYLINDER = 2,  /* params = radius, half length; axis = local x */
+  TACCHI_INDENTER_CONE = 3,      /* params = half angle (rad), height; apex at pose, opens to local +z */
+  TACCHI_INDENTER_PRISM = 4,     /* params = half angle, half length (local y), height; edge at pose */
+  TACCHI_INDENTER_HEIGHTMAP = 5  /* params[0] = thickness above the back plane; see hm */
+} tacchi_indenter_kind;
+
+/* Rigid indenter (Sec. III-A, Eq. 10; Sec. III-C).  The indenter acts on the
+ * grid: a grid node inside the solid at the pose of the start of a substep
+ * takes the indenter's rigid velocity.  For TACCHI_INDENTER_HEIGHTMAP the
+ * solid is { |x_l|,|y_l| within the map, -hm(x_l, y_l) <= z_l <= params[0] }
+ * in the local frame: hm holds protrusion heights (m, >= 0) below the flat
+ * back plane z_l = 0, sampled at pixel centres, row j along local y. */
+typedef struct {
+  int kind;           /* tacchi_indenter_kind */
+  double params[8];   /* shape lengths in metres, angles in radians */
+  int hm_w, hm_h;     /* height-map samples (>= 2 each) */
+  double hm_pixel_m;  /* height-map sample spacing (m) */
+  const float *hm;    /* host, [hm_h][hm_w]; copied by the call */
+} tacchi_indenter_desc;
+
+/* Phong lighting (Eqs. 12-14).  dir[m] is the unit vector from the surface
+ * towards light m; the camera looks along +z from below (V = (0,0,-1)). */
+typedef struct {
+  int n_lights;          /* 0..8 */
+  float dir[8][3];
+  float diffuse[8][3];   /* i_{m,d}, RGB */
+  float specular[8][3];  /* i_{m,s}, RGB */
+  float ambient[3];      /* i_a, RGB */
+  float ka, kd, ks, alpha;
+} tacchi_render_params;
+
+typedef struct {
+  int64_t n_particles;
+  int64_t n_surface;      /* particles of the top layer (height map samples) */
+  int grid[3];            /* grid nodes per axis */
+  int64_t n_nodes;
+  double origin_m[3];     /* world position of grid node 0 */
+  double dx_m;
+  double z_top_m;         /* rest height of the top face */
+  int block[3];           /* particle-sort block in cells */
+  int64_t n_blocks;
+  size_t device_bytes;    /* device memory held by the context */
+} tacchi_info_t;
+
+/* Create a simulator on the current CUDA device (Sec. III-A, Initialization;
+ * Eq. 1).  Particles: 2x2x2 per grid cell of the block, each in its own
+ * sub-cell, jittered with the counter-based splitmix64 generator seeded by
+ * desc->seed (draw 3p+a for axis a of particle p); v = 0, C = 0, F = I.
+ * Particles of the bottom cell layer form the fixed set B of Eq. 10; the
+ * upper particle layer of the top cell layer gives the height-map samples.
+ * stream: a cudaStream_t (NULL = the legacy default stream); the library
+ * does not take ownership.  *out receives the handle.
+ * Errors: INVALID_ARG (bad sizes/material, extents not multiples of dx_m,
+ * padding < 3), OOM, CUDA. */
+tacchi_status tacchi_create(const tacchi_elastomer_desc *desc, void *stream,
+                            tacchi_handle *out);
+
+/* Release every resource of the context (waits for its queued work). */
+void tacchi_destroy(tacchi_handle h);
+
+/* Sizes and frames of the context; out: host. */
+tacchi_status tacchi_info(tacchi_handle h, tacchi_info_t *out);
+
+/* Indenter shape, pose and velocity (Sec. III-C: the main simulator supplies
+ * the indenter's position or velocity every step).  Each argument may be
+ * NULL to keep the current value.  pose = position (m) and unit quaternion
+ * (w, x, y, z) of the local frame; vel = linear (m/s) and angular (rad/s)
+ * velocity in the world frame.  Within a tacchi_step the pose advances by
+ * dt * vel per substep (Eq. 11 applied to the rigid indenter).
+ * Errors: INVALID_ARG (unknown kind, bad height map, non-finite values). */
+tacchi_status tacchi_set_indenter(tacchi_handle h, const tacchi_indenter_desc *desc,
+                                  const double pose[7], const double vel[6]);
+
+/* Current indenter pose (after the substeps queued so far); out: host. */
+tacchi_status tacchi_get_indenter_pose(tacchi_handle h, double pose[7]);
+
+/* Advance n_substeps explicit MLS-MPM substeps of length dt (Sec. III-A:
+ * particle-to-grid Eqs. 2-5, grid velocity Eq. 6 with the indenter, the
+ * fixed base and the padding band, grid-to-particle Eqs. 7-9, the base
+ * override Eq. 10 and advection Eq. 11).  Asynchronous; the substeps run as
+ * one CUDA graph.  Errors: INVALID_ARG (n_substeps < 1, dt <= 0), CUDA;
+ * device-side errors are reported by the next synchronising call. */
+tacchi_status tacchi_step(tacchi_handle h, int n_substeps, double dt);
+
+/* Height map of the deformed top surface (Sec. III-B, "2D interpolation").
+ * Each top-layer particle carries the height z_top + dx * (u_z - u_z_rest);
+ * a pixel whose centre lies within dx/2 of a particle in the xy plane takes
+ * the largest height among such particles; other pixels copy the nearest
+ * covered pixel within fill_radius pixels (ties: lowest row-major index), or
+ * z_top if none.  window_m = (x0, y0, x1, y1) in the world frame; pixel
+ * (r, c) is centred at (x0 + (c + 1/2)(x1-x0)/w, y0 + (r + 1/2)(y1-y0)/hgt).
+ * out: host or dev, float [hgt][w], metres (host output synchronises).
+ * Errors: INVALID_ARG (w, hgt < 1, empty window, fill_radius outside 0..64). */
+tacchi_status tacchi_heightmap(tacchi_handle h, int w, int hgt, const double window_m[4],
+                               int fill_radius, float *out);
+
+/* Tactile image (Sec. III-B, Eqs. 12-14): the height map above, converted to
+ * the indentation depth D = z_top - H, shaded with Phong's model; normals
+ * N = normalize(dD/dx, dD/dy, -1) from the [-1, 0, 1] / (2 r) stencil with
+ * replicated edges; each channel clamped to [0, 1].
+ * out_rgb: host or dev, float [hgt][w][3]; out_height: optional (NULL) host
+ * or dev float [hgt][w].  Errors as tacchi_heightmap, plus INVALID_ARG for
+ * n_lights outside 0..8. */
+tacchi_status tacchi_render(tacchi_handle h, const tacchi_render_params *rp, int w,
+                            int hgt, const double window_m[4], int fill_radius,
+                            float *out_rgb, float *out_height);
+
+/* Shading alone (Eqs. 12-14) of a caller-provided height map H_dev (dev,
+ * float [hgt][w], metres) with pixel sizes pixel_x_m, pixel_y_m and rest top
+ * height z_top_m, into rgb_dev (dev, float [hgt][w][3]), on stream.
+ * Needs no context.  Errors: INVALID_ARG, CUDA. */
+tacchi_status tacchi_shade(const tacchi_render_params *rp, const float *H_dev, int w,
+                           int hgt, double pixel_x_m, double pixel_y_m, double z_top_m,
+                           float *rgb_dev, void *stream);
+
+/* Copy the particle state out (synchronises).  Each pointer may be NULL to
+ * skip it; all are dev: u float [3][N] (cells), v float [3][N] (m/s),
+ * C float [9][N] (1/s), Fm float [9][N] (F - I), flags uint8 [N] (bit 0 =
+ * base set of Eq. 10, bit 1 = top-layer surface particle).  Returns the
+ * sticky device error, if any, after copying. */
+tacchi_status tacchi_get_state(tacchi_handle h, float *u, float *v, float *C, float *Fm,
+                               uint8_t *flags);
+
+/* Replace the particle state (dev pointers in the layout of tacchi_get_state;
+ * v, C, Fm may be NULL for zero / zero / identity).  Clears the sticky error
+ * and re-sorts the particles.  Errors: INVALID_ARG (u NULL), CUDA. */
+tacchi_status tacchi_set_state(tacchi_handle h, const float *u, const float *v,
+                               const float *C, const float *Fm);
+
+/* Grid mass and momentum of the most recent particle-to-grid transfer
+ * (Eqs. 2-5), i.e. of the state at the start of the last substep of the last
+ * tacchi_step.  out: dev float [n_nodes][4] = (M_i, MG_i x, y, z), node
+ * index (k * grid[1] + j) * grid[0] + i.  Errors: STATE (no step yet). */
+tacchi_status tacchi_get_grid(tacchi_handle h, float *out);
+
+/* Wait for the context's queued work and report the sticky device error. */
+tacchi_status tacchi_sync(tacchi_handle h);
+
+/* Clear the sticky device error. */
+tacchi_status tacchi_clear_error(tacchi_handle h);
+
+/* The particle lattice tacchi_create would make, written to host arrays
+ * (no GPU needed): u float [3][N] cells, flags uint8 [N];
+ * N = 8 * nx * ny * nz.  Errors: INVALID_ARG. */
+tacchi_status tacchi_init_lattice(int nx, int ny, int nz, int pad_side, int pad_bottom,
+                                  uint64_t seed, int jitter, float *u, uint8_t *flags);
+
+/* Short English description of a status. */
+const char *tacchi_status_string(tacchi_status s);
+
+/* Library version as MAJOR * 10000 + MINOR * 100 + PATCH. */
+int tacchi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TACCHI_H */

@@ -1,0 +1,236 @@
+"""GB300-native Tacchi: MLS-MPM elastomer simulation and tactile rendering.
+
+Thin Python binding of the C ABI in ``include/tacchi.h``.  PyTorch provides
+device memory and streams; every step of the simulation and rendering runs in
+the library's CUDA kernels (``libtacchi.so``).  There is no CPU fallback: the
+binding raises when the library or a CUDA device is missing.
+
+Method: Tacchi (arXiv 2301.08343) -- Sec. III-A (MPM substep, Eqs. 1-11),
+Sec. III-B (height map and Phong shading, Eqs. 12-14), Sec. III-C (the
+indenter pose/velocity supplied by a main simulator).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+import numpy as np
+
+from . import _lib
+from ._lib import TacchiError, check, lib, ptr
+
+__all__ = ["Tacchi", "TacchiError", "IndenterKind", "default_render_params", "shade",
+           "init_lattice", "lib"]
+
+
+class IndenterKind:
+    NONE, SPHERE, CYLINDER, CONE, PRISM, HEIGHTMAP = range(6)
+
+
+def _torch():
+    import torch
+    if not torch.cuda.is_available():
+        raise RuntimeError("paper_2301_08343_gb300 needs a CUDA device (no CPU fallback)")
+    return torch
+
+
+def _stream_handle(torch, stream):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def default_render_params(n_lights=3, elevation_deg=30.0, ka=0.2, kd=0.6, ks=0.2, alpha=5.0):
+    """Three RGB lights 120 degrees apart in azimuth on the camera side
+    (this project's defaults; Eq. 12 leaves the constants to calibration)."""
+    rp = _lib.RenderParams()
+    rp.n_lights = n_lights
+    el = math.radians(elevation_deg)
+    cols = [(1.0, 0.0, 0.0), (0.0, 1.0, 0.0), (0.0, 0.0, 1.0)]
+    for m in range(n_lights):
+        az = math.radians(90.0 + 120.0 * m)
+        d = (math.cos(el) * math.cos(az), math.cos(el) * math.sin(az), -math.sin(el))
+        for a in range(3):
+            rp.dir[m][a] = d[a]
+            rp.diffuse[m][a] = cols[m % 3][a]
+            rp.specular[m][a] = 1.0
+    for a in range(3):
+        rp.ambient[a] = 1.0
+    rp.ka, rp.kd, rp.ks, rp.alpha = ka, kd, ks, alpha
+    return rp
+
+
+def render_params_from(d):
+    """RenderParams from a dict with n_lights, dirs, diffuse, specular,
+    ambient, ka, kd, ks, alpha."""
+    rp = _lib.RenderParams()
+    rp.n_lights = d["n_lights"]
+    for m in range(d["n_lights"]):
+        for a in range(3):
+            rp.dir[m][a] = d["dirs"][m][a]
+            rp.diffuse[m][a] = d["diffuse"][m][a]
+            rp.specular[m][a] = d["specular"][m][a]
+    for a in range(3):
+        rp.ambient[a] = d["ambient"][a]
+    rp.ka, rp.kd, rp.ks, rp.alpha = d["ka"], d["kd"], d["ks"], d["alpha"]
+    return rp
+
+
+def init_lattice(nx, ny, nz, pad_side=4, pad_bottom=3, seed=0, jitter=True):
+    """Host copy of the particle lattice tacchi_create makes (no GPU)."""
+    n = 8 * nx * ny * nz
+    u = np.zeros((3, n), np.float32)
+    fl = np.zeros(n, np.uint8)
+    check(lib().tacchi_init_lattice(nx, ny, nz, pad_side, pad_bottom, seed, int(bool(jitter)),
+                                    u.ctypes.data_as(C.POINTER(C.c_float)),
+                                    fl.ctypes.data_as(C.POINTER(C.c_uint8))), "tacchi_init_lattice")
+    return u, fl
+
+
+def shade(H, pixel_x, pixel_y, z_top, rp=None, out=None, stream=None):
+    """Phong shading (Eqs. 12-14) of a device height map H [h, w] (metres)."""
+    torch = _torch()
+    rp = rp or default_render_params()
+    h, w = H.shape
+    H = H.contiguous().float()
+    out = out if out is not None else torch.empty((h, w, 3), device=H.device, dtype=torch.float32)
+    check(lib().tacchi_shade(C.byref(rp), ptr(H), w, h, pixel_x, pixel_y, z_top, ptr(out),
+                             _stream_handle(torch, stream)), "tacchi_shade")
+    return out
+
+
+class Tacchi:
+    """One simulated sensor elastomer (a tacchi_handle)."""
+
+    def __init__(self, extent_m, dx, E=3.0e5, nu=0.45, density=1000.0, seed=0, jitter=True,
+                 pad_side=4, pad_bottom=3, pad_top=4, gravity=(0.0, 0.0, 0.0), fix_base=True,
+                 block=None, stream=None):
+        torch = _torch()
+        self._torch = torch
+        d = _lib.ElastomerDesc()
+        for a in range(3):
+            d.extent_m[a] = extent_m[a]
+            d.gravity[a] = gravity[a]
+        d.dx_m, d.E_pa, d.nu, d.density = dx, E, nu, density
+        d.seed, d.jitter = seed, int(bool(jitter))
+        d.pad_side, d.pad_bottom, d.pad_top = pad_side, pad_bottom, pad_top
+        d.free_base = 0 if fix_base else 1
+        if block is not None:
+            for a in range(3):
+                d.block[a] = block[a]
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        self._h = None
+        check(lib().tacchi_create(C.byref(d), C.c_void_p(self._stream.cuda_stream), C.byref(h)),
+              "tacchi_create")
+        self._h = h
+        info = _lib.Info()
+        check(lib().tacchi_info(self._h, C.byref(info)), "tacchi_info")
+        self.N = int(info.n_particles)
+        self.n_surface = int(info.n_surface)
+        self.grid = tuple(int(x) for x in info.grid)
+        self.n_nodes = int(info.n_nodes)
+        self.origin = tuple(float(x) for x in info.origin_m)
+        self.dx = float(info.dx_m)
+        self.z_top = float(info.z_top_m)
+        self.block = tuple(int(x) for x in info.block)
+        self.n_blocks = int(info.n_blocks)
+        self.device_bytes = int(info.device_bytes)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.extent = tuple(float(x) for x in extent_m)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().tacchi_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- indenter ---------------------------------------------------------
+    def set_indenter(self, kind=None, params=(), pose=None, vel=None, hm=None, hm_pixel=0.0):
+        dp = None
+        keep = None
+        if kind is not None:
+            dp = _lib.IndenterDesc()
+            dp.kind = int(kind)
+            for e, x in enumerate(params):
+                dp.params[e] = x
+            if hm is not None:
+                keep = np.ascontiguousarray(hm, np.float32)
+                dp.hm_h, dp.hm_w = keep.shape
+                dp.hm_pixel_m = hm_pixel
+                dp.hm = keep.ctypes.data_as(C.POINTER(C.c_float))
+        pz = None if pose is None else (C.c_double * 7)(*pose)
+        vz = None if vel is None else (C.c_double * 6)(*vel)
+        check(lib().tacchi_set_indenter(self._h, C.byref(dp) if dp is not None else None, pz, vz),
+              "tacchi_set_indenter")
+        del keep
+
+    def indenter_pose(self):
+        p = (C.c_double * 7)()
+        check(lib().tacchi_get_indenter_pose(self._h, p), "tacchi_get_indenter_pose")
+        return tuple(p)
+
+    # -- stepping -----------------------------------------------------------
+    def step(self, n_substeps, dt):
+        check(lib().tacchi_step(self._h, int(n_substeps), float(dt)), "tacchi_step")
+
+    def sync(self):
+        check(lib().tacchi_sync(self._h), "tacchi_sync")
+
+    def status(self) -> int:
+        """Synchronise and return the device status code (0 = OK)."""
+        return int(lib().tacchi_sync(self._h))
+
+    def clear_error(self):
+        check(lib().tacchi_clear_error(self._h), "tacchi_clear_error")
+
+    # -- rendering ------------------------------------------------------------
+    def _window(self, window):
+        if window is None:  # the whole top face
+            window = (0.0, 0.0, self.extent[0], self.extent[1])
+        return (C.c_double * 4)(*window)
+
+    def heightmap(self, w, h, window=None, fill_radius=8, out=None):
+        torch = self._torch
+        out = out if out is not None else torch.empty((h, w), device=self.device, dtype=torch.float32)
+        check(lib().tacchi_heightmap(self._h, w, h, self._window(window), fill_radius, ptr(out)),
+              "tacchi_heightmap")
+        return out
+
+    def render(self, w, h, window=None, rp=None, fill_radius=8, out=None, out_height=None):
+        torch = self._torch
+        rp = rp or default_render_params()
+        out = out if out is not None else torch.empty((h, w, 3), device=self.device, dtype=torch.float32)
+        check(lib().tacchi_render(self._h, C.byref(rp), w, h, self._window(window), fill_radius,
+                                  ptr(out), ptr(out_height)), "tacchi_render")
+        return out
+
+    # -- state ----------------------------------------------------------------
+    def get_state(self):
+        torch = self._torch
+        n = self.N
+        f = lambda *s: torch.empty(s, device=self.device, dtype=torch.float32)
+        u, v, Cm, Fm = f(3, n), f(3, n), f(9, n), f(9, n)
+        flags = torch.empty(n, device=self.device, dtype=torch.uint8)
+        st = lib().tacchi_get_state(self._h, ptr(u), ptr(v), ptr(Cm), ptr(Fm), ptr(flags))
+        return dict(u=u, v=v, C=Cm, Fm=Fm, flags=flags, status=int(st))
+
+    def set_state(self, u, v=None, Cm=None, Fm=None):
+        torch = self._torch
+        dev = lambda t, r: None if t is None else torch.as_tensor(t, dtype=torch.float32).reshape(
+            r, self.N).contiguous().to(self.device)
+        tu, tv, tC, tF = dev(u, 3), dev(v, 3), dev(Cm, 9), dev(Fm, 9)
+        check(lib().tacchi_set_state(self._h, ptr(tu), ptr(tv), ptr(tC), ptr(tF)), "tacchi_set_state")
+        check(lib().tacchi_sync(self._h), "tacchi_set_state")
+
+    def get_grid(self):
+        """[n_nodes, 4] = (M, MG) of the last particle-to-grid transfer."""
+        torch = self._torch
+        out = torch.empty((self.n_nodes, 4), device=self.device, dtype=torch.float32)
+        check(lib().tacchi_get_grid(self._h, ptr(out)), "tacchi_get_grid")
+        self.sync()
+        return out

@@ -1,0 +1,133 @@
+// render.cu -- tactile rendering kernels for sm_103a (Tacchi, arXiv
+// 2301.08343, Sec. III-B).
+//
+//   k_hm_clear / k_hm_splat / k_hm_fill  height map of the deformed top
+//       surface: z-max splat of the top-layer particles (coverage radius
+//       dx/2, decided in FP32 with a fixed operation order), then
+//       nearest-covered-pixel hole filling within a bounded radius.
+//   k_shade  Phong shading, Eqs. 12-14, one thread per pixel.
+#include "tacchi_internal.cuh"
+
+#include <climits>
+
+namespace tacchi {
+
+// Monotone map of floats to ints so that atomicMax orders heights.
+__device__ __forceinline__ int ordered_from_float(float f) {
+  const int i = __float_as_int(f);
+  return i >= 0 ? i : i ^ 0x7FFFFFFF;
+}
+__device__ __forceinline__ float float_from_ordered(int i) {
+  return __int_as_float(i >= 0 ? i : i ^ 0x7FFFFFFF);
+}
+
+__global__ void __launch_bounds__(256) k_hm_clear(int *cov, long long n) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) cov[e] = INT_MIN;
+}
+
+__global__ void __launch_bounds__(256) k_hm_splat(HeightmapArgs a) {
+  const int s = blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= a.Ns) return;
+  const uint32_t p = a.surf[s];
+  const float ux = a.u[p], uy = a.u[a.Ntot + p], uz = a.u[2 * a.Ntot + p];
+  // rest top plane plus the particle's vertical displacement (metres)
+  const float h = a.z_top + a.dx * (uz - a.z0[s]);
+  if (!(isfinite(ux) && isfinite(uy) && isfinite(h))) return;
+  // conservative pixel box of the disc of radius 1/2 cell; the exact test decides
+  int c0 = (int)floorf((ux - 0.5f - a.A0X) / a.SX) - 1;
+  int c1 = (int)ceilf((ux + 0.5f - a.A0X) / a.SX) + 1;
+  int r0 = (int)floorf((uy - 0.5f - a.A0Y) / a.SY) - 1;
+  int r1 = (int)ceilf((uy + 0.5f - a.A0Y) / a.SY) + 1;
+  c0 = max(c0, 0);
+  r0 = max(r0, 0);
+  c1 = min(c1, a.w - 1);
+  r1 = min(r1, a.h - 1);
+  const int key = ordered_from_float(h);
+  for (int r = r0; r <= r1; ++r) {
+    const float qy = __fmaf_rn((float)r, a.SY, a.A0Y);
+    const float ey = __fsub_rn(qy, uy);
+    const float b2 = __fmul_rn(ey, ey);
+    for (int c = c0; c <= c1; ++c) {
+      const float qx = __fmaf_rn((float)c, a.SX, a.A0X);
+      const float ex = __fsub_rn(qx, ux);
+      if (__fadd_rn(__fmul_rn(ex, ex), b2) <= 0.25f) atomicMax(a.cov + (long long)r * a.w + c, key);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(256) k_hm_fill(HeightmapArgs a) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)a.w * a.h) return;
+  const int r = (int)(e / a.w), c = (int)(e % a.w);
+  const int key = a.cov[e];
+  if (key != INT_MIN) {
+    a.out[e] = float_from_ordered(key);
+    return;
+  }
+  const int R = a.fill_radius;
+  long long best = -1;
+  int bestd = 0;
+  for (int rr = max(r - R, 0); rr <= min(r + R, a.h - 1); ++rr)
+    for (int cc = max(c - R, 0); cc <= min(c + R, a.w - 1); ++cc) {
+      const long long f = (long long)rr * a.w + cc;
+      if (a.cov[f] == INT_MIN) continue;
+      const int d = (rr - r) * (rr - r) + (cc - c) * (cc - c);
+      if (best < 0 || d < bestd) {  // row-major scan: first hit wins ties
+        best = f;
+        bestd = d;
+      }
+    }
+  a.out[e] = best >= 0 ? float_from_ordered(a.cov[best]) : a.z_top;
+}
+
+cudaError_t launch_heightmap(const HeightmapArgs &a, cudaStream_t st) {
+  const long long P = (long long)a.w * a.h;
+  const unsigned gp = (unsigned)((P + 255) / 256);
+  k_hm_clear<<<gp, 256, 0, st>>>(a.cov, P);
+  if (a.Ns > 0) k_hm_splat<<<(a.Ns + 255) / 256, 256, 0, st>>>(a);
+  k_hm_fill<<<gp, 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Eqs. 12-14: D = z_top - H; N = normalize(dD/dx, dD/dy, -1) by central
+// differences with replicated edges; V = (0, 0, -1);
+// I = ka ia + sum_m kd max(L.N, 0) i_md + ks max(R.V, 0)^alpha i_ms,
+// R = 2 (L.N) N - L; clamped to [0, 1].
+__global__ void __launch_bounds__(256) k_shade(ShadeArgs a, const float *__restrict__ H, float *__restrict__ rgb) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)a.w * a.h) return;
+  const int r = (int)(e / a.w), c = (int)(e % a.w);
+  const int cl = c > 0 ? c - 1 : 0, cr = c < a.w - 1 ? c + 1 : a.w - 1;
+  const int ru = r > 0 ? r - 1 : 0, rd = r < a.h - 1 ? r + 1 : a.h - 1;
+  const float Dl = a.z_top - H[(long long)r * a.w + cl], Dr = a.z_top - H[(long long)r * a.w + cr];
+  const float Du = a.z_top - H[(long long)ru * a.w + c], Dd = a.z_top - H[(long long)rd * a.w + c];
+  const float gx = (Dr - Dl) * a.inv2px;
+  const float gy = (Dd - Du) * a.inv2py;
+  const float inn = 1.0f / sqrtf(gx * gx + gy * gy + 1.0f);
+  const float N0 = gx * inn, N1 = gy * inn, N2 = -inn;
+  float I0 = a.ka * a.amb[0], I1 = a.ka * a.amb[1], I2 = a.ka * a.amb[2];
+  for (int m = 0; m < a.n_lights; ++m) {
+    const float L0 = a.dir[m][0], L1 = a.dir[m][1], L2 = a.dir[m][2];
+    const float LN = L0 * N0 + L1 * N1 + L2 * N2;
+    const float R2 = 2.0f * LN * N2 - L2;  // R.V with V = (0, 0, -1) is -R_z
+    const float RV = -R2;
+    const float dif = a.kd * fmaxf(LN, 0.0f);
+    const float spe = RV > 0.0f ? a.ks * powf(RV, a.alpha) : 0.0f;
+    I0 += dif * a.dif[m][0] + spe * a.spe[m][0];
+    I1 += dif * a.dif[m][1] + spe * a.spe[m][1];
+    I2 += dif * a.dif[m][2] + spe * a.spe[m][2];
+  }
+  rgb[3 * e + 0] = fminf(fmaxf(I0, 0.0f), 1.0f);
+  rgb[3 * e + 1] = fminf(fmaxf(I1, 0.0f), 1.0f);
+  rgb[3 * e + 2] = fminf(fmaxf(I2, 0.0f), 1.0f);
+}
+
+cudaError_t launch_shade(const ShadeArgs &a, const float *H, float *rgb, cudaStream_t st) {
+  const long long P = (long long)a.w * a.h;
+  k_shade<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(a, H, rgb);
+  return cudaGetLastError();
+}
+
+}  // namespace tacchi

@@ -1,0 +1,176 @@
+// tacchi_internal.cuh -- device-side data layout and small shared helpers of
+// the GB300 Tacchi library.  Included only by the library's own .cu files.
+//
+// Layout in HBM (all instances of a batch concatenated):
+//   particles (global index p, total Ntot), structure of arrays:
+//     u  [3][Ntot]  position in grid-cell units from the instance's node 0
+//     Fm [9][Ntot]  F - I, row-major
+//     v  [3][Ntot], C [9][Ntot]  only written at the end of a step call and
+//                                read by the first transfer of the next call
+//     flags [Ntot]  bit0 base set (Eq. 10), bit1 top-layer surface particle
+//   sort: idx [Ntot] particle ids grouped by grid block, bstart [Nblk+1],
+//     key [Ntot], bcount/cursor [Nblk]
+//   grid (global node n, total Nnodes): gmm float4 (M, MGx, MGy, MGz),
+//     gv float4 (Vx, Vy, Vz, 0)
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace tacchi {
+
+enum : int {
+  ERRBIT_OUT_OF_GRID = 1,
+  ERRBIT_NUMERICAL = 2,
+  ERRBIT_CFL = 4,
+  ERRBIT_TIMEOUT = 8,
+};
+
+enum : int {
+  IND_NONE = 0,
+  IND_SPHERE = 1,
+  IND_CYLINDER = 2,
+  IND_CONE = 3,
+  IND_PRISM = 4,
+  IND_HEIGHTMAP = 5,
+};
+
+// Indenter frame of one substep, rounded to FP32 on the host from the FP64
+// pose.  Local coordinates of node X: l = R^T (X - c), in cells.
+struct IndenterFrame {
+  float c[3];     // centre, cells
+  float r[9];     // local -> world rotation, row-major
+  float vlin[3];  // m/s
+  float w[3];     // rad/s
+};
+
+struct IndenterShape {
+  int kind;
+  float s0, s1, s2, s3;        // shape constants in cells (see set_indenter)
+  float inv_pix, offx, offy;   // height-map sampling
+  int hm_w, hm_h;
+  const float *hm;             // device, heights in cells
+};
+
+// One elastomer instance of a batch.
+struct Instance {
+  int G[3];          // nodes per axis
+  int nb[3];         // sort blocks per axis
+  int pad_bottom;    // node layer of the base plane
+  int fix_base;
+  long long node_off, N, part_off, block_off, nblocks;
+  float dx, inv_dx;  // m, 1/m
+  float m, V0;       // particle mass (kg), rest volume (m^3)
+  float mu, la;      // Lame parameters (Pa)
+  float gdt[3];      // gravity (m/s^2), multiplied by dt on use
+  IndenterShape shape;
+  const IndenterFrame *frames;  // [substep] for the running step chunk
+};
+
+struct Batch {
+  const Instance *inst;       // [n_inst]
+  const long long *node_offs; // [n_inst] first global node of each instance
+  const long long *part_offs; // [n_inst] first global particle of each instance
+  const uint32_t *block_inst; // [Nblk] instance of each global block
+  int n_inst;
+  long long Ntot, Nnodes, Nblk;
+  float *u, *Fm, *v, *C;
+  const uint8_t *flags;
+  uint32_t *idx, *key, *bstart, *bcount, *cursor;
+  float4 *gmm, *gv;
+  int *err, *movers;
+};
+
+// Largest i with offs[i] <= x (offs ascending, offs[0] = 0).
+__device__ __forceinline__ int find_instance(const long long *offs, int n, long long x) {
+  int lo = 0, hi = n - 1;
+  while (lo < hi) {
+    int mid = (lo + hi + 1) >> 1;
+    if (__ldg(offs + mid) <= x) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Inside test of grid node (i, j, k), FP32, operation order fixed by
+// round-to-nearest intrinsics (no contraction), so that any FP32
+// implementation of the same sequence decides identically.
+__device__ __forceinline__ bool inside_indenter(const IndenterShape &s, const IndenterFrame &f,
+                                                int i, int j, int k) {
+  if (s.kind == IND_NONE) return false;
+  float d0 = __fsub_rn((float)i, f.c[0]);
+  float d1 = __fsub_rn((float)j, f.c[1]);
+  float d2 = __fsub_rn((float)k, f.c[2]);
+  if (s.kind == IND_SPHERE) {
+    float r2 = __fadd_rn(__fadd_rn(__fmul_rn(d0, d0), __fmul_rn(d1, d1)), __fmul_rn(d2, d2));
+    return r2 <= s.s0;
+  }
+  float l0 = __fadd_rn(__fadd_rn(__fmul_rn(f.r[0], d0), __fmul_rn(f.r[3], d1)), __fmul_rn(f.r[6], d2));
+  float l1 = __fadd_rn(__fadd_rn(__fmul_rn(f.r[1], d0), __fmul_rn(f.r[4], d1)), __fmul_rn(f.r[7], d2));
+  float l2 = __fadd_rn(__fadd_rn(__fmul_rn(f.r[2], d0), __fmul_rn(f.r[5], d1)), __fmul_rn(f.r[8], d2));
+  switch (s.kind) {
+    case IND_CYLINDER:
+      return fabsf(l0) <= s.s1 && __fadd_rn(__fmul_rn(l1, l1), __fmul_rn(l2, l2)) <= s.s0;
+    case IND_CONE: {
+      if (!(l2 >= 0.f && l2 <= s.s1)) return false;
+      float tz = __fmul_rn(s.s0, l2);
+      return __fadd_rn(__fmul_rn(l0, l0), __fmul_rn(l1, l1)) <= __fmul_rn(tz, tz);
+    }
+    case IND_PRISM:
+      if (!(fabsf(l1) <= s.s1 && l2 >= 0.f && l2 <= s.s2)) return false;
+      return fabsf(l0) <= __fmul_rn(s.s0, l2);
+    case IND_HEIGHTMAP: {
+      const int w = s.hm_w, h = s.hm_h;
+      float fx = __fadd_rn(__fmul_rn(l0, s.inv_pix), s.offx);
+      float fy = __fadd_rn(__fmul_rn(l1, s.inv_pix), s.offy);
+      if (fx < -0.5f || fx > __fsub_rn((float)w, 0.5f) || fy < -0.5f || fy > __fsub_rn((float)h, 0.5f))
+        return false;
+      float cx = fx < 0.f ? 0.f : (fx > (float)(w - 1) ? (float)(w - 1) : fx);
+      float cy = fy < 0.f ? 0.f : (fy > (float)(h - 1) ? (float)(h - 1) : fy);
+      int ix = (int)floorf(cx), iy = (int)floorf(cy);
+      ix = ix > w - 2 ? w - 2 : ix;
+      iy = iy > h - 2 ? h - 2 : iy;
+      float tx = __fsub_rn(cx, (float)ix), ty = __fsub_rn(cy, (float)iy);
+      float ux = __fsub_rn(1.0f, tx), uy = __fsub_rn(1.0f, ty);
+      const float *H = s.hm;
+      float r0 = __fadd_rn(__fmul_rn(__ldg(H + iy * w + ix), ux), __fmul_rn(__ldg(H + iy * w + ix + 1), tx));
+      float r1 = __fadd_rn(__fmul_rn(__ldg(H + (iy + 1) * w + ix), ux),
+                           __fmul_rn(__ldg(H + (iy + 1) * w + ix + 1), tx));
+      float hh = __fadd_rn(__fmul_rn(r0, uy), __fmul_rn(r1, ty));
+      return l2 >= -hh && l2 <= s.s0;
+    }
+    default:
+      return false;
+  }
+}
+
+// Launchers implemented in mpm.cu / render.cu (host side).
+struct SortBlock { int x, y, z; };
+cudaError_t launch_grid_update(const Batch &b, int substep, float dt, int clear, cudaStream_t st);
+cudaError_t launch_transfer(const Batch &b, SortBlock blk, int mode, float dt, cudaStream_t st);
+cudaError_t launch_sort(const Batch &b, SortBlock blk, int force, cudaStream_t st);
+
+enum : int { XFER_P2G = 1, XFER_G2P = 2, XFER_FUSED = 3 };
+
+struct HeightmapArgs {
+  const float *u;         // particle positions [3][Ntot]
+  long long Ntot;
+  const uint32_t *surf;   // [Ns] global particle ids of top-layer particles
+  const float *z0;        // [Ns] rest z (cells)
+  int Ns;
+  float A0X, A0Y, SX, SY; // pixel (r, c) centre = (c*SX + A0X, r*SY + A0Y) in cells
+  float z_top, dx;        // m
+  int w, h, fill_radius;
+  int *cov;               // [h*w] scratch, ordered-int heights
+  float *out;             // [h*w] metres
+};
+cudaError_t launch_heightmap(const HeightmapArgs &a, cudaStream_t st);
+
+struct ShadeArgs {
+  int n_lights;
+  float dir[8][3], dif[8][3], spe[8][3], amb[3];
+  float ka, kd, ks, alpha;
+  float inv2px, inv2py, z_top;
+  int w, h;
+};
+cudaError_t launch_shade(const ShadeArgs &a, const float *H, float *rgb, cudaStream_t st);
+
+}  // namespace tacchi

@@ -1,0 +1,323 @@
+"""GPU path vs the FP64 oracle, through the C ABI (marked gpu).
+
+Tolerances (FP32 kernels against FP64 arithmetic):
+  grid mass / momentum of one transfer from an identical state:
+      max_i |dX_i| / max_i |X_i| <= 1e-5;
+  one substep from an identical state: positions <= 2e-5 cells, v and C
+      <= 1e-4 relative to their largest magnitude, F - I <= 1e-6;
+  C0 workload, 500 substeps from the identical FP32 lattice: positions
+      <= 1e-3 dx; height map from an identical state <= 1e-3 dx;
+  shading from an identical height map <= 2e-5 per channel.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    oracle.set_threads(16)
+
+
+def T():
+    import paper_2301_08343_gb300 as T_
+    return T_
+
+
+def make_pair(b, seed=None, fix_base=True, block=None, jitter=True):
+    seed = b.seed if seed is None else seed
+    g = T().Tacchi(b.extent_m, b.dx, b.E, b.nu, b.rho, seed=seed, jitter=jitter,
+                   pad_side=b.pad_side, pad_bottom=b.pad_bottom, pad_top=b.pad_top,
+                   fix_base=fix_base, block=block)
+    o = oracle.Sim(b.nx, b.ny, b.nz, b.dx, b.E, b.nu, b.rho, b.pad_side, b.pad_bottom, b.pad_top,
+                   fix_base=fix_base)
+    u0, fl = oracle.lattice(b.nx, b.ny, b.nz, b.pad_side, b.pad_bottom, seed, jitter)
+    o.set_state(u0, flags=fl)
+    o.set_rest(u0)
+    return g, o, u0, fl
+
+
+def gstate(g):
+    s = g.get_state()
+    assert s["status"] == 0, s["status"]
+    return {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in s.items()}
+
+
+def rel(a, b):
+    return np.abs(np.asarray(a, np.float64) - b).max() / max(np.abs(b).max(), 1e-300)
+
+
+def grid_gpu(g):
+    G = g.get_grid().cpu().numpy().astype(np.float64)
+    return G[:, 0], G[:, 1:].T
+
+
+SMALL = W.Block(10, 9, 3, 0.5e-3, seed=3)  # several 4^3 blocks plus a ragged tail
+
+
+def test_initial_lattice_is_the_oracles_bit_for_bit():
+    g, o, u0, fl = make_pair(W.C0)
+    s = gstate(g)
+    assert np.array_equal(s["u"].view(np.uint32), u0.view(np.uint32))
+    assert np.array_equal(s["flags"], fl)
+    assert np.all(s["Fm"] == 0) and np.all(s["v"] == 0) and np.all(s["C"] == 0)
+
+
+@pytest.mark.parametrize("block", [(4, 4, 4), (8, 8, 4), (8, 8, 8), (16, 8, 4)])
+def test_p2g_grid_momentum_matches_oracle_from_identical_state(block):
+    """Eqs. 2-5 on a random near-rest state: 1e-5 relative on M and MG."""
+    b = SMALL
+    g, o, u0, fl = make_pair(b, block=block, fix_base=False)
+    u, v, Cm, Fm = W.perturbed_state(u0, 21)
+    g.set_state(u, v, Cm, Fm)
+    o.set_state(u, v, Cm, Fm, fl)
+    dt = 1e-5
+    g.step(1, dt)  # the grid kept is the P2G of the state at the start
+    M, MG = grid_gpu(g)
+    Mo, MGo = o.p2g(dt)
+    assert rel(M, Mo) <= 1e-5
+    assert rel(MG, MGo) <= 1e-5
+
+
+def test_one_substep_state_matches_oracle():
+    b = SMALL
+    g, o, u0, fl = make_pair(b)
+    u, v, Cm, Fm = W.perturbed_state(u0, 22)
+    g.set_state(u, v, Cm, Fm)
+    o.set_state(u, v, Cm, Fm, fl)
+    R = 1.5e-3
+    pose = (2.5e-3, 2.2e-3, b.nz * b.dx + R - 0.4e-3, 1, 0, 0, 0)
+    vel = (0.05, 0.0, -0.2, 0.0, 0.0, 3.0)
+    g.set_indenter(T().IndenterKind.SPHERE, (R,), pose, vel)
+    o.set_indenter(oracle.IND_SPHERE, (R,), pose, vel)
+    dt = 1e-5
+    g.step(1, dt)
+    assert o.substep(dt) == 0
+    s = gstate(g)
+    xi, vo, Co, Fo = o.state()
+    assert np.abs(s["u"] - xi).max() <= 2e-5
+    assert rel(s["v"], vo) <= 1e-4
+    assert rel(s["C"], Co) <= 1e-4
+    assert np.abs(s["Fm"] - (Fo - np.eye(3).reshape(9, 1))).max() <= 1e-6
+    assert np.allclose(g.indenter_pose(), o.pose(), rtol=0, atol=1e-15)
+
+
+def test_fused_transfer_grid_matches_oracle_after_one_substep():
+    """Two substeps: the kept grid is the fused kernel's P2G of the state
+    after substep 1, compared with the oracle's P2G of its own state there."""
+    b = SMALL
+    g, o, u0, fl = make_pair(b)
+    u, v, Cm, Fm = W.perturbed_state(u0, 23)
+    g.set_state(u, v, Cm, Fm)
+    o.set_state(u, v, Cm, Fm, fl)
+    dt = 1e-5
+    g.step(2, dt)
+    o.substep(dt)
+    o.substep(dt)
+    M, MG = grid_gpu(g)
+    Mo, MGo = o.last_grid()
+    assert rel(M, Mo) <= 1e-5
+    assert rel(MG, MGo) <= 1e-5
+
+
+def _c0_pair():
+    g, o, u0, fl = make_pair(W.C0)
+    g.set_indenter(T().IndenterKind.SPHERE, (W.C0_SPHERE_R,), W.c0_sphere_pose(), W.c0_sphere_vel())
+    o.set_indenter(oracle.IND_SPHERE, (W.C0_SPHERE_R,), W.c0_sphere_pose(), W.c0_sphere_vel())
+    return g, o, u0, fl
+
+
+@pytest.mark.parametrize("at", [100, 500])
+def test_c0_grid_momentum_per_substep_from_oracle_state(at):
+    """At substeps 100 and 500 of the C0 press, the oracle's own state
+    (rounded to FP32) is given to both sides for one more substep."""
+    g, o, u0, fl = _c0_pair()
+    assert o.run(at, W.C0_DT) == 0
+    us, vs, Cs, Fs = o.state_f32()
+    pose = o.pose()
+    g.set_state(us, vs, Cs, Fs)
+    o.set_state(us, vs, Cs, Fs, fl)
+    g.set_indenter(pose=pose, vel=W.c0_sphere_vel())
+    o.set_indenter(oracle.IND_SPHERE, (W.C0_SPHERE_R,), pose, W.c0_sphere_vel())
+    g.step(1, W.C0_DT)
+    o.substep(W.C0_DT)
+    M, MG = grid_gpu(g)
+    Mo, MGo = o.last_grid()
+    assert rel(M, Mo) <= 1e-5
+    assert rel(MG, MGo) <= 1e-5
+
+
+def test_c0_positions_after_500_substeps_within_1e3_dx():
+    g, o, u0, fl = _c0_pair()
+    g.step(W.C0_SUBSTEPS, W.C0_DT)
+    assert o.run(W.C0_SUBSTEPS, W.C0_DT) == 0
+    s = gstate(g)
+    xi = o.state()[0]
+    err = np.abs(s["u"] - xi).max()  # cells, i.e. units of dx
+    assert err <= 1e-3, err
+    # the press really happened: surface particles moved down by > 0.5 mm
+    assert (u0[2] - s["u"][2]).max() * W.C0.dx > 0.5e-3
+
+
+def test_chunked_step_equals_unchunked_oracle():
+    """600 substeps run as graph chunks of 512 + 88."""
+    b = W.Block(6, 6, 2, 0.5e-3, seed=5)
+    g, o, u0, fl = make_pair(b)
+    R = 1.5e-3
+    pose = (1.5e-3, 1.5e-3, 1e-3 + R, 1, 0, 0, 0)
+    vel = (0, 0, -0.05, 0, 0, 0)
+    g.set_indenter(T().IndenterKind.SPHERE, (R,), pose, vel)
+    o.set_indenter(oracle.IND_SPHERE, (R,), pose, vel)
+    g.step(600, 1e-5)
+    assert o.run(600, 1e-5) == 0
+    assert np.abs(gstate(g)["u"] - o.state()[0]).max() <= 1e-3
+
+
+def _rot_quat(seed):
+    q = np.random.default_rng(seed).normal(size=4)
+    return tuple(q / np.linalg.norm(q))
+
+
+@pytest.mark.parametrize("kind", ["cylinder", "cone", "prism", "heightmap"])
+def test_indenter_shapes_decide_like_the_oracle(kind):
+    """Each shape, rotated, cutting into a block: one substep from rest; a
+    node decided differently would change nearby particle velocities by the
+    full indenter speed."""
+    b = W.Block(12, 12, 4, 0.5e-3, seed=6)
+    g, o, u0, fl = make_pair(b)
+    c = (3e-3, 3e-3, 2e-3)
+    q = _rot_quat({"cylinder": 1, "cone": 2, "prism": 3, "heightmap": 4}[kind])
+    pose = c + q
+    vel = (0.02, -0.01, -0.3, 1.0, -2.0, 0.5)
+    Tk = T().IndenterKind
+    hm = None
+    if kind == "cylinder":
+        args = (Tk.CYLINDER, oracle.IND_CYLINDER, (1.1e-3, 1.6e-3))
+    elif kind == "cone":
+        args = (Tk.CONE, oracle.IND_CONE, (math.radians(35), 2.2e-3))
+    elif kind == "prism":
+        args = (Tk.PRISM, oracle.IND_PRISM, (math.radians(40), 1.7e-3, 2.0e-3))
+    else:
+        hm = W.hm_perlin(n=32, pix=0.15e-3, seed=1, amp=0.8e-3)
+        args = (Tk.HEIGHTMAP, oracle.IND_HEIGHTMAP, (1.5e-3,))
+    g.set_indenter(args[0], args[2], pose, vel, hm=hm, hm_pixel=0.15e-3)
+    o.set_indenter(args[1], args[2], pose, vel, hm=hm, hm_pixel=0.15e-3)
+    dt = 1e-5
+    g.step(3, dt)
+    o.run(3, dt)
+    s = gstate(g)
+    xi, vo, Co, Fo = o.state()
+    assert np.abs(vo).max() > 0.05  # the indenter did act
+    assert rel(s["v"], vo) <= 1e-4
+    assert np.abs(s["u"] - xi).max() <= 2e-5
+
+
+def test_heightmap_matches_oracle_from_identical_state():
+    g, o, u0, fl = _c0_pair()
+    assert o.run(300, W.C0_DT) == 0
+    us, vs, Cs, Fs = o.state_f32()
+    g.set_state(us, vs, Cs, Fs)
+    o.set_state(us, vs, Cs, Fs, fl)
+    win = W.top_window(W.C0)
+    w, h = W.C0_IMAGE
+    Hg = g.heightmap(w, h, win).cpu().numpy()
+    Ho = o.heightmap(win, w, h)
+    assert np.abs(Hg - Ho).max() <= 1e-3 * W.C0.dx
+    assert Ho.min() < W.C0.nz * W.C0.dx - 0.2e-3  # indented
+    # a window wider than the block exercises hole filling
+    win2 = (-1.5e-3, -1e-3, 13.5e-3, 12.5e-3)
+    Hg2 = g.heightmap(97, 83, win2, fill_radius=5).cpu().numpy()
+    Ho2 = o.heightmap(win2, 97, 83, fill_radius=5)
+    assert np.abs(Hg2 - Ho2).max() <= 1e-3 * W.C0.dx
+
+
+def test_c0_heightmap_after_500_substeps():
+    """End to end: both sides run their own 500 substeps; the height maps
+    agree to 1e-3 dx wherever the coverage decision agrees, which is all but
+    a few pixels on disc edges; the median error is far below that."""
+    g, o, u0, fl = _c0_pair()
+    g.step(W.C0_SUBSTEPS, W.C0_DT)
+    assert o.run(W.C0_SUBSTEPS, W.C0_DT) == 0
+    win = W.top_window(W.C0)
+    w, h = W.C0_IMAGE
+    d = np.abs(g.heightmap(w, h, win).cpu().numpy() - o.heightmap(win, w, h)) / W.C0.dx
+    assert np.median(d) <= 1e-4
+    assert (d <= 1e-3).mean() >= 0.99
+
+
+def test_shading_matches_oracle_from_identical_heightmap():
+    P = T()
+    Lt = W.default_lights()
+    rpo = oracle.render_params(**{k: Lt[k] for k in ("n_lights",)}, dirs=Lt["dirs"],
+                               diffuse=Lt["diffuse"], specular=Lt["specular"],
+                               ambient=Lt["ambient"], ka=Lt["ka"], kd=Lt["kd"], ks=Lt["ks"],
+                               alpha=Lt["alpha"])
+    rpg = P.render_params_from(Lt)
+    w, h, pix, z_top = 131, 97, 1e-4, 3e-3
+    x = (np.arange(w) - w / 2) * pix
+    y = (np.arange(h) - h / 2) * pix
+    XX, YY = np.meshgrid(x, y, indexing="xy")
+    rng = np.random.default_rng(3)
+    H = (z_top - np.maximum(0.0, 0.8e-3 - (XX ** 2 + YY ** 2) / (2 * 4e-3))
+         + rng.normal(0, 2e-6, XX.shape)).astype(np.float32)
+    out = P.shade(torch.from_numpy(H).cuda(), pix, pix, z_top, rpg).cpu().numpy()
+    ref = oracle.shade(H.astype(np.float64), pix, pix, z_top, rpo)
+    assert np.abs(out - ref).max() <= 2e-5
+
+
+def test_render_equals_shade_of_heightmap():
+    g, o, u0, fl = _c0_pair()
+    g.step(200, W.C0_DT)
+    win = W.top_window(W.C0)
+    Hd = torch.empty((120, 120), device="cuda")
+    rgb = g.render(120, 120, win, out_height=Hd)
+    ref = T().shade(Hd, 1e-4, 1e-4, g.z_top)
+    assert torch.equal(rgb, ref)
+    host = np.zeros((120, 120, 3), np.float32)
+    from paper_2301_08343_gb300 import _lib
+    import ctypes as C
+    st = _lib.lib().tacchi_render(g._h, C.byref(T().default_render_params()), 120, 120,
+                                  (C.c_double * 4)(*win), 8, _lib.ptr(host), None)
+    assert st == 0 and np.array_equal(host, rgb.cpu().numpy())
+
+
+def test_tiny_instance_one_cell():
+    b = W.Block(1, 1, 1, 1e-3, seed=9)
+    g, o, u0, fl = make_pair(b, fix_base=False)
+    v = np.tile(np.array([[0.3], [-0.2], [0.1]], np.float32), (1, 8))
+    g.set_state(u0, v)
+    o.set_state(u0, v, None, None, fl)
+    g.step(20, 1e-5)
+    o.run(20, 1e-5)
+    assert np.abs(gstate(g)["u"] - o.state()[0]).max() <= 1e-5
+
+
+def test_out_of_grid_and_numerical_errors_are_reported_not_faulted():
+    b = W.Block(4, 4, 2, 0.5e-3, seed=2)
+    g, o, u0, fl = make_pair(b, fix_base=False)
+    u = u0.copy()
+    u[0, 0] = 2.2  # stencil base 1: inside the padding band
+    g.set_state(u)
+    g.step(1, 1e-5)
+    assert g.status() == -5
+    u = u0.copy()
+    Fm = np.zeros((9, u.shape[1]), np.float32)
+    Fm[0, 3] = np.nan
+    g.set_state(u, None, None, Fm)
+    g.step(1, 1e-5)
+    assert g.status() == -4
+    g.set_state(u0)
+    g.step(1, 1e-5)
+    assert g.status() == 0
