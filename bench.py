@@ -1,0 +1,381 @@
+#!/usr/bin/env python
+"""Throughput of the Tacchi hot path on GB300: MPM particle-substeps/s.
+
+One bench step = one frame of the GelSight-scale workload (32 x 24 x 4 mm
+elastomer, dX = 0.1 mm, 24,576,000 particles): reset the elastomer to rest,
+set one of the nine procedural indenters (cycled; depths 0.2-1.5 mm cycled),
+run 200 MLS-MPM substeps of dt = 1e-6 s pressing to that depth, and render
+the 640 x 480 height map and tactile image.  value = particles x substeps x
+steps / time (all ranks), timed with CUDA events on the simulator's stream;
+the particle state (2.7 GB) is far larger than L2.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+--impl reference times the FP64 CPU oracle on the host cores on bounded
+samples of the same workload (the paper's method has no GPU reference code).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import workloads as W  # noqa: E402
+
+METRIC = "MPM particle-substeps/s"
+UNIT = "particle-substeps/s"
+
+# Algorithmic traffic and work of the fused G2P+P2G transfer, per unit:
+#   per particle-substep: read u (12 B) and F - I (36 B), write both (48 B);
+#   per grid node: read V (16 B float4) and accumulate M, MG (16 B float4).
+BYTES_PER_PARTICLE = 96
+BYTES_PER_NODE = 32
+# FP32 operations per particle in the fused transfer (FMA = 2), tallied from
+# the kernel source with three Newton polar iterations: G2P 641, stress 420,
+# P2G 385.
+FLOPS_PER_PARTICLE = 1446
+# FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz.
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+WORKLOADS = {
+    # name: (block, dt, substeps per step, image)
+    "c1": (W.C1, W.C1_DT, 200, W.C1_IMAGE),
+    "c1-quarter": (W.Block(160, 120, 40, 0.1e-3, pad_side=10, pad_top=20), W.C1_DT, 200, (320, 240)),
+    "c0": (W.C0, W.C0_DT, 500, W.C0_IMAGE),
+}
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 7:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax = float(f[1])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+def indenter_for_step(block, s, substeps, dt):
+    """Indenter s (cycled over the nine shapes and four depths): its tip
+    starts at the rest top face over the block centre and moves straight
+    down to the step's depth over the step's substeps."""
+    ind = W.c1_indenters()
+    name, params, hm, tip = ind[s % len(ind)]
+    depth = W.C1_DEPTHS[s % len(W.C1_DEPTHS)]
+    z_top = block.nz * block.dx
+    pose = (block.nx * block.dx / 2, block.ny * block.dx / 2, z_top + tip, 1.0, 0.0, 0.0, 0.0)
+    vel = (0.0, 0.0, -depth / (substeps * dt), 0.0, 0.0, 0.0)
+    return name, params, hm, pose, vel, depth
+
+
+def kind_of(name, K):
+    base = name.split(":")[0]
+    return {"sphere": K.SPHERE, "cylinder": K.CYLINDER, "cone": K.CONE, "prism": K.PRISM,
+            "heightmap": K.HEIGHTMAP}[base]
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_2301_08343_gb300 as T
+
+    block, dt, substeps, (w, h) = WORKLOADS[args.workload]
+    if args.substeps:
+        substeps = args.substeps
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    sim = T.Tacchi(block.extent_m, block.dx, block.E, block.nu, block.rho, seed=block.seed + rank,
+                   pad_side=block.pad_side, pad_bottom=block.pad_bottom, pad_top=block.pad_top)
+    rest = sim.get_state()
+    assert rest["status"] == 0
+    rest_u = rest["u"].clone()
+    win = W.top_window(block)
+    rp = T.default_render_params()
+    img = torch.empty((h, w, 3), device=dev)
+    hmap = torch.empty((h, w), device=dev)
+
+    def one_step(s, host_out=None):
+        name, params, hm, pose, vel, depth = indenter_for_step(block, s, substeps, dt)
+        T.lib().tacchi_set_state(sim._h, T._lib.ptr(rest_u), None, None, None)
+        sim.set_indenter(kind_of(name, T.IndenterKind), params, pose, vel, hm=hm, hm_pixel=0.1e-3)
+        sim.step(substeps, dt)
+        if host_out is None:
+            sim.render(w, h, win, rp, out=img, out_height=hmap)
+        else:
+            sim.render(w, h, win, rp, out=host_out[0], out_height=host_out[1])
+        st = sim.status()  # the next reset clears the device error word
+        if st != 0:
+            raise RuntimeError(f"step {s} ({name}, depth {depth*1e3:.1f} mm) failed with status {st}")
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    for s in range(args.warmup):
+        one_step(s)
+
+    # device-resident timed region
+    clocks = ClockSampler(local_rank)
+    sim.set_profiling(True)
+    sim.profile(reset=True)
+    barrier()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s in range(args.steps):
+        one_step(args.warmup + s)
+    e1.record(stream)
+    barrier()
+    clk = clocks.stop()
+    sim.set_profiling(False)
+    ms = e0.elapsed_time(e1)
+    prof = sim.profile(reset=True)
+
+    # end-to-end through the C ABI with host buffers: per step the indenter
+    # description goes in from host memory and the image and height map come
+    # back to pinned host memory
+    host_img = torch.empty((h, w, 3), dtype=torch.float32).pin_memory()
+    host_h = torch.empty((h, w), dtype=torch.float32).pin_memory()
+    e_steps = max(1, min(args.steps, 5))
+    barrier()
+    t0 = time.perf_counter()
+    for s in range(e_steps):
+        one_step(args.warmup + s, (host_img, host_h))
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    hm_bytes = sum(0 if indenter_for_step(block, args.warmup + s, substeps, dt)[2] is None else
+                   indenter_for_step(block, args.warmup + s, substeps, dt)[2].nbytes
+                   for s in range(e_steps)) / e_steps
+    frame_bytes = 72 * substeps + 256  # per-substep indenter frames + instance record
+    h2d = int(hm_bytes + frame_bytes + 13 * 8)
+    d2h = int(host_img.numel() * 4 + host_h.numel() * 4)
+
+    totals = torch.tensor([ms, e2e_s], dtype=torch.float64, device=dev)
+    if world > 1:
+        torch.distributed.all_reduce(totals, op=torch.distributed.ReduceOp.MAX)
+    ms, e2e_s = float(totals[0]), float(totals[1])
+    units_per_step = sim.N * substeps
+    value = units_per_step * args.steps * world / (ms * 1e-3)
+    e2e_value = units_per_step * e_steps * world / e2e_s
+
+    peaks, src = measured_peaks()
+    fused_avg_ms = prof["fused_ms"] / max(prof["fused_launches"], 1)
+    bytes_fused = BYTES_PER_PARTICLE * sim.N + BYTES_PER_NODE * sim.n_nodes
+    flops_fused = FLOPS_PER_PARTICLE * sim.N
+    gbs = bytes_fused / (fused_avg_ms * 1e-3) / 1e9
+    tfl = flops_fused / (fused_avg_ms * 1e-3) / 1e12
+    traffic = load_traffic(args.workload)
+    roof = {
+        "kernel": "k_transfer (fused G2P+P2G)",
+        "bound": "alu",
+        "achieved": round(tfl, 3), "peak": round(FP32_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
+        "frac": round(tfl / FP32_PEAK_TFLOPS, 4),
+        "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+        "traffic": traffic,
+        "hbm": {"achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": round(gbs / peaks["hbm_gbs"], 4), "peak_source": f"{src} (MEASURED_PEAKS hbm_gbs)"},
+        "avg_launch_ms": round(fused_avg_ms, 4),
+        "launches": prof["fused_launches"],
+        "algorithmic_bytes_per_launch": bytes_fused,
+        "algorithmic_flops_per_launch": flops_fused,
+    }
+    share = {k: round(prof[k + "_ms"] / max(ms, 1e-9) / 1.0, 4) for k in ("grid", "fused", "edge", "sort")}
+    launches = args.steps * (5 * substeps + 1 + 4 + 3)  # step graph, render, reset sort
+    result = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {block.nx}x{block.ny}x{block.nz} cells dx={block.dx*1e3:g} mm, "
+                               f"{sim.N} particles, {substeps} substeps dt={dt:g} s + {w}x{h} frame per step, "
+                               "nine procedural indenters cycled, depths 0.2-1.5 mm",
+                   "particles": sim.N, "grid_nodes": sim.n_nodes, "substeps_per_step": substeps,
+                   "image": [w, h], "sort_block": list(sim.block), "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (particle state %.2f GB)" % (sim.N * 96 / 1e9)},
+        "roofline": roof,
+        "kernel_share_of_step": share,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": e_steps},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    return result, sim
+
+
+def load_traffic(workload):
+    """DRAM bytes per fused launch from the committed ncu summary; null when
+    the kernel source changed since the counters were taken."""
+    import hashlib
+    p = os.path.join(ROOT, "profiles", "k_transfer_fused_traffic.json")
+    src = os.path.join(ROOT, "paper_2301_08343_gb300", "csrc", "mpm.cu")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+        with open(src, "rb") as f:
+            fp = hashlib.sha1(f.read()).hexdigest()[:12]
+        if d.get("mpm_cu_sha1") != fp or workload not in d:
+            return None
+        return d[workload]["dram_bytes_per_launch"]
+    except Exception:
+        return None
+
+
+# ---------------------------------------------------------------------------
+def oracle_sample(block, dt, n_substeps_target_s, threads):
+    """The FP64 oracle on an 80 x 60 x nz-cell sub-block of the workload with
+    the sphere press; returns (particle-substeps/s, description)."""
+    import oracle
+    oracle.set_threads(threads)
+    sub = W.Block(min(block.nx, 80), min(block.ny, 60), block.nz, block.dx, block.E, block.nu,
+                  block.rho, block.pad_side, block.pad_bottom, block.pad_top, block.seed)
+    o = oracle.Sim(sub.nx, sub.ny, sub.nz, sub.dx, sub.E, sub.nu, sub.rho, sub.pad_side,
+                   sub.pad_bottom, sub.pad_top)
+    u0, fl = oracle.lattice(sub.nx, sub.ny, sub.nz, sub.pad_side, sub.pad_bottom, sub.seed)
+    o.set_state(u0, flags=fl)
+    o.set_rest(u0)
+    R = 4e-3
+    z_top = sub.nz * sub.dx
+    o.set_indenter(oracle.IND_SPHERE, (R,), (sub.nx * sub.dx / 2, sub.ny * sub.dx / 2, z_top + R,
+                                             1, 0, 0, 0), (0, 0, -1.0, 0, 0, 0))
+    t = time.perf_counter()
+    o.run(1, dt)
+    one = time.perf_counter() - t
+    n = max(1, min(200, int(n_substeps_target_s / max(one, 1e-6))))
+    t = time.perf_counter()
+    o.run(n, dt)
+    el = time.perf_counter() - t
+    return o.N * n / el, (f"FP64 oracle, {sub.nx}x{sub.ny}x{sub.nz}-cell sub-block of the workload "
+                          f"({o.N} particles), sphere press, {n} substeps, {threads} threads, {el:.1f} s")
+
+
+def run_reference(args, rank, world):
+    """The oracle as it stands, on the host cores, bounded samples per step."""
+    block, dt, substeps, _ = WORKLOADS[args.workload]
+    threads = os.cpu_count() or 1
+    for _ in range(args.warmup):
+        oracle_sample(block, dt, 0.2, threads)
+    vals, descs = [], []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, d = oracle_sample(block, dt, 1.0, threads)
+        vals.append(v)
+        descs.append(d)
+    el = time.perf_counter() - t0
+    value = statistics.mean(vals)
+    return {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": el / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload} (bounded CPU samples)", "parallelism": "host threads"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": descs[-1]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c1")
+    ap.add_argument("--substeps", type=int, default=0, help="override substeps per step")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours" and not args.substeps:
+        print("note: fewer than 3 warm-up steps", file=sys.stderr)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank == 0:
+            print(json.dumps(run_reference(args, rank, world)))
+        return
+
+    import torch
+    if world > 1:
+        torch.cuda.set_device(local_rank)
+        torch.distributed.init_process_group("nccl")
+    result, sim = run_ours(args, rank, world, local_rank)
+    if rank == 0:
+        if not args.no_cpu_baseline:
+            block, dt, _, _ = WORKLOADS[args.workload]
+            v, desc = oracle_sample(block, dt, args.cpu_seconds, os.cpu_count() or 1)
+            result["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": os.cpu_count(),
+                                      "kind": "oracle", "sample": desc}
+        print(json.dumps(result))
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -209,6 +209,24 @@ tacchi_status tacchi_set_state(tacchi_handle h, const float *u, const float *v,
  * index (k * grid[1] + j) * grid[0] + i.  Errors: STATE (no step yet). */
 tacchi_status tacchi_get_grid(tacchi_handle h, float *out);
 
+/* Device time per kernel kind, accumulated while profiling is on. */
+typedef struct {
+  double grid_ms;        /* grid updates (Eq. 6 + boundaries) */
+  double fused_ms;       /* fused G2P + P2G transfers (Eqs. 2-5, 7-11) */
+  double edge_ms;        /* P2G-only and G2P-only transfers opening/closing a step */
+  double sort_ms;        /* particle sort (three kernels, timed together) */
+  int64_t grid_launches, fused_launches, edge_launches, sort_launches;
+} tacchi_profile_t;
+
+/* Turn kernel timing on (1) or off (0).  While on, every step graph carries
+ * CUDA events around its kernels and tacchi_step synchronises after each
+ * graph launch to accumulate their durations.  Errors: INVALID_ARG. */
+tacchi_status tacchi_set_profiling(tacchi_handle h, int on);
+
+/* Accumulated kernel times since profiling was turned on or last reset;
+ * reset != 0 zeroes them after reading.  out: host. */
+tacchi_status tacchi_get_profile(tacchi_handle h, tacchi_profile_t *out, int reset);
+
 /* Wait for the context's queued work and report the sticky device error. */
 tacchi_status tacchi_sync(tacchi_handle h);
 

@@ -185,6 +185,14 @@ class Tacchi:
         """Synchronise and return the device status code (0 = OK)."""
         return int(lib().tacchi_sync(self._h))
 
+    def set_profiling(self, on=True):
+        check(lib().tacchi_set_profiling(self._h, int(bool(on))), "tacchi_set_profiling")
+
+    def profile(self, reset=False):
+        p = _lib.Profile()
+        check(lib().tacchi_get_profile(self._h, C.byref(p), int(bool(reset))), "tacchi_get_profile")
+        return {f: getattr(p, f) for f, _ in p._fields_}
+
     def clear_error(self):
         check(lib().tacchi_clear_error(self._h), "tacchi_clear_error")
 

@@ -48,6 +48,13 @@ class Info(C.Structure):
                 ("device_bytes", C.c_size_t)]
 
 
+class Profile(C.Structure):
+    _fields_ = [("grid_ms", C.c_double), ("fused_ms", C.c_double), ("edge_ms", C.c_double),
+                ("sort_ms", C.c_double), ("grid_launches", C.c_int64),
+                ("fused_launches", C.c_int64), ("edge_launches", C.c_int64),
+                ("sort_launches", C.c_int64)]
+
+
 _lock = threading.Lock()
 _lib = None
 
@@ -68,6 +75,8 @@ SIGNATURES = {
     "tacchi_set_state": (C.c_int, [_vp, _vp, _vp, _vp, _vp]),
     "tacchi_get_grid": (C.c_int, [_vp, _vp]),
     "tacchi_sync": (C.c_int, [_vp]),
+    "tacchi_set_profiling": (C.c_int, [_vp, C.c_int]),
+    "tacchi_get_profile": (C.c_int, [_vp, C.POINTER(Profile), C.c_int]),
     "tacchi_clear_error": (C.c_int, [_vp]),
     "tacchi_init_lattice": (C.c_int, [C.c_int] * 5 + [C.c_uint64, C.c_int, _fp, _u8p]),
     "tacchi_status_string": (C.c_char_p, [C.c_int]),

@@ -82,10 +82,18 @@ tacchi_status cuda_status(cudaError_t e) { return e == cudaSuccess ? TACCHI_OK :
 
 }  // namespace
 
+// Timing events of one kernel (or kernel group) inside a captured graph.
+struct TimedSpan {
+  int kind;  // 0 grid, 1 fused, 2 edge transfer, 3 sort
+  cudaEvent_t a, b;
+};
+
 struct GraphEntry {
   int n = 0;
   float dt = 0.f;
+  bool profiled = false;
   cudaGraphExec_t exec = nullptr;
+  std::vector<TimedSpan> spans;
 };
 
 struct tacchi_ctx {
@@ -138,6 +146,9 @@ struct tacchi_ctx {
   double vel[6] = {0, 0, 0, 0, 0, 0};
 
   std::vector<GraphEntry> graphs;
+  bool profiling = false;
+  double prof_ms[4] = {0, 0, 0, 0};
+  int64_t prof_n[4] = {0, 0, 0, 0};
   bool stepped = false;
   size_t device_bytes = 0;
 };
@@ -241,46 +252,97 @@ void advance_pose(double *pose, const double *vel, double dt) {
   }
 }
 
-cudaError_t build_graph(tacchi_ctx *c, int n, float dt, cudaGraphExec_t *out) {
+void destroy_entry(GraphEntry &ge) {
+  if (ge.exec) cudaGraphExecDestroy(ge.exec);
+  for (auto &sp : ge.spans) {
+    cudaEventDestroy(sp.a);
+    cudaEventDestroy(sp.b);
+  }
+  ge.spans.clear();
+  ge.exec = nullptr;
+}
+
+// Enqueue one kernel (group) on the capture stream, bracketed by timing
+// events when the graph is built for profiling.
+template <typename F>
+cudaError_t timed(tacchi_ctx *c, GraphEntry *ge, int kind, F &&launch) {
+  if (!ge) return launch();
+  TimedSpan sp{kind, nullptr, nullptr};
+  cudaError_t e = cudaEventCreate(&sp.a);
+  if (e == cudaSuccess) e = cudaEventCreate(&sp.b);
+  if (e != cudaSuccess) return e;
+  ge->spans.push_back(sp);
+  // external record nodes: the events are really recorded when the graph runs
+  e = cudaEventRecordWithFlags(sp.a, c->cap, cudaEventRecordExternal);
+  if (e == cudaSuccess) e = launch();
+  if (e == cudaSuccess) e = cudaEventRecordWithFlags(sp.b, c->cap, cudaEventRecordExternal);
+  return e;
+}
+
+cudaError_t build_graph(tacchi_ctx *c, int n, float dt, GraphEntry *ge) {
   cudaGraph_t g = nullptr;
+  GraphEntry *pe = ge->profiled ? ge : nullptr;
   cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) return e;
-  cudaError_t le = cudaMemsetAsync(c->b.gmm, 0, sizeof(float4) * c->nodes, c->cap);
-  if (le == cudaSuccess) le = launch_transfer(c->b, c->blk, XFER_P2G, dt, c->cap);
+  const Batch &b = c->b;
+  const SortBlock blk = c->blk;
+  cudaStream_t s = c->cap;
+  cudaError_t le = cudaMemsetAsync(b.gmm, 0, sizeof(float4) * c->nodes, s);
+  if (le == cudaSuccess) le = timed(c, pe, 2, [&] { return launch_transfer(b, blk, XFER_P2G, dt, s); });
   for (int k = 0; k + 1 < n && le == cudaSuccess; ++k) {
-    le = launch_grid_update(c->b, k, dt, 1, c->cap);
-    if (le == cudaSuccess) le = launch_transfer(c->b, c->blk, XFER_FUSED, dt, c->cap);
-    if (le == cudaSuccess) le = launch_sort(c->b, c->blk, 0, c->cap);
+    le = timed(c, pe, 0, [&] { return launch_grid_update(b, k, dt, 1, s); });
+    if (le == cudaSuccess) le = timed(c, pe, 1, [&] { return launch_transfer(b, blk, XFER_FUSED, dt, s); });
+    if (le == cudaSuccess) le = timed(c, pe, 3, [&] { return launch_sort(b, blk, 0, s); });
   }
-  if (le == cudaSuccess) le = launch_grid_update(c->b, n - 1, dt, 0, c->cap);
-  if (le == cudaSuccess) le = launch_transfer(c->b, c->blk, XFER_G2P, dt, c->cap);
-  if (le == cudaSuccess) le = launch_sort(c->b, c->blk, 0, c->cap);
+  if (le == cudaSuccess) le = timed(c, pe, 0, [&] { return launch_grid_update(b, n - 1, dt, 0, s); });
+  if (le == cudaSuccess) le = timed(c, pe, 2, [&] { return launch_transfer(b, blk, XFER_G2P, dt, s); });
+  if (le == cudaSuccess) le = timed(c, pe, 3, [&] { return launch_sort(b, blk, 0, s); });
   e = cudaStreamEndCapture(c->cap, &g);
   if (le != cudaSuccess) {
     if (g) cudaGraphDestroy(g);
     return le;
   }
   if (e != cudaSuccess) return e;
-  e = cudaGraphInstantiate(out, g, 0);
+  e = cudaGraphInstantiate(&ge->exec, g, 0);
   cudaGraphDestroy(g);
   return e;
 }
 
-cudaError_t graph_for(tacchi_ctx *c, int n, float dt, cudaGraphExec_t *out) {
+cudaError_t graph_for(tacchi_ctx *c, int n, float dt, GraphEntry **out) {
   for (auto &ge : c->graphs)
-    if (ge.n == n && ge.dt == dt) {
-      *out = ge.exec;
+    if (ge.n == n && ge.dt == dt && ge.profiled == c->profiling) {
+      *out = &ge;
       return cudaSuccess;
     }
-  cudaGraphExec_t ex = nullptr;
-  cudaError_t e = build_graph(c, n, dt, &ex);
-  if (e != cudaSuccess) return e;
   if ((int)c->graphs.size() >= kMaxGraphs) {
-    cudaGraphExecDestroy(c->graphs.front().exec);
+    destroy_entry(c->graphs.front());
     c->graphs.erase(c->graphs.begin());
   }
-  c->graphs.push_back(GraphEntry{n, dt, ex});
-  *out = ex;
+  c->graphs.push_back(GraphEntry{});
+  GraphEntry &ge = c->graphs.back();
+  ge.n = n;
+  ge.dt = dt;
+  ge.profiled = c->profiling;
+  cudaError_t e = build_graph(c, n, dt, &ge);
+  if (e != cudaSuccess) {
+    destroy_entry(ge);
+    c->graphs.pop_back();
+    return e;
+  }
+  *out = &ge;
+  return cudaSuccess;
+}
+
+cudaError_t collect_profile(tacchi_ctx *c, GraphEntry *ge) {
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return e;
+  for (auto &sp : ge->spans) {
+    float ms = 0.f;
+    e = cudaEventElapsedTime(&ms, sp.a, sp.b);
+    if (e != cudaSuccess) return e;
+    c->prof_ms[sp.kind] += ms;
+    c->prof_n[sp.kind] += 1;
+  }
   return cudaSuccess;
 }
 
@@ -385,7 +447,7 @@ tacchi_status fill_shade_args(const tacchi_render_params *rp, int w, int h, doub
 void release(tacchi_ctx *c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
-  for (auto &g : c->graphs) cudaGraphExecDestroy(g.exec);
+  for (auto &g : c->graphs) destroy_entry(g);
   c->graphs.clear();
   void *bufs[] = {c->b.u, c->b.Fm, c->b.v, c->b.C, (void *)c->b.flags, c->b.idx, c->b.key, c->b.bstart,
                   c->b.bcount, c->b.cursor, c->b.gmm, c->b.gv, c->b.err, c->b.movers, c->d_inst, c->d_offs,
@@ -688,8 +750,8 @@ tacchi_status tacchi_step(tacchi_handle c, int n_substeps, double dt) {
   int left = n_substeps;
   while (left > 0) {
     const int n = std::min(left, kMaxChunk);
-    cudaGraphExec_t ex = nullptr;
-    CK(graph_for(c, n, fdt, &ex));
+    GraphEntry *ge = nullptr;
+    CK(graph_for(c, n, fdt, &ge));
     // the previous upload must have left the pinned staging buffer
     CK(cudaEventSynchronize(c->stage_done));
     tacchi_ctx::Stage *s = c->h_stage;
@@ -703,7 +765,8 @@ tacchi_status tacchi_step(tacchi_handle c, int n_substeps, double dt) {
     CK(cudaMemcpyAsync(c->d_inst, &s->inst, sizeof(Instance), cudaMemcpyHostToDevice, c->stream));
     CK(cudaMemcpyAsync(c->d_frames, s->frames, sizeof(IndenterFrame) * n, cudaMemcpyHostToDevice, c->stream));
     CK(cudaEventRecord(c->stage_done, c->stream));
-    CK(cudaGraphLaunch(ex, c->stream));
+    CK(cudaGraphLaunch(ge->exec, c->stream));
+    if (ge->profiled) CK(collect_profile(c, ge));
     left -= n;
   }
   c->stepped = true;
@@ -810,6 +873,30 @@ tacchi_status tacchi_get_grid(tacchi_handle c, float *out) {
   if (!c || !out) return TACCHI_ERR_INVALID_ARG;
   if (!c->stepped) return TACCHI_ERR_STATE;
   CK(cudaMemcpyAsync(out, c->b.gmm, sizeof(float4) * c->nodes, cudaMemcpyDeviceToDevice, c->stream));
+  return TACCHI_OK;
+}
+
+tacchi_status tacchi_set_profiling(tacchi_handle c, int on) {
+  if (!c) return TACCHI_ERR_INVALID_ARG;
+  c->profiling = on != 0;
+  return TACCHI_OK;
+}
+
+tacchi_status tacchi_get_profile(tacchi_handle c, tacchi_profile_t *o, int reset) {
+  if (!c || !o) return TACCHI_ERR_INVALID_ARG;
+  o->grid_ms = c->prof_ms[0];
+  o->fused_ms = c->prof_ms[1];
+  o->edge_ms = c->prof_ms[2];
+  o->sort_ms = c->prof_ms[3];
+  o->grid_launches = c->prof_n[0];
+  o->fused_launches = c->prof_n[1];
+  o->edge_launches = c->prof_n[2];
+  o->sort_launches = c->prof_n[3];
+  if (reset)
+    for (int k = 0; k < 4; ++k) {
+      c->prof_ms[k] = 0;
+      c->prof_n[k] = 0;
+    }
   return TACCHI_OK;
 }
 

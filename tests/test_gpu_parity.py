@@ -321,3 +321,17 @@ def test_out_of_grid_and_numerical_errors_are_reported_not_faulted():
     g.set_state(u0)
     g.step(1, 1e-5)
     assert g.status() == 0
+
+
+def test_profiling_counts_every_kernel_of_a_step():
+    g, o, u0, fl = make_pair(W.Block(6, 6, 2, 0.5e-3, seed=4))
+    g.set_profiling(True)
+    g.step(5, 1e-5)
+    g.step(5, 1e-5)
+    p = g.profile(reset=True)
+    g.set_profiling(False)
+    assert p["fused_launches"] == 8 and p["grid_launches"] == 10
+    assert p["edge_launches"] == 4 and p["sort_launches"] == 10
+    assert all(p[k] > 0 for k in ("fused_ms", "grid_ms", "edge_ms", "sort_ms"))
+    g.step(5, 1e-5)
+    assert g.profile()["fused_launches"] == 0

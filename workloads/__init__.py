@@ -51,7 +51,9 @@ C0_SPHERE_R = 3.0e-3
 C0_SPEED = 1.0e-3 / (C0_SUBSTEPS * C0_DT)  # 1 mm over 500 substeps = 0.2 m/s
 C0_IMAGE = (120, 120)
 
-C1 = Block(320, 240, 40, 0.1e-3)
+# 2 mm of grid above the gel and 1 mm at its sides leave room for the bulge
+# a deep press of a large flat-backed indenter raises in the incompressible gel
+C1 = Block(320, 240, 40, 0.1e-3, pad_side=10, pad_top=20)
 C1_DT = 1.0e-6
 C1_IMAGE = (640, 480)
 
@@ -167,17 +169,43 @@ def hm_perlin(n=128, pix=0.1e-3, seed=1, octaves=3, amp=1.0e-3):
     return (amp * acc).astype(np.float32)
 
 
-def hm_worn_sphere(n=128, pix=0.1e-3, R=4e-3, seed=2, n_pits=60, pit_r=0.3e-3, pit_d=0.15e-3):
-    """A spherical cap of radius R with Poisson-placed pits (a worn surface)."""
+def hm_worn_sphere(n=128, pix=0.1e-3, R=4e-3, cap=1.2e-3, seed=2, n_pits=60, pit_r=0.3e-3,
+                   pit_d=0.15e-3):
+    """A paraboloid cap (curvature radius R, height cap) with Poisson-placed
+    pits: a worn spherical indenter."""
     X, Y = _grid(n, pix)
     rng = np.random.default_rng(seed)
-    r2 = X ** 2 + Y ** 2
-    cap = np.where(r2 < R * R, np.sqrt(np.maximum(R * R - r2, 0.0)) - 0.0, 0.0)
-    base = R - (n * pix / 2) ** 2 / (2 * R)
-    h = np.maximum(cap - max(base, 0.0) * 0.0, 0.0)
-    k = rng.poisson(n_pits)
-    for _ in range(k):
+    h = np.maximum(cap - (X ** 2 + Y ** 2) / (2 * R), 0.0)
+    for _ in range(rng.poisson(n_pits)):
         cx, cy = rng.uniform(-n * pix / 2, n * pix / 2, 2)
         d2 = (X - cx) ** 2 + (Y - cy) ** 2
         h = np.where(d2 < pit_r ** 2, np.maximum(h - pit_d * (1 - d2 / pit_r ** 2), 0.0), h)
     return h.astype(np.float32)
+
+
+# The nine procedural indenters of the GelSight-scale workload, each as
+# (kind name, shape parameters, height map or None, tip offset above the
+# pose's z): sphere R 4 mm, cylinder R 2 mm (lying, 10 mm long), cone of
+# 60 degree apex angle, triangular prism (90 degree edge, 8 mm long), 5 x 5
+# dot grid, 0.5 x 10 mm line, wave of 2 mm wavelength, gradient-noise texture
+# and a pitted spherical cap.
+C1_DEPTHS = (0.2e-3, 0.5e-3, 1.0e-3, 1.5e-3)
+
+
+def c1_indenters():
+    pix = 0.1e-3
+    maps = {
+        "dots": hm_dots(n=96, pix=pix),
+        "line": hm_line(n=128, pix=pix),
+        "wave": hm_wave(n=96, pix=pix),
+        "perlin": hm_perlin(n=128, pix=pix, seed=1, octaves=3),
+        "worn": hm_worn_sphere(n=96, pix=pix, seed=2),
+    }
+    out = [("sphere", (4e-3,), None, 4e-3),
+           ("cylinder", (2e-3, 5e-3), None, 2e-3),
+           ("cone", (math.radians(30.0), 5e-3), None, 0.0),
+           ("prism", (math.radians(45.0), 4e-3, 3e-3), None, 0.0)]
+    for name in ("dots", "line", "wave", "perlin", "worn"):
+        hm = maps[name]
+        out.append(("heightmap:" + name, (2e-3,), hm, float(hm.max())))
+    return out
