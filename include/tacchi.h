@@ -189,6 +189,36 @@ tacchi_status tacchi_shade(const tacchi_render_params *rp, const float *H_dev, i
                            int hgt, double pixel_x_m, double pixel_y_m, double z_top_m,
                            float *rgb_dev, void *stream);
 
+/* Largest height map, in pixels, that tacchi_heightmap_static accepts. */
+#define TACCHI_STATIC_HEIGHTMAP_MAX_PIXELS (1 << 20)
+
+/* Height map without any memory allocation.  The paper has no counterpart:
+ * this entry point exists for callers that cannot allocate device memory
+ * while they run, such as a robot simulator's real-time control thread (where
+ * cudaMalloc can block and synchronise the device for an unbounded time) or a
+ * plugin whose host application owns the whole device-memory budget.
+ * It computes the same height map as tacchi_heightmap, but from particle
+ * arrays the caller passes in: u_dev (dev, float [3][n_particles], positions
+ * in cells from grid node 0, the layout of tacchi_get_state), surf_dev (dev,
+ * uint32 [n_surface], ids of the top-layer particles, flag bit 1), z0_dev
+ * (dev, float [n_surface], their rest z in cells), dx_m, origin_m (x and y of
+ * grid node 0, m), z_top_m (rest height of the top face).  window_m, w, hgt,
+ * fill_radius and out_dev (dev, float [hgt][w], metres) are as in
+ * tacchi_heightmap; the work is queued on stream.
+ * Scratch: a static device array of TACCHI_STATIC_HEIGHTMAP_MAX_PIXELS ints
+ * (4 MiB) that every GPU loading the library holds until the process exits.
+ * The first call on a device looks up that array's device address (with the
+ * device current); make that first call before any stream capture.  Every
+ * call clears and reuses the same array, so calls that overlap on the GPU
+ * (unordered streams or threads) race and corrupt each other's output.
+ * Errors: INVALID_ARG (null pointers, w * hgt above the maximum, bad window),
+ * CUDA. */
+tacchi_status tacchi_heightmap_static(const float *u_dev, int64_t n_particles,
+                                      const uint32_t *surf_dev, const float *z0_dev,
+                                      int n_surface, double dx_m, const double origin_m[2],
+                                      double z_top_m, int w, int hgt, const double window_m[4],
+                                      int fill_radius, float *out_dev, void *stream);
+
 /* Copy the particle state out (synchronises).  Each pointer may be NULL to
  * skip it; all are dev: u float [3][N] (cells), v float [3][N] (m/s),
  * C float [9][N] (1/s), Fm float [9][N] (F - I), flags uint8 [N] (bit 0 =

@@ -82,7 +82,10 @@ SIGNATURES = {
     "tacchi_status_string": (C.c_char_p, [C.c_int]),
     "tacchi_version": (C.c_int, []),
 }
-EXTRA_SIGNATURES = {}
+EXTRA_SIGNATURES = {
+    "tacchi_heightmap_static": (C.c_int, [_vp, C.c_int64, _vp, _vp, C.c_int, C.c_double, _dp,
+                                          C.c_double, C.c_int, C.c_int, _dp, C.c_int, _vp, _vp]),
+}
 
 
 def lib():
