@@ -651,7 +651,8 @@ tacchi_status tacchi_create(const tacchi_elastomer_desc *d, void *stream, tacchi
             cudaMemsetAsync(c->b.gv, 0, sizeof(float4) * Nn, st) == cudaSuccess &&
             cudaMemsetAsync(c->b.err, 0, sizeof(int), st) == cudaSuccess &&
             cudaMemsetAsync(c->b.movers, 0, sizeof(int), st) == cudaSuccess &&
-            launch_sort(c->b, c->blk, 1, st) == cudaSuccess && cudaStreamSynchronize(st) == cudaSuccess;
+            prepare_transfer(c->blk) == cudaSuccess && launch_sort(c->b, c->blk, 1, st) == cudaSuccess &&
+            cudaStreamSynchronize(st) == cudaSuccess;
   if (!up) {
     cudaGetLastError();
     return fail(TACCHI_ERR_CUDA);

@@ -42,7 +42,9 @@ __device__ __forceinline__ void polar_rotation_delta(const float H[9], float Y[9
     Y[e] = H[e];
     hmag = fmaxf(hmag, fabsf(H[e]));
   }
-  const float tol = 1e-7f * hmag;
+  // Newton converges quadratically: with |Y_{k+1} - Y_k| = e the next error is
+  // about e^2 / 2, below 1e-7 of the strain scale once e^2 <= 2e-7 |H|.
+  const float tol2 = 2e-7f * hmag;
 #pragma unroll 1
   for (int it = 0; it < 12; ++it) {
     float c[9];
@@ -64,7 +66,7 @@ __device__ __forceinline__ void polar_rotation_delta(const float H[9], float Y[9
       }
 #pragma unroll
     for (int e = 0; e < 9; ++e) Y[e] = Yn[e];
-    if (!(diff > tol)) break;
+    if (!(diff * diff > tol2)) break;
   }
 }
 
@@ -145,206 +147,424 @@ __global__ void __launch_bounds__(256) k_grid_update(Batch b, int substep, float
 }
 
 // ---------------------------------------------------------------------------
+// Transfer kernel.  One CTA per sort block of BX x BY x BZ cells with origin
+// B0.  A particle belongs to the block while its stencil base ("home cell")
+// stays within one cell of it, cells [B0-1, B0+B]; the sort runs only after
+// some particle leaves that range.  The CTA groups its particles by home cell
+// (counting sort in shared memory) and gives each non-empty cell to one
+// thread, which runs G2P for the cell's particles against the shared
+// velocity tile and accumulates their P2G contributions to the cell's 27
+// nodes in registers; the accumulators reach the shared grid tile once per
+// cell.  A particle whose stencil base changes during the substep scatters
+// on its own.
+template <int BX, int BY, int BZ>
+struct XferPlan {
+  static constexpr int THREADS = 128;
+  static constexpr int EX = BX + 2, EY = BY + 2, EZ = BZ + 2;       // home cells
+  static constexpr int NE = EX * EY * EZ;
+  static constexpr int VX = BX + 4, VY = BY + 4, VZ = BZ + 4;       // V tile, nodes [B0-1, B0+B+3)
+  static constexpr int VN = VX * VY * VZ;
+  static constexpr int TX = BX + 6, TY = BY + 6, TZ = BZ + 6;       // P2G tile, nodes [B0-2, B0+B+4)
+  static constexpr int TN = TX * TY * TZ;
+  static constexpr int MAXP = 16 * BX * BY * BZ;                    // particles grouped in smem
+  static constexpr int PER = (NE + 1 + THREADS - 1) / THREADS;      // scan entries per thread
+  // byte offsets in dynamic shared memory
+  static constexpr size_t OFF_TILE = 0;                             // float [4][TN]; first u32 key[MAXP]
+  static constexpr size_t OFF_V = OFF_TILE + 16 * (size_t)TN;       // float4 [VN]
+  static constexpr size_t OFF_LIST = OFF_V + 16 * (size_t)VN;       // u32 [MAXP] particles by cell
+  static constexpr size_t OFF_CNT = OFF_LIST + 4 * (size_t)MAXP;    // u32 [NE] count, then start
+  static constexpr size_t OFF_START = OFF_CNT + 4 * (size_t)NE;     // u32 [NE + 1]
+  static constexpr size_t OFF_CELLS = OFF_START + 4 * (size_t)(NE + 1);  // u16 [NE] non-empty cells
+  static constexpr size_t BYTES = OFF_CELLS + 2 * (size_t)NE + 16;
+  static_assert(4 * TN >= MAXP, "the P2G tile doubles as the key scratch");
+};
+
+// Exclusive scan over n (<= THREADS * PER) entries of `a` into `out` (out[n] =
+// total); also compacts the indices with a[c] > 0 into `cells`, returning
+// their number.  All threads of the CTA call it.
+template <int THREADS, int PER>
+__device__ __forceinline__ uint32_t block_scan_compact(const uint32_t *a, uint32_t *out, uint16_t *cells,
+                                                       int n, uint32_t *warp_buf) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NWARP = THREADS / 32;
+  uint32_t v[PER], nz[PER];
+  uint32_t sum = 0, nzs = 0;
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int c = tid * PER + q;
+    v[q] = c < n ? a[c] : 0u;
+    nz[q] = v[q] > 0 ? 1u : 0u;
+    sum += v[q];
+    nzs += nz[q];
+  }
+  // pack both running sums: counts < 2^20 per CTA, non-empty cells < 2^12
+  uint32_t x = sum | (nzs << 20);
+  const uint32_t mine = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_buf[warp] = x;
+  __syncthreads();
+  uint32_t wpre = 0;
+  for (int w = 0; w < warp; ++w) wpre += warp_buf[w];
+  uint32_t run = x - mine + wpre;
+  uint32_t rs = run & 0xFFFFFu, rn = run >> 20;
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int c = tid * PER + q;
+    if (c < n) {
+      out[c] = rs;
+      if (nz[q]) cells[rn] = (uint16_t)c;
+    }
+    rs += v[q];
+    rn += nz[q];
+  }
+  uint32_t tot = 0;
+  for (int w = 0; w < NWARP; ++w) tot += warp_buf[w];
+  if (tid == 0) out[n] = tot & 0xFFFFFu;
+  __syncthreads();
+  return tot >> 20;
+}
+
+// P2G of one particle straight into the shared tile (particles that change
+// cell during the substep, and the capacity fallback).
+__device__ __forceinline__ void scatter_particle(float *tile, int TN, int TX, int TY, int lx, int ly, int lz,
+                                                 const float f[3], const float mv[3], const float A[9]) {
+  float wx[3], wy[3], wz[3], dpx[3], dpy[3], dpz[3];
+  bspline3(f[0], wx, dpx);
+  bspline3(f[1], wy, dpy);
+  bspline3(f[2], wz, dpz);
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const float wjk = wy[j] * wz[k];
+      float *t = tile + ((lz + k) * TY + (ly + j)) * TX + lx;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const float w = wx[i] * wjk;
+        atomicAdd(t + i, w);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+          atomicAdd(t + (a + 1) * TN + i,
+                    w * (mv[a] + A[a * 3 + 0] * dpx[i] + A[a * 3 + 1] * dpy[j] + A[a * 3 + 2] * dpz[k]));
+      }
+    }
+}
+
+// Resident transfer CTAs per SM the register allocation is bounded for.
+#ifndef TACCHI_XFER_MIN_BLOCKS
+#define TACCHI_XFER_MIN_BLOCKS 2
+#endif
+
 template <int BX, int BY, int BZ, int MODE>
-__global__ void __launch_bounds__(256) k_transfer(Batch b, float dt) {
+__global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer(Batch b, float dt) {
+  using P = XferPlan<BX, BY, BZ>;
   constexpr bool DO_G2P = (MODE & XFER_G2P) != 0;
   constexpr bool DO_P2G = (MODE & XFER_P2G) != 0;
-  constexpr int TX = BX + 4, TY = BY + 4, TZ = BZ + 4, TN = TX * TY * TZ;
-  extern __shared__ float tile[];  // [4][TN] when DO_P2G
-  __shared__ int s_moved;
+  constexpr int TX = P::TX, TY = P::TY, TN = P::TN, VX = P::VX, VY = P::VY;
+  extern __shared__ __align__(16) unsigned char smem[];
+  float *tile = reinterpret_cast<float *>(smem + P::OFF_TILE);
+  uint32_t *s_key = reinterpret_cast<uint32_t *>(smem + P::OFF_TILE);
+  float4 *vt = reinterpret_cast<float4 *>(smem + P::OFF_V);
+  uint32_t *s_list = reinterpret_cast<uint32_t *>(smem + P::OFF_LIST);
+  uint32_t *s_cnt = reinterpret_cast<uint32_t *>(smem + P::OFF_CNT);
+  uint32_t *s_start = reinterpret_cast<uint32_t *>(smem + P::OFF_START);
+  uint16_t *s_cells = reinterpret_cast<uint16_t *>(smem + P::OFF_CELLS);
+  __shared__ uint32_t s_warp[P::THREADS / 32];
+  __shared__ int s_moved, s_overflow;
 
   const long long gblk = blockIdx.x;
   const uint32_t start = b.bstart[gblk], end = b.bstart[gblk + 1];
   if (start == end) return;
+  const uint32_t n = end - start;
   const int ii = b.block_inst[gblk];
   const Instance &I = b.inst[ii];
   const int G0 = I.G[0], G1 = I.G[1], G2 = I.G[2];
   const long long lb = gblk - I.block_off;
   const int nb0 = I.nb[0], nb1 = I.nb[1];
-  const int cbx = (int)(lb % nb0), cby = (int)((lb / nb0) % nb1), cbz = (int)(lb / ((long long)nb0 * nb1));
-  const int T0x = cbx * BX - 1, T0y = cby * BY - 1, T0z = cbz * BZ - 1;
+  const int B0x = (int)(lb % nb0) * BX, B0y = (int)((lb / nb0) % nb1) * BY,
+            B0z = (int)(lb / ((long long)nb0 * nb1)) * BZ;
   const long long Ntot = b.Ntot;
   const float inv_dx = I.inv_dx, dx = I.dx, m = I.m;
+  const float c4 = 4.0f * dt * inv_dx;
+  const float ks = 4.0f * dt * I.V0 * inv_dx;
+  const int tid = threadIdx.x;
 
+  // ---- group the block's particles by home cell
+  for (int c = tid; c < P::NE; c += P::THREADS) s_cnt[c] = 0;
+  if (tid == 0) {
+    s_moved = 0;
+    s_overflow = n > (uint32_t)P::MAXP;
+  }
+  __syncthreads();
+  if (n <= (uint32_t)P::MAXP) {
+    for (uint32_t l = tid; l < n; l += P::THREADS) {
+      const uint32_t p = b.idx[start + l];
+      const int ex = (int)floorf(b.u[p] - 0.5f) - (B0x - 1);
+      const int ey = (int)floorf(b.u[Ntot + p] - 0.5f) - (B0y - 1);
+      const int ez = (int)floorf(b.u[2 * Ntot + p] - 0.5f) - (B0z - 1);
+      uint32_t key = 0xFFFFFFFFu;
+      if (ex >= 0 && ey >= 0 && ez >= 0 && ex < P::EX && ey < P::EY && ez < P::EZ) {
+        const uint32_t c = (uint32_t)((ez * P::EY + ey) * P::EX + ex);
+        key = (atomicAdd(s_cnt + c, 1u) << 12) | c;  // rank, cell (< 4096)
+      } else {
+        s_overflow = 1;  // not at home: the sort invariant is broken
+      }
+      s_key[l] = key;
+    }
+  }
+  __syncthreads();
+  const bool grouped = !s_overflow;
+  uint32_t ncells = 0;
+  if (grouped) {
+    ncells = block_scan_compact<P::THREADS, P::PER>(s_cnt, s_start, s_cells, P::NE, s_warp);
+    for (uint32_t l = tid; l < n; l += P::THREADS) {
+      const uint32_t key = s_key[l];
+      s_list[s_start[key & 0xFFFu] + (key >> 12)] = b.idx[start + l];
+    }
+  }
+  __syncthreads();
   if (DO_P2G)
-    for (int t = threadIdx.x; t < 4 * TN; t += blockDim.x) tile[t] = 0.f;
-  if (threadIdx.x == 0) s_moved = 0;
+    for (int t = tid; t < 4 * TN; t += P::THREADS) tile[t] = 0.f;
+  if (DO_G2P) {  // grid velocities of nodes [B0-1, B0+B+3) into the V tile
+    const float4 *gv = b.gv + I.node_off;
+    for (int t = tid; t < P::VN; t += P::THREADS) {
+      const int x = B0x - 1 + t % VX, y = B0y - 1 + (t / VX) % VY, z = B0z - 1 + t / (VX * VY);
+      float4 V = make_float4(0.f, 0.f, 0.f, 0.f);
+      if (x >= 0 && y >= 0 && z >= 0 && x < G0 && y < G1 && z < G2)
+        V = __ldg(gv + ((long long)z * G1 + y) * G0 + x);
+      vt[t] = V;
+    }
+  }
   __syncthreads();
 
-  for (uint32_t it = start + threadIdx.x; it < end; it += blockDim.x) {
-    const uint32_t p = b.idx[it];
-    float u[3] = {b.u[p], b.u[Ntot + p], b.u[2 * Ntot + p]};
-    float H[9];
-#pragma unroll
-    for (int e = 0; e < 9; ++e) H[e] = b.Fm[e * Ntot + p];
-    float v[3], Bm[9];  // Bm = sum_i w V (i - f)^T (cells); C = 4/dx Bm
-    int err = 0;
-
-    if (DO_G2P) {
-      int bs[3];
-      float f[3];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        bs[a] = (int)floorf(u[a] - 0.5f);
-        f[a] = u[a] - (float)bs[a];
-      }
-      if (bs[0] < 0 || bs[1] < 0 || bs[2] < 0 || bs[0] > G0 - 3 || bs[1] > G1 - 3 || bs[2] > G2 - 3) {
-        err |= ERRBIT_OUT_OF_GRID;  // keep memory access inside the grid
-        bs[0] = clampi(bs[0], 0, G0 - 3);
-        bs[1] = clampi(bs[1], 0, G1 - 3);
-        bs[2] = clampi(bs[2], 0, G2 - 3);
-        f[0] = f[1] = f[2] = 1.0f;
-      }
-      float wx[3], wy[3], wz[3], dpx[3], dpy[3], dpz[3];
-      bspline3(f[0], wx, dpx);
-      bspline3(f[1], wy, dpy);
-      bspline3(f[2], wz, dpz);
-      float wdx[3];
-#pragma unroll
-      for (int i = 0; i < 3; ++i) wdx[i] = wx[i] * dpx[i];
-#pragma unroll
-      for (int e = 0; e < 9; ++e) Bm[e] = 0.f;
-      v[0] = v[1] = v[2] = 0.f;
-      const float4 *gv = b.gv + I.node_off;
-#pragma unroll
-      for (int k = 0; k < 3; ++k)
-#pragma unroll
-        for (int j = 0; j < 3; ++j) {
-          const float4 *row = gv + ((long long)(bs[2] + k) * G1 + (bs[1] + j)) * G0 + bs[0];
-          const float4 V0 = __ldg(row), V1 = __ldg(row + 1), V2 = __ldg(row + 2);
-          // row sums over i: s = sum w_i V_i, t = sum w_i (i - f_x) V_i
-          const float s0 = wx[0] * V0.x + wx[1] * V1.x + wx[2] * V2.x;
-          const float s1 = wx[0] * V0.y + wx[1] * V1.y + wx[2] * V2.y;
-          const float s2 = wx[0] * V0.z + wx[1] * V1.z + wx[2] * V2.z;
-          const float t0 = wdx[0] * V0.x + wdx[1] * V1.x + wdx[2] * V2.x;
-          const float t1 = wdx[0] * V0.y + wdx[1] * V1.y + wdx[2] * V2.y;
-          const float t2 = wdx[0] * V0.z + wdx[1] * V1.z + wdx[2] * V2.z;
-          const float wjk = wy[j] * wz[k];
-          const float wjy = wjk * dpy[j], wjz = wjk * dpz[k];
-          v[0] += wjk * s0; v[1] += wjk * s1; v[2] += wjk * s2;               // Eq. 7
-          Bm[0] += wjk * t0; Bm[3] += wjk * t1; Bm[6] += wjk * t2;            // Eq. 8
-          Bm[1] += wjy * s0; Bm[4] += wjy * s1; Bm[7] += wjy * s2;
-          Bm[2] += wjz * s0; Bm[5] += wjz * s1; Bm[8] += wjz * s2;
-        }
-      // Eq. 9: F <- (I + dt C) F, i.e. H <- H + dt C (I + H), C = 4/dx Bm
-      const float c4 = 4.0f * dt * inv_dx;
-      float Hn[9];
-#pragma unroll
-      for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int q = 0; q < 3; ++q) {
-          const float M0 = (q == 0 ? 1.f : 0.f) + H[0 * 3 + q];
-          const float M1 = (q == 1 ? 1.f : 0.f) + H[1 * 3 + q];
-          const float M2 = (q == 2 ? 1.f : 0.f) + H[2 * 3 + q];
-          Hn[r * 3 + q] = H[r * 3 + q] + c4 * (Bm[r * 3 + 0] * M0 + Bm[r * 3 + 1] * M1 + Bm[r * 3 + 2] * M2);
-        }
-#pragma unroll
-      for (int e = 0; e < 9; ++e) H[e] = Hn[e];
-      if (I.fix_base && (b.flags[p] & 1)) v[0] = v[1] = v[2] = 0.f;  // Eq. 10
-#pragma unroll
-      for (int a = 0; a < 3; ++a) u[a] = u[a] + dt * inv_dx * v[a];  // Eq. 11
-      // the particle's new stencil must stay clear of the padding band
-      int nbs[3];
-#pragma unroll
-      for (int a = 0; a < 3; ++a) nbs[a] = (int)floorf(u[a] - 0.5f);
-      if (!(isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]))) err |= ERRBIT_NUMERICAL;
-      if (nbs[0] < 2 || nbs[1] < 2 || nbs[2] < 2 || nbs[0] > G0 - 5 || nbs[1] > G1 - 5 || nbs[2] > G2 - 5)
-        err |= ERRBIT_OUT_OF_GRID;
-      if (nbs[0] < T0x + 1 || nbs[0] > T0x + BX || nbs[1] < T0y + 1 || nbs[1] > T0y + BY ||
-          nbs[2] < T0z + 1 || nbs[2] > T0z + BZ)
-        s_moved = 1;  // left its sort block: re-sort after this transfer
-      b.u[p] = u[0];
-      b.u[Ntot + p] = u[1];
-      b.u[2 * Ntot + p] = u[2];
-#pragma unroll
-      for (int e = 0; e < 9; ++e) b.Fm[e * Ntot + p] = H[e];
-      if (!DO_P2G) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) b.v[a * Ntot + p] = v[a];
-#pragma unroll
-        for (int e = 0; e < 9; ++e) b.C[e * Ntot + p] = 4.0f * inv_dx * Bm[e];
-      }
+  // ---- one cell per thread (or, without grouping, one particle per thread)
+  const uint32_t nwork = grouped ? ncells : n;
+  for (uint32_t wk = tid; wk < nwork; wk += P::THREADS) {
+    uint32_t q0, q1;
+    int cx, cy, cz;
+    if (grouped) {
+      const uint32_t c = s_cells[wk];
+      q0 = s_start[c];
+      q1 = s_start[c + 1];
+      cx = (int)(c % P::EX);
+      cy = (int)((c / P::EX) % P::EY);
+      cz = (int)(c / (P::EX * P::EY));
     } else {
-      // first transfer of a step: v and C come from the stored state
-#pragma unroll
-      for (int a = 0; a < 3; ++a) v[a] = b.v[a * Ntot + p];
-#pragma unroll
-      for (int e = 0; e < 9; ++e) Bm[e] = 0.25f * dx * b.C[e * Ntot + p];
+      q0 = wk;
+      q1 = wk + 1;
+      cx = cy = cz = 0;
     }
-
-    if (DO_P2G) {
-      // Eqs. 2-5 with S_p = tau and the affine term of Eq. 4 carrying m_p:
-      // MG_i += w (m v + A (X_i - x)),  A (X_i - x) = Abar (i - f),
-      // Abar = dx (m C - dt V0 (4/dx^2) tau) = 4 m Bm - (4 dt V0 / dx) tau.
-      float tau[9];
-      const float Jm1 = kirchhoff_stress(H, I.mu, I.la, tau);
-      if (!(1.0f + Jm1 > 0.f)) err |= ERRBIT_NUMERICAL;
-      const float ks = 4.0f * dt * I.V0 * inv_dx;
-      float A[9];
+    // accumulators of the cell's 27 nodes: sum of w (mass / m) and of
+    // w (m v + A (X_i - x)) per axis
+    float accw[27], acc0[27], acc1[27], acc2[27];
+    if (DO_P2G && grouped) {
 #pragma unroll
-      for (int e = 0; e < 9; ++e) A[e] = 4.0f * m * Bm[e] - ks * tau[e];
-      int bs[3];
-      float f[3];
+      for (int e = 0; e < 27; ++e) accw[e] = acc0[e] = acc1[e] = acc2[e] = 0.f;
+    }
+    // the state of particle q+1 is loaded while particle q computes
+    uint32_t pn = grouped ? s_list[q0] : b.idx[start + q0];
+    float un[3] = {b.u[pn], b.u[Ntot + pn], b.u[2 * Ntot + pn]};
+    float Hnx[9];
 #pragma unroll
-      for (int a = 0; a < 3; ++a) {
-        bs[a] = (int)floorf(u[a] - 0.5f);
-        f[a] = u[a] - (float)bs[a];
+    for (int e = 0; e < 9; ++e) Hnx[e] = b.Fm[e * Ntot + pn];
+    for (uint32_t q = q0; q < q1; ++q) {
+      const uint32_t p = pn;
+      float u[3] = {un[0], un[1], un[2]};
+      float H[9];
+#pragma unroll
+      for (int e = 0; e < 9; ++e) H[e] = Hnx[e];
+      if (q + 1 < q1) {
+        pn = grouped ? s_list[q + 1] : b.idx[start + q + 1];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) un[a] = b.u[a * Ntot + pn];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) Hnx[e] = b.Fm[e * Ntot + pn];
       }
-      const int lx = bs[0] - T0x, ly = bs[1] - T0y, lz = bs[2] - T0z;
-      if (lx < 0 || ly < 0 || lz < 0 || lx > TX - 3 || ly > TY - 3 || lz > TZ - 3 || (err & ERRBIT_NUMERICAL)) {
-        err |= ERRBIT_CFL;  // moved a cell or more in one substep: not scattered
-      } else {
+      int bs[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) bs[a] = (int)floorf(u[a] - 0.5f);
+      float v[3], Bm[9];  // Bm = sum_i w V (i - f)^T (cells); C = 4/dx Bm
+      int err = 0;
+      if (DO_G2P) {
+        float f[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) f[a] = u[a] - (float)bs[a];
         float wx[3], wy[3], wz[3], dpx[3], dpy[3], dpz[3];
         bspline3(f[0], wx, dpx);
         bspline3(f[1], wy, dpy);
         bspline3(f[2], wz, dpz);
-        float ax[3][3], ay[3][3], az[3][3];
+        float wdx[3];
 #pragma unroll
-        for (int i = 0; i < 3; ++i)
+        for (int i = 0; i < 3; ++i) wdx[i] = wx[i] * dpx[i];
 #pragma unroll
-          for (int a = 0; a < 3; ++a) {
-            ax[i][a] = A[a * 3 + 0] * dpx[i];
-            ay[i][a] = A[a * 3 + 1] * dpy[i];
-            az[i][a] = A[a * 3 + 2] * dpz[i];
-          }
-        const float mv0 = m * v[0], mv1 = m * v[1], mv2 = m * v[2];
-        float wxm[3];
-#pragma unroll
-        for (int i = 0; i < 3; ++i) wxm[i] = wx[i] * m;
+        for (int e = 0; e < 9; ++e) Bm[e] = 0.f;
+        v[0] = v[1] = v[2] = 0.f;
+        // home cells lie inside the V tile; clamp only as a guard
+        const int vx = clampi(bs[0] - (B0x - 1), 0, VX - 3), vy = clampi(bs[1] - (B0y - 1), 0, VY - 3),
+                  vz = clampi(bs[2] - (B0z - 1), 0, P::VZ - 3);
+        if (vx != bs[0] - (B0x - 1) || vy != bs[1] - (B0y - 1) || vz != bs[2] - (B0z - 1)) err |= ERRBIT_CFL;
 #pragma unroll
         for (int k = 0; k < 3; ++k)
 #pragma unroll
           for (int j = 0; j < 3; ++j) {
+            const float4 *row = vt + ((vz + k) * VY + (vy + j)) * VX + vx;
+            const float4 V0 = row[0], V1 = row[1], V2 = row[2];
+            // row sums over i: s = sum w_i V_i, t = sum w_i (i - f_x) V_i
+            const float s0 = wx[0] * V0.x + wx[1] * V1.x + wx[2] * V2.x;
+            const float s1 = wx[0] * V0.y + wx[1] * V1.y + wx[2] * V2.y;
+            const float s2 = wx[0] * V0.z + wx[1] * V1.z + wx[2] * V2.z;
+            const float t0 = wdx[0] * V0.x + wdx[1] * V1.x + wdx[2] * V2.x;
+            const float t1 = wdx[0] * V0.y + wdx[1] * V1.y + wdx[2] * V2.y;
+            const float t2 = wdx[0] * V0.z + wdx[1] * V1.z + wdx[2] * V2.z;
             const float wjk = wy[j] * wz[k];
-            const float q0 = mv0 + ay[j][0] + az[k][0];
-            const float q1 = mv1 + ay[j][1] + az[k][1];
-            const float q2 = mv2 + ay[j][2] + az[k][2];
-            float *t = tile + ((lz + k) * TY + (ly + j)) * TX + lx;
-#pragma unroll
-            for (int i = 0; i < 3; ++i) {
-              const float w = wx[i] * wjk;
-              atomicAdd(t + i, wxm[i] * wjk);                       // Eq. 2
-              atomicAdd(t + TN + i, w * (q0 + ax[i][0]));           // Eqs. 3-5
-              atomicAdd(t + 2 * TN + i, w * (q1 + ax[i][1]));
-              atomicAdd(t + 3 * TN + i, w * (q2 + ax[i][2]));
-            }
+            const float wjy = wjk * dpy[j], wjz = wjk * dpz[k];
+            v[0] += wjk * s0; v[1] += wjk * s1; v[2] += wjk * s2;               // Eq. 7
+            Bm[0] += wjk * t0; Bm[3] += wjk * t1; Bm[6] += wjk * t2;            // Eq. 8
+            Bm[1] += wjy * s0; Bm[4] += wjy * s1; Bm[7] += wjy * s2;
+            Bm[2] += wjz * s0; Bm[5] += wjz * s1; Bm[8] += wjz * s2;
           }
+        // Eq. 9: F <- (I + dt C) F, i.e. H <- H + dt C (I + H), C = 4/dx Bm
+        float Hn[9];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+          for (int c = 0; c < 3; ++c) {
+            const float M0 = (c == 0 ? 1.f : 0.f) + H[0 * 3 + c];
+            const float M1 = (c == 1 ? 1.f : 0.f) + H[1 * 3 + c];
+            const float M2 = (c == 2 ? 1.f : 0.f) + H[2 * 3 + c];
+            Hn[r * 3 + c] = H[r * 3 + c] + c4 * (Bm[r * 3 + 0] * M0 + Bm[r * 3 + 1] * M1 + Bm[r * 3 + 2] * M2);
+          }
+#pragma unroll
+        for (int e = 0; e < 9; ++e) H[e] = Hn[e];
+        if (I.fix_base && (b.flags[p] & 1)) v[0] = v[1] = v[2] = 0.f;  // Eq. 10
+#pragma unroll
+        for (int a = 0; a < 3; ++a) u[a] = u[a] + dt * inv_dx * v[a];  // Eq. 11
+        if (!(isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]))) err |= ERRBIT_NUMERICAL;
+        b.u[p] = u[0];
+        b.u[Ntot + p] = u[1];
+        b.u[2 * Ntot + p] = u[2];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) b.Fm[e * Ntot + p] = H[e];
+        if (!DO_P2G) {
+#pragma unroll
+          for (int a = 0; a < 3; ++a) b.v[a * Ntot + p] = v[a];
+#pragma unroll
+          for (int e = 0; e < 9; ++e) b.C[e * Ntot + p] = 4.0f * inv_dx * Bm[e];
+        }
+      } else {
+        // first transfer of a step: v and C come from the stored state
+#pragma unroll
+        for (int a = 0; a < 3; ++a) v[a] = b.v[a * Ntot + p];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) Bm[e] = 0.25f * dx * b.C[e * Ntot + p];
       }
+      // the particle's (new) stencil must stay clear of the padding band
+      int nbs[3];
+#pragma unroll
+      for (int a = 0; a < 3; ++a) nbs[a] = (int)floorf(u[a] - 0.5f);
+      if (nbs[0] < 2 || nbs[1] < 2 || nbs[2] < 2 || nbs[0] > G0 - 5 || nbs[1] > G1 - 5 || nbs[2] > G2 - 5)
+        err |= ERRBIT_OUT_OF_GRID;
+      if (DO_G2P && (nbs[0] < B0x - 1 || nbs[0] > B0x + BX || nbs[1] < B0y - 1 || nbs[1] > B0y + BY ||
+                     nbs[2] < B0z - 1 || nbs[2] > B0z + BZ))
+        s_moved = 1;  // left its home cells: re-sort after this transfer
+
+      if (DO_P2G) {
+        // Eqs. 2-5 with S_p = tau and the affine term of Eq. 4 carrying m_p:
+        // MG_i += w (m v + A (X_i - x)),  A (X_i - x) = Abar (i - f),
+        // Abar = dx (m C - dt V0 (4/dx^2) tau) = 4 m Bm - (4 dt V0 / dx) tau.
+        float tau[9];
+        const float Jm1 = kirchhoff_stress(H, I.mu, I.la, tau);
+        if (!(1.0f + Jm1 > 0.f)) err |= ERRBIT_NUMERICAL;
+        float A[9];
+#pragma unroll
+        for (int e = 0; e < 9; ++e) A[e] = 4.0f * m * Bm[e] - ks * tau[e];
+        const float mv[3] = {m * v[0], m * v[1], m * v[2]};
+        float f[3];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) f[a] = u[a] - (float)nbs[a];
+        const bool same_cell = grouped && nbs[0] - (B0x - 1) == cx && nbs[1] - (B0y - 1) == cy &&
+                               nbs[2] - (B0z - 1) == cz;
+        if (err & ERRBIT_NUMERICAL) {
+          err |= ERRBIT_CFL;  // not scattered
+        } else if (same_cell) {
+          float wx[3], wy[3], wz[3], dpx[3], dpy[3], dpz[3];
+          bspline3(f[0], wx, dpx);
+          bspline3(f[1], wy, dpy);
+          bspline3(f[2], wz, dpz);
+          float ax[3][3], ay[3][3], az[3][3];
+#pragma unroll
+          for (int i = 0; i < 3; ++i)
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+              ax[i][a] = A[a * 3 + 0] * dpx[i];
+              ay[i][a] = A[a * 3 + 1] * dpy[i];
+              az[i][a] = A[a * 3 + 2] * dpz[i];
+            }
+#pragma unroll
+          for (int k = 0; k < 3; ++k)
+#pragma unroll
+            for (int j = 0; j < 3; ++j) {
+              const float wjk = wy[j] * wz[k];
+              const float r0 = mv[0] + ay[j][0] + az[k][0];
+              const float r1 = mv[1] + ay[j][1] + az[k][1];
+              const float r2 = mv[2] + ay[j][2] + az[k][2];
+#pragma unroll
+              for (int i = 0; i < 3; ++i) {
+                const int e = (k * 3 + j) * 3 + i;
+                const float w = wx[i] * wjk;
+                accw[e] += w;                        // Eq. 2 (/ m)
+                acc0[e] += w * (r0 + ax[i][0]);      // Eqs. 3-5
+                acc1[e] += w * (r1 + ax[i][1]);
+                acc2[e] += w * (r2 + ax[i][2]);
+              }
+            }
+        } else {
+          const int lx = nbs[0] - (B0x - 2), ly = nbs[1] - (B0y - 2), lz = nbs[2] - (B0z - 2);
+          if (lx < 0 || ly < 0 || lz < 0 || lx > TX - 3 || ly > TY - 3 || lz > P::TZ - 3) {
+            err |= ERRBIT_CFL;  // moved a cell or more in one substep: not scattered
+          } else {
+            const float wm[3] = {mv[0], mv[1], mv[2]};
+            scatter_particle(tile, TN, TX, TY, lx, ly, lz, f, wm, A);
+          }
+        }
+      }
+      if (err) atomicOr(b.err, err);
     }
-    if (err) atomicOr(b.err, err);
+    if (DO_P2G && grouped && q1 > q0) {
+      // the cell's base node in the P2G tile: home cell (cx, cy, cz) sits at
+      // node B0 - 1 + c, i.e. tile index c + 1
+      float *t = tile + ((cz + 1) * TY + (cy + 1)) * TX + (cx + 1);
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int j = 0; j < 3; ++j)
+#pragma unroll
+          for (int i = 0; i < 3; ++i) {
+            const int e = (k * 3 + j) * 3 + i;
+            float *tt = t + (k * TY + j) * TX + i;
+            atomicAdd(tt, accw[e]);
+            atomicAdd(tt + TN, acc0[e]);
+            atomicAdd(tt + 2 * TN, acc1[e]);
+            atomicAdd(tt + 3 * TN, acc2[e]);
+          }
+    }
   }
   __syncthreads();
-  if (DO_G2P && threadIdx.x == 0 && s_moved) *b.movers = 1;
+  if (DO_G2P && tid == 0 && s_moved) *b.movers = 1;
   if (DO_P2G) {
     float4 *gmm = b.gmm + I.node_off;
-    for (int t = threadIdx.x; t < TN; t += blockDim.x) {
-      const float mass = tile[t];
-      if (mass == 0.f) continue;
+    for (int t = tid; t < TN; t += P::THREADS) {
+      const float wsum = tile[t];
+      if (wsum == 0.f) continue;
       const int tx = t % TX, ty = (t / TX) % TY, tz = t / (TX * TY);
-      const int gx = T0x + tx, gy = T0y + ty, gz = T0z + tz;
+      const int gx = B0x - 2 + tx, gy = B0y - 2 + ty, gz = B0z - 2 + tz;
       if (gx < 0 || gy < 0 || gz < 0 || gx >= G0 || gy >= G1 || gz >= G2) continue;
       atomicAdd(gmm + ((long long)gz * G1 + gy) * G0 + gx,
-                make_float4(mass, tile[TN + t], tile[2 * TN + t], tile[3 * TN + t]));
+                make_float4(m * wsum, tile[TN + t], tile[2 * TN + t], tile[3 * TN + t]));
     }
   }
 }
@@ -442,23 +662,45 @@ cudaError_t launch_grid_update(const Batch &b, int substep, float dt, int clear,
 
 template <int BX, int BY, int BZ>
 static cudaError_t launch_transfer_t(const Batch &b, int mode, float dt, cudaStream_t st) {
-  constexpr int TN = (BX + 4) * (BY + 4) * (BZ + 4);
-  const size_t smem = (mode & XFER_P2G) ? 4 * TN * sizeof(float) : 0;
+  const size_t smem = XferPlan<BX, BY, BZ>::BYTES;
   const unsigned grid = (unsigned)b.Nblk;
   switch (mode) {
     case XFER_P2G:
-      k_transfer<BX, BY, BZ, XFER_P2G><<<grid, 256, smem, st>>>(b, dt);
+      k_transfer<BX, BY, BZ, XFER_P2G><<<grid, XferPlan<BX, BY, BZ>::THREADS, smem, st>>>(b, dt);
       break;
     case XFER_G2P:
-      k_transfer<BX, BY, BZ, XFER_G2P><<<grid, 256, smem, st>>>(b, dt);
+      k_transfer<BX, BY, BZ, XFER_G2P><<<grid, XferPlan<BX, BY, BZ>::THREADS, smem, st>>>(b, dt);
       break;
     case XFER_FUSED:
-      k_transfer<BX, BY, BZ, XFER_FUSED><<<grid, 256, smem, st>>>(b, dt);
+      k_transfer<BX, BY, BZ, XFER_FUSED><<<grid, XferPlan<BX, BY, BZ>::THREADS, smem, st>>>(b, dt);
       break;
     default:
       return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
+}
+
+template <int BX, int BY, int BZ>
+static cudaError_t prepare_t() {
+  const int smem = (int)XferPlan<BX, BY, BZ>::BYTES;
+  cudaError_t e = cudaFuncSetAttribute(k_transfer<BX, BY, BZ, XFER_P2G>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_transfer<BX, BY, BZ, XFER_G2P>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_transfer<BX, BY, BZ, XFER_FUSED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             smem);
+  return e;
+}
+
+// Opt the transfer kernels of a block shape into their shared-memory size;
+// called once per context before any launch or capture.
+cudaError_t prepare_transfer(SortBlock blk) {
+  if (blk.x == 8 && blk.y == 8 && blk.z == 4) return prepare_t<8, 8, 4>();
+  if (blk.x == 4 && blk.y == 4 && blk.z == 4) return prepare_t<4, 4, 4>();
+  if (blk.x == 8 && blk.y == 8 && blk.z == 8) return prepare_t<8, 8, 8>();
+  if (blk.x == 16 && blk.y == 8 && blk.z == 4) return prepare_t<16, 8, 4>();
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_transfer(const Batch &b, SortBlock blk, int mode, float dt, cudaStream_t st) {

@@ -147,6 +147,7 @@ struct SortBlock { int x, y, z; };
 cudaError_t launch_grid_update(const Batch &b, int substep, float dt, int clear, cudaStream_t st);
 cudaError_t launch_transfer(const Batch &b, SortBlock blk, int mode, float dt, cudaStream_t st);
 cudaError_t launch_sort(const Batch &b, SortBlock blk, int force, cudaStream_t st);
+cudaError_t prepare_transfer(SortBlock blk);
 
 enum : int { XFER_P2G = 1, XFER_G2P = 2, XFER_FUSED = 3 };
 
