@@ -175,12 +175,12 @@ def run_ours(args, rank, world, local_rank):
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
 
+    sim.set_profiling(True)  # profiled step graphs are built during warm-up
     for s in range(args.warmup):
         one_step(s)
 
     # device-resident timed region
     clocks = ClockSampler(local_rank)
-    sim.set_profiling(True)
     sim.profile(reset=True)
     barrier()
     clocks.start()
@@ -265,6 +265,80 @@ def run_ours(args, rank, world, local_rank):
     return result, sim
 
 
+def run_batch_bench(args, rank, world, local_rank):
+    """256 uneven sensors stepped together (one graph launch per chunk); even
+    steps press every indenter down to its depth, odd steps lift it back;
+    each step ends with a 64 x 64 height map per sensor."""
+    import torch
+    import paper_2301_08343_gb300 as T
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    specs = W.c2_instances(args.instances, seed_base=1000 + 100000 * rank)
+    substeps = args.substeps or 200
+    dt = W.C2_DT
+    bt = T.TacchiBatch([b for b, _ in specs])
+    K = T.IndenterKind
+    kinds = {"sphere": K.SPHERE, "cylinder": K.CYLINDER, "cone": K.CONE, "prism": K.PRISM}
+    for i, (b, ind) in enumerate(specs):
+        bt.set_indenter(i, kinds[ind["kind"]], ind["params"], ind["pose"], (0, 0, 0, 0, 0, 0))
+    tuned = None
+    if not args.no_autotune:
+        for i, (b, ind) in enumerate(specs):
+            bt.set_indenter(i, vel=(0, 0, -ind["depth"] / (substeps * dt), 0, 0, 0))
+        tuned = bt.autotune(min(32, substeps), dt)
+    hm = torch.empty((64, 64), device=dev)
+
+    def one_step(s):
+        sign = -1.0 if s % 2 == 0 else 1.0
+        for i, (b, ind) in enumerate(specs):
+            bt.set_indenter(i, vel=(0, 0, sign * ind["depth"] / (substeps * dt), 0, 0, 0))
+        bt.step(substeps, dt)
+        for i, (b, ind) in enumerate(specs):
+            bt.heightmap(i, 64, 64, W.top_window(b), out=hm)
+        st = bt.status()
+        if st != 0:
+            raise RuntimeError(f"batched step {s} failed with status {st}")
+
+    bt.set_profiling(True)  # profiled step graphs are built during warm-up
+    for s in range(args.warmup):
+        one_step(s)
+    clocks = ClockSampler(local_rank)
+    bt.profile(reset=True)
+    torch.cuda.synchronize(dev)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for s in range(args.steps):
+        one_step(args.warmup + s)
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clk = clocks.stop()
+    bt.set_profiling(False)
+    ms = e0.elapsed_time(e1)
+    prof = bt.profile(reset=True)
+    value = bt.N_total * substeps * args.steps * world / (ms * 1e-3)
+    sizes = [b.n_particles for b, _ in specs]
+    fused_avg = prof["fused_ms"] / max(prof["fused_launches"], 1)
+    return {
+        "metric": METRIC + " (batched sensors)", "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": f"c2: {len(specs)} sensors, sides U[8,16] mm x thickness U[2,4] mm, "
+                               f"dx=0.25 mm, {bt.N_total} particles ({min(sizes)}-{max(sizes)} each), "
+                               f"{substeps} substeps dt={dt:g} s + 64x64 map per sensor per step",
+                   "instances": len(specs), "particles": bt.N_total, "autotune": tuned,
+                   "parallelism": f"replicas x{world}", "l2": "inputs larger than L2"},
+        "kernel_share_of_step": {k: round(prof[k + "_ms"] / max(ms, 1e-9), 4)
+                                 for k in ("grid", "fused", "edge", "sort")},
+        "fused_avg_launch_ms": fused_avg,
+        "gpu_launches": args.steps * (5 * substeps + 1 + 3 * len(specs)),
+        "clocks": clk,
+    }
+
+
 def load_traffic(workload):
     """DRAM bytes per fused launch from the committed ncu summary; null when
     the kernel source changed since the counters were taken."""
@@ -343,10 +417,12 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c1")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["c2"], default="c1")
     ap.add_argument("--substeps", type=int, default=0, help="override substeps per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--instances", type=int, default=256, help="sensors of the batched workload")
+    ap.add_argument("--no-autotune", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours" and not args.substeps:
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
@@ -364,6 +440,14 @@ def main():
     if world > 1:
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
+    if args.workload == "c2":
+        result = run_batch_bench(args, rank, world, local_rank)
+        if rank == 0:
+            print(json.dumps(result))
+        if world > 1:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
+        return
     result, sim = run_ours(args, rank, world, local_rank)
     if rank == 0:
         if not args.no_cpu_baseline:

@@ -269,6 +269,57 @@ tacchi_status tacchi_clear_error(tacchi_handle h);
 tacchi_status tacchi_init_lattice(int nx, int ny, int nz, int pad_side, int pad_bottom,
                                   uint64_t seed, int jitter, float *u, uint8_t *flags);
 
+/* ---- Batches of independent sensors --------------------------------------
+ * A batch holds n independent elastomer instances (each with its own size,
+ * material, particles, grid and indenter) that advance together: one
+ * tacchi_step runs every substep of every instance as one CUDA graph launch,
+ * each kernel covering all instances.  A handle made by tacchi_create is a
+ * batch of one; the calls above act on instance 0 of any handle.  The paper
+ * simulates one sensor at a time; batching is this library's addition. */
+
+/* Create a batch of n instances from descs[0..n-1] (host array), on the
+ * current device and the given stream.  Errors: as tacchi_create, and
+ * INVALID_ARG for n < 1 or n > 65536. */
+tacchi_status tacchi_batch_create(int n, const tacchi_elastomer_desc *descs, void *stream,
+                                  tacchi_handle *out);
+
+/* Number of instances of a handle (1 for tacchi_create); out: host. */
+tacchi_status tacchi_batch_size(tacchi_handle h, int *out);
+
+/* Per-instance forms of tacchi_info / tacchi_set_indenter /
+ * tacchi_get_indenter_pose / tacchi_heightmap / tacchi_render /
+ * tacchi_get_state / tacchi_set_state (same arguments, layouts and errors;
+ * state arrays hold that instance's n_particles).  INVALID_ARG if i is out
+ * of range. */
+tacchi_status tacchi_batch_info(tacchi_handle h, int i, tacchi_info_t *out);
+tacchi_status tacchi_batch_set_indenter(tacchi_handle h, int i, const tacchi_indenter_desc *desc,
+                                        const double pose[7], const double vel[6]);
+tacchi_status tacchi_batch_get_indenter_pose(tacchi_handle h, int i, double pose[7]);
+tacchi_status tacchi_batch_heightmap(tacchi_handle h, int i, int w, int hgt, const double window_m[4],
+                                     int fill_radius, float *out);
+tacchi_status tacchi_batch_render(tacchi_handle h, int i, const tacchi_render_params *rp, int w,
+                                  int hgt, const double window_m[4], int fill_radius, float *out_rgb,
+                                  float *out_height);
+tacchi_status tacchi_batch_get_state(tacchi_handle h, int i, float *u, float *v, float *C, float *Fm,
+                                     uint8_t *flags);
+tacchi_status tacchi_batch_set_state(tacchi_handle h, int i, const float *u, const float *v,
+                                     const float *C, const float *Fm);
+
+/* Sort-block shape (cells) used by the transfer kernel for every instance:
+ * 4x4x4, 8x8x4, 8x8x8 or 16x8x4.  Re-sorts the particles and drops cached
+ * graphs.  Errors: INVALID_ARG for other shapes. */
+tacchi_status tacchi_set_block(tacchi_handle h, int bx, int by, int bz);
+
+/* Autotuner: times n_substeps substeps of length dt with each supported
+ * block shape on the handle's current state (which it saves and restores,
+ * together with the indenter poses), keeps the fastest shape and writes it to
+ * best[3] (host); ms_per_substep[4] (host, optional) receives the time per
+ * substep of the four candidates in the order 4x4x4, 8x8x4, 8x8x8, 16x8x4.
+ * Synchronises.  Errors: INVALID_ARG, CUDA, and any device error raised
+ * while timing. */
+tacchi_status tacchi_autotune(tacchi_handle h, int n_substeps, double dt, int best[3],
+                              double ms_per_substep[4]);
+
 /* Short English description of a status. */
 const char *tacchi_status_string(tacchi_status s);
 

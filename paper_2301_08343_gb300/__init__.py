@@ -242,3 +242,147 @@ class Tacchi:
         check(lib().tacchi_get_grid(self._h, ptr(out)), "tacchi_get_grid")
         self.sync()
         return out
+
+
+def _desc_from(block, seed=None, fix_base=True, gravity=(0.0, 0.0, 0.0), sort_block=None, jitter=True):
+    """ElastomerDesc from an object with nx, ny, nz, dx, E, nu, rho, pad_side,
+    pad_bottom, pad_top and seed attributes."""
+    d = _lib.ElastomerDesc()
+    ext = (block.nx * block.dx, block.ny * block.dx, block.nz * block.dx)
+    for a in range(3):
+        d.extent_m[a] = ext[a]
+        d.gravity[a] = gravity[a]
+    d.dx_m, d.E_pa, d.nu, d.density = block.dx, block.E, block.nu, block.rho
+    d.seed = block.seed if seed is None else seed
+    d.jitter = int(bool(jitter))
+    d.pad_side, d.pad_bottom, d.pad_top = block.pad_side, block.pad_bottom, block.pad_top
+    d.free_base = 0 if fix_base else 1
+    if sort_block is not None:
+        for a in range(3):
+            d.block[a] = sort_block[a]
+    return d
+
+
+class TacchiBatch:
+    """Many independent sensor elastomers advanced together (one handle)."""
+
+    def __init__(self, blocks, fix_base=True, sort_block=None, stream=None):
+        torch = _torch()
+        self._torch = torch
+        n = len(blocks)
+        arr = (_lib.ElastomerDesc * n)()
+        for i, b in enumerate(blocks):
+            arr[i] = _desc_from(b, fix_base=fix_base, sort_block=sort_block)
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        h = C.c_void_p()
+        self._h = None
+        check(lib().tacchi_batch_create(n, arr, C.c_void_p(self._stream.cuda_stream), C.byref(h)),
+              "tacchi_batch_create")
+        self._h = h
+        self.n = n
+        self.blocks = list(blocks)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+        self.info = []
+        for i in range(n):
+            info = _lib.Info()
+            check(lib().tacchi_batch_info(self._h, i, C.byref(info)), "tacchi_batch_info")
+            self.info.append(dict(N=int(info.n_particles), n_surface=int(info.n_surface),
+                                  grid=tuple(info.grid), n_nodes=int(info.n_nodes),
+                                  origin=tuple(info.origin_m), dx=float(info.dx_m),
+                                  z_top=float(info.z_top_m)))
+        self.N_total = sum(x["N"] for x in self.info)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().tacchi_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_indenter(self, i, kind=None, params=(), pose=None, vel=None, hm=None, hm_pixel=0.0):
+        dp = None
+        keep = None
+        if kind is not None:
+            dp = _lib.IndenterDesc()
+            dp.kind = int(kind)
+            for e, x in enumerate(params):
+                dp.params[e] = x
+            if hm is not None:
+                keep = np.ascontiguousarray(hm, np.float32)
+                dp.hm_h, dp.hm_w = keep.shape
+                dp.hm_pixel_m = hm_pixel
+                dp.hm = keep.ctypes.data_as(C.POINTER(C.c_float))
+        pz = None if pose is None else (C.c_double * 7)(*pose)
+        vz = None if vel is None else (C.c_double * 6)(*vel)
+        check(lib().tacchi_batch_set_indenter(self._h, i, C.byref(dp) if dp is not None else None,
+                                              pz, vz), "tacchi_batch_set_indenter")
+        del keep
+
+    def indenter_pose(self, i):
+        p = (C.c_double * 7)()
+        check(lib().tacchi_batch_get_indenter_pose(self._h, i, p), "tacchi_batch_get_indenter_pose")
+        return tuple(p)
+
+    def step(self, n_substeps, dt):
+        check(lib().tacchi_step(self._h, int(n_substeps), float(dt)), "tacchi_step")
+
+    def sync(self):
+        check(lib().tacchi_sync(self._h), "tacchi_sync")
+
+    def status(self) -> int:
+        return int(lib().tacchi_sync(self._h))
+
+    def set_profiling(self, on=True):
+        check(lib().tacchi_set_profiling(self._h, int(bool(on))), "tacchi_set_profiling")
+
+    def profile(self, reset=False):
+        p = _lib.Profile()
+        check(lib().tacchi_get_profile(self._h, C.byref(p), int(bool(reset))), "tacchi_get_profile")
+        return {f: getattr(p, f) for f, _ in p._fields_}
+
+    def set_block(self, shape):
+        check(lib().tacchi_set_block(self._h, *shape), "tacchi_set_block")
+
+    def autotune(self, n_substeps, dt):
+        best = (C.c_int * 3)()
+        ms = (C.c_double * 4)()
+        check(lib().tacchi_autotune(self._h, int(n_substeps), float(dt), best, ms), "tacchi_autotune")
+        return tuple(best), dict(zip(["4x4x4", "8x8x4", "8x8x8", "16x8x4"], list(ms)))
+
+    def heightmap(self, i, w, h, window, fill_radius=8, out=None):
+        torch = self._torch
+        out = out if out is not None else torch.empty((h, w), device=self.device, dtype=torch.float32)
+        check(lib().tacchi_batch_heightmap(self._h, i, w, h, (C.c_double * 4)(*window), fill_radius,
+                                           ptr(out)), "tacchi_batch_heightmap")
+        return out
+
+    def render(self, i, w, h, window, rp=None, fill_radius=8, out=None, out_height=None):
+        torch = self._torch
+        rp = rp or default_render_params()
+        out = out if out is not None else torch.empty((h, w, 3), device=self.device, dtype=torch.float32)
+        check(lib().tacchi_batch_render(self._h, i, C.byref(rp), w, h, (C.c_double * 4)(*window),
+                                        fill_radius, ptr(out), ptr(out_height)), "tacchi_batch_render")
+        return out
+
+    def get_state(self, i):
+        torch = self._torch
+        n = self.info[i]["N"]
+        f = lambda *s: torch.empty(s, device=self.device, dtype=torch.float32)
+        u, v, Cm, Fm = f(3, n), f(3, n), f(9, n), f(9, n)
+        flags = torch.empty(n, device=self.device, dtype=torch.uint8)
+        st = lib().tacchi_batch_get_state(self._h, i, ptr(u), ptr(v), ptr(Cm), ptr(Fm), ptr(flags))
+        return dict(u=u, v=v, C=Cm, Fm=Fm, flags=flags, status=int(st))
+
+    def set_state(self, i, u, v=None, Cm=None, Fm=None):
+        torch = self._torch
+        n = self.info[i]["N"]
+        dev = lambda t, r: None if t is None else torch.as_tensor(t, dtype=torch.float32).reshape(
+            r, n).contiguous().to(self.device)
+        tu, tv, tC, tF = dev(u, 3), dev(v, 3), dev(Cm, 9), dev(Fm, 9)
+        check(lib().tacchi_batch_set_state(self._h, i, ptr(tu), ptr(tv), ptr(tC), ptr(tF)),
+              "tacchi_batch_set_state")
+        check(lib().tacchi_sync(self._h), "tacchi_batch_set_state")

@@ -83,6 +83,18 @@ SIGNATURES = {
     "tacchi_version": (C.c_int, []),
 }
 EXTRA_SIGNATURES = {
+    "tacchi_batch_create": (C.c_int, [C.c_int, C.POINTER(ElastomerDesc), _vp, C.POINTER(_vp)]),
+    "tacchi_batch_size": (C.c_int, [_vp, C.POINTER(C.c_int)]),
+    "tacchi_batch_info": (C.c_int, [_vp, C.c_int, C.POINTER(Info)]),
+    "tacchi_batch_set_indenter": (C.c_int, [_vp, C.c_int, C.POINTER(IndenterDesc), _dp, _dp]),
+    "tacchi_batch_get_indenter_pose": (C.c_int, [_vp, C.c_int, _dp]),
+    "tacchi_batch_heightmap": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _dp, C.c_int, _vp]),
+    "tacchi_batch_render": (C.c_int, [_vp, C.c_int, C.POINTER(RenderParams), C.c_int, C.c_int, _dp,
+                                      C.c_int, _vp, _vp]),
+    "tacchi_batch_get_state": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp]),
+    "tacchi_batch_set_state": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp]),
+    "tacchi_set_block": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int]),
+    "tacchi_autotune": (C.c_int, [_vp, C.c_int, C.c_double, C.POINTER(C.c_int), _dp]),
     "tacchi_heightmap_static": (C.c_int, [_vp, C.c_int64, _vp, _vp, C.c_int, C.c_double, _dp,
                                           C.c_double, C.c_int, C.c_int, _dp, C.c_int, _vp, _vp]),
 }

@@ -1,15 +1,18 @@
 // api.cu -- host implementation of the C ABI declared in include/tacchi.h.
 //
-// One tacchi_ctx owns one elastomer instance laid out as a batch of one (the
-// batched entry points reuse the same kernels over many instances).  A
-// tacchi_step of n substeps is queued as one CUDA graph:
+// A tacchi_ctx owns a batch of one or more independent elastomer instances
+// laid out back to back in device memory (particles, grid nodes and sort
+// blocks concatenated).  A tacchi_step of n substeps is queued as one CUDA
+// graph per chunk of at most 512 substeps, each kernel covering every
+// instance:
 //   clear grid -> P2G -> [grid update(k) -> fused G2P+P2G -> sort?] x (n-1)
 //   -> grid update(n-1) -> G2P -> sort?
-// The indenter's per-substep FP32 frames are computed on the host in FP64
-// and uploaded before each graph launch.
+// The indenters' per-substep FP32 frames are computed on the host in FP64 and
+// uploaded before each graph launch.
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -23,11 +26,13 @@ using namespace tacchi;
 
 namespace {
 
-constexpr int kMaxChunk = 512;      // substeps per captured graph
-constexpr int kMaxGraphs = 8;       // cached (n, dt) graphs per context
+constexpr int kMaxChunk = 512;  // substeps per captured graph
+constexpr int kMaxGraphs = 8;   // cached (n, dt) graphs per context
 constexpr int kMaxFillRadius = 64;
+constexpr int kMaxInstances = 65536;
+const SortBlock kShapes[4] = {{4, 4, 4}, {8, 8, 4}, {8, 8, 8}, {16, 8, 4}};
 
-bool finite3(const double *a, int n) {
+bool finite_all(const double *a, int n) {
   for (int i = 0; i < n; ++i)
     if (!std::isfinite(a[i])) return false;
   return true;
@@ -47,9 +52,9 @@ inline double uniform01(uint64_t seed, uint64_t k) {
 
 // Particle lattice: particle p = cell * 8 + sub, cells ordered z, y, x;
 // sub = sz * 4 + sy * 2 + sx; axis a at (cell + (sub_a + U) / 2) cells.
-void make_lattice(int nx, int ny, int nz, int pad_side, int pad_bottom, uint64_t seed, int jitter,
-                  float *u, uint8_t *flags) {
-  const long long N = 8ll * nx * ny * nz;
+// u points at component 0 of this instance; components are `stride` apart.
+void make_lattice(int nx, int ny, int nz, int pad_side, int pad_bottom, uint64_t seed, int jitter, float *u,
+                  long long stride, uint8_t *flags) {
   for (long long cell = 0; cell < (long long)nx * ny * nz; ++cell) {
     const int cx = (int)(cell % nx), cy = (int)((cell / nx) % ny), cz = (int)(cell / ((long long)nx * ny));
     const int org[3] = {cx + pad_side, cy + pad_side, cz + pad_bottom};
@@ -59,17 +64,17 @@ void make_lattice(int nx, int ny, int nz, int pad_side, int pad_bottom, uint64_t
       for (int a = 0; a < 3; ++a) {
         const double U = jitter ? uniform01(seed, (uint64_t)(3 * p + a)) : 0.5;
         const double off = ((double)sa[a] + U) * 0.5;
-        u[a * N + p] = (float)((double)org[a] + off);
+        u[a * stride + p] = (float)((double)org[a] + off);
       }
       flags[p] = (uint8_t)((cz == 0 ? 1 : 0) | (cz == nz - 1 && sa[2] == 1 ? 2 : 0));
     }
   }
 }
 
-// Block shapes the transfer kernel is instantiated for.
 bool block_supported(SortBlock b) {
-  return (b.x == 8 && b.y == 8 && b.z == 4) || (b.x == 4 && b.y == 4 && b.z == 4) ||
-         (b.x == 8 && b.y == 8 && b.z == 8) || (b.x == 16 && b.y == 8 && b.z == 4);
+  for (const SortBlock &s : kShapes)
+    if (s.x == b.x && s.y == b.y && s.z == b.z) return true;
+  return false;
 }
 
 tacchi_status cuda_status(cudaError_t e) { return e == cudaSuccess ? TACCHI_OK : TACCHI_ERR_CUDA; }
@@ -79,6 +84,35 @@ tacchi_status cuda_status(cudaError_t e) { return e == cudaSuccess ? TACCHI_OK :
     cudaError_t e_ = (expr);                       \
     if (e_ != cudaSuccess) return cuda_status(e_); \
   } while (0)
+
+// Validated geometry of one instance description.
+struct Geometry {
+  int n[3];
+  int ps, pb, pt;
+};
+
+tacchi_status validate_desc(const tacchi_elastomer_desc *d, Geometry *g) {
+  if (!d) return TACCHI_ERR_INVALID_ARG;
+  if (!(d->dx_m > 0) || !std::isfinite(d->dx_m) || !finite_all(d->extent_m, 3) || !finite_all(d->gravity, 3))
+    return TACCHI_ERR_INVALID_ARG;
+  if (!(d->E_pa > 0) || !(d->nu > -1.0 && d->nu < 0.5) || !(d->density > 0) || !std::isfinite(d->E_pa) ||
+      !std::isfinite(d->density))
+    return TACCHI_ERR_INVALID_ARG;
+  for (int a = 0; a < 3; ++a) {
+    const double r = d->extent_m[a] / d->dx_m;
+    g->n[a] = (int)std::llround(r);
+    if (g->n[a] < 1 || std::fabs(r - g->n[a]) > 1e-6 * std::max(1.0, r)) return TACCHI_ERR_INVALID_ARG;
+  }
+  g->ps = d->pad_side ? d->pad_side : 4;
+  g->pb = d->pad_bottom ? d->pad_bottom : 3;
+  g->pt = d->pad_top ? d->pad_top : 4;
+  if (g->ps < 3 || g->pb < 3 || g->pt < 3) return TACCHI_ERR_INVALID_ARG;
+  if (8.0 * g->n[0] * g->n[1] * g->n[2] > 2.0e9) return TACCHI_ERR_INVALID_ARG;
+  const bool user_block = d->block[0] != 0 || d->block[1] != 0 || d->block[2] != 0;
+  if (user_block && !block_supported(SortBlock{d->block[0], d->block[1], d->block[2]}))
+    return TACCHI_ERR_INVALID_ARG;
+  return TACCHI_OK;
+}
 
 }  // namespace
 
@@ -96,32 +130,44 @@ struct GraphEntry {
   std::vector<TimedSpan> spans;
 };
 
+// Host record of one instance.
+struct InstHost {
+  int n[3] = {0, 0, 0};
+  int pad_side = 0, pad_bottom = 0, pad_top = 0;
+  int G[3] = {0, 0, 0};
+  double dx = 0, origin[3] = {0, 0, 0}, z_top = 0;
+  long long N = 0, nodes = 0, part_off = 0, node_off = 0;
+  long long surf_off = 0;
+  int Ns = 0;
+  Instance dev{};  // mirror of the device record (blocks, shape and frames filled in later)
+  // indenter (FP64)
+  int ind_kind = IND_NONE;
+  double ind_params[8] = {0};
+  int hm_w = 0, hm_h = 0;
+  double hm_pixel = 0;
+  float *d_hm = nullptr;
+  double pose[7] = {0, 0, 0, 1, 0, 0, 0};
+  double vel[6] = {0, 0, 0, 0, 0, 0};
+};
+
 struct tacchi_ctx {
   int device = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   cudaStream_t cap = nullptr;
 
-  // geometry (host, FP64)
-  int nx = 0, ny = 0, nz = 0, pad_side = 0, pad_bottom = 0, pad_top = 0;
-  int G[3] = {0, 0, 0};
-  double dx = 0, origin[3] = {0, 0, 0}, z_top = 0;
-  long long N = 0, nodes = 0;
+  std::vector<InstHost> in;
   SortBlock blk{8, 8, 4};
-  long long nblocks = 0;
+  long long Ntot = 0, Nnodes = 0, Nblk = 0, Nblk_cap = 0, Ns_tot = 0;
 
-  Instance inst{};  // host mirror
-  Batch b{};        // device pointers
+  Batch b{};  // device pointers of the whole batch
 
-  // device buffers
   Instance *d_inst = nullptr;
-  long long *d_offs = nullptr;  // [2]: node offset, particle offset (one instance)
+  long long *d_node_offs = nullptr, *d_part_offs = nullptr;
   uint32_t *d_block_inst = nullptr;
-  IndenterFrame *d_frames = nullptr;
-  float *d_hm = nullptr;
+  IndenterFrame *d_frames = nullptr;  // [n_inst][kMaxChunk]
   uint32_t *d_surf = nullptr;
   float *d_z0 = nullptr;
-  int Ns = 0;
   int *d_cov = nullptr;
   size_t cov_cap = 0;
   float *d_hbuf = nullptr;
@@ -129,21 +175,10 @@ struct tacchi_ctx {
   float *d_rgb = nullptr;
   size_t rgb_cap = 0;
 
-  // host staging for the per-step upload (pinned)
-  struct Stage {
-    Instance inst;
-    IndenterFrame frames[kMaxChunk];
-  } *h_stage = nullptr;
+  // pinned staging of the per-chunk upload: instance records, then frames
+  unsigned char *h_stage = nullptr;
   cudaEvent_t stage_done = nullptr;
   int *h_err = nullptr;
-
-  // indenter (host, FP64)
-  int ind_kind = IND_NONE;
-  double ind_params[8] = {0};
-  int hm_w = 0, hm_h = 0;
-  double hm_pixel = 0;
-  double pose[7] = {0, 0, 0, 1, 0, 0, 0};
-  double vel[6] = {0, 0, 0, 0, 0, 0};
 
   std::vector<GraphEntry> graphs;
   bool profiling = false;
@@ -151,6 +186,8 @@ struct tacchi_ctx {
   int64_t prof_n[4] = {0, 0, 0, 0};
   bool stepped = false;
   size_t device_bytes = 0;
+
+  int n_inst() const { return (int)in.size(); }
 };
 
 namespace {
@@ -164,12 +201,12 @@ cudaError_t dalloc(tacchi_ctx *c, T **p, size_t count) {
 }
 
 // Shape constants of the inside test in cells, FP32 (rounded from FP64).
-IndenterShape make_shape(const tacchi_ctx *c) {
+IndenterShape make_shape(const InstHost &h) {
   IndenterShape s{};
-  s.kind = c->ind_kind;
-  const double dx = c->dx;
-  const double *P = c->ind_params;
-  switch (c->ind_kind) {
+  s.kind = h.ind_kind;
+  const double dx = h.dx;
+  const double *P = h.ind_params;
+  switch (h.ind_kind) {
     case IND_SPHERE:
       s.s0 = (float)((P[0] / dx) * (P[0] / dx));
       break;
@@ -188,12 +225,12 @@ IndenterShape make_shape(const tacchi_ctx *c) {
       break;
     case IND_HEIGHTMAP:
       s.s0 = (float)(P[0] / dx);
-      s.inv_pix = (float)(dx / c->hm_pixel);
-      s.offx = (float)(c->hm_w * 0.5 - 0.5);
-      s.offy = (float)(c->hm_h * 0.5 - 0.5);
-      s.hm_w = c->hm_w;
-      s.hm_h = c->hm_h;
-      s.hm = c->d_hm;
+      s.inv_pix = (float)(dx / h.hm_pixel);
+      s.offx = (float)(h.hm_w * 0.5 - 0.5);
+      s.offy = (float)(h.hm_h * 0.5 - 0.5);
+      s.hm_w = h.hm_w;
+      s.hm_h = h.hm_h;
+      s.hm = h.d_hm;
       break;
     default:
       break;
@@ -216,9 +253,9 @@ void rotation_of(const double *q, double R[9]) {
   R[8] = 1.0 - 2.0 * (x * x + y * y);
 }
 
-IndenterFrame frame_of(const tacchi_ctx *c, const double *pose, const double *vel) {
+IndenterFrame frame_of(const InstHost &h, const double *pose, const double *vel) {
   IndenterFrame f{};
-  for (int a = 0; a < 3; ++a) f.c[a] = (float)((pose[a] - c->origin[a]) / c->dx);
+  for (int a = 0; a < 3; ++a) f.c[a] = (float)((pose[a] - h.origin[a]) / h.dx);
   double R[9];
   rotation_of(pose + 3, R);
   for (int e = 0; e < 9; ++e) f.r[e] = (float)R[e];
@@ -262,6 +299,11 @@ void destroy_entry(GraphEntry &ge) {
   ge.exec = nullptr;
 }
 
+void drop_graphs(tacchi_ctx *c) {
+  for (auto &g : c->graphs) destroy_entry(g);
+  c->graphs.clear();
+}
+
 // Enqueue one kernel (group) on the capture stream, bracketed by timing
 // events when the graph is built for profiling.
 template <typename F>
@@ -287,7 +329,7 @@ cudaError_t build_graph(tacchi_ctx *c, int n, float dt, GraphEntry *ge) {
   const Batch &b = c->b;
   const SortBlock blk = c->blk;
   cudaStream_t s = c->cap;
-  cudaError_t le = cudaMemsetAsync(b.gmm, 0, sizeof(float4) * c->nodes, s);
+  cudaError_t le = cudaMemsetAsync(b.gmm, 0, sizeof(float4) * c->Nnodes, s);
   if (le == cudaSuccess) le = timed(c, pe, 2, [&] { return launch_transfer(b, blk, XFER_P2G, dt, s); });
   for (int k = 0; k + 1 < n && le == cudaSuccess; ++k) {
     le = timed(c, pe, 0, [&] { return launch_grid_update(b, k, dt, 1, s); });
@@ -386,30 +428,32 @@ cudaError_t ensure(tacchi_ctx *c, T **p, size_t *cap, size_t count) {
 }
 
 tacchi_status validate_window(int w, int h, const double *win, int fill_radius) {
-  if (w < 1 || h < 1 || !win || !finite3(win, 4)) return TACCHI_ERR_INVALID_ARG;
+  if (w < 1 || h < 1 || !win || !finite_all(win, 4)) return TACCHI_ERR_INVALID_ARG;
   if (!(win[2] > win[0]) || !(win[3] > win[1])) return TACCHI_ERR_INVALID_ARG;
   if (fill_radius < 0 || fill_radius > kMaxFillRadius) return TACCHI_ERR_INVALID_ARG;
   if ((long long)w * h > (1ll << 28)) return TACCHI_ERR_INVALID_ARG;
   return TACCHI_OK;
 }
 
-tacchi_status run_heightmap(tacchi_ctx *c, int w, int h, const double *win, int fill_radius, float *dev_out) {
+tacchi_status run_heightmap(tacchi_ctx *c, int i, int w, int h, const double *win, int fill_radius,
+                            float *dev_out) {
+  const InstHost &I = c->in[i];
   CK(ensure(c, &c->d_cov, &c->cov_cap, (size_t)w * h));
   HeightmapArgs a{};
   a.u = c->b.u;
-  a.Ntot = c->N;
-  a.surf = c->d_surf;
-  a.z0 = c->d_z0;
-  a.Ns = c->Ns;
-  const double pxc = ((win[2] - win[0]) / (double)w) / c->dx;
-  const double pyc = ((win[3] - win[1]) / (double)h) / c->dx;
-  a.A0X = (float)((win[0] - c->origin[0]) / c->dx + 0.5 * pxc);
-  a.A0Y = (float)((win[1] - c->origin[1]) / c->dx + 0.5 * pyc);
+  a.Ntot = c->Ntot;
+  a.surf = c->d_surf + I.surf_off;
+  a.z0 = c->d_z0 + I.surf_off;
+  a.Ns = I.Ns;
+  const double pxc = ((win[2] - win[0]) / (double)w) / I.dx;
+  const double pyc = ((win[3] - win[1]) / (double)h) / I.dx;
+  a.A0X = (float)((win[0] - I.origin[0]) / I.dx + 0.5 * pxc);
+  a.A0Y = (float)((win[1] - I.origin[1]) / I.dx + 0.5 * pyc);
   a.SX = (float)pxc;
   a.SY = (float)pyc;
   if (!(a.SX > 0.f) || !(a.SY > 0.f)) return TACCHI_ERR_INVALID_ARG;
-  a.z_top = (float)c->z_top;
-  a.dx = (float)c->dx;
+  a.z_top = (float)I.z_top;
+  a.dx = (float)I.dx;
   a.w = w;
   a.h = h;
   a.fill_radius = fill_radius;
@@ -444,14 +488,53 @@ tacchi_status fill_shade_args(const tacchi_render_params *rp, int w, int h, doub
   return TACCHI_OK;
 }
 
+// Block decomposition of every instance for shape blk; uploads the instance
+// table and the block-to-instance map and re-sorts.  Capacity for the most
+// blocks any supported shape needs was allocated at creation.
+tacchi_status apply_blocks(tacchi_ctx *c, SortBlock blk) {
+  if (!block_supported(blk)) return TACCHI_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  drop_graphs(c);
+  c->blk = blk;
+  long long off = 0;
+  std::vector<uint32_t> bi;
+  for (int i = 0; i < c->n_inst(); ++i) {
+    InstHost &h = c->in[i];
+    const int nb[3] = {(h.G[0] + blk.x - 1) / blk.x, (h.G[1] + blk.y - 1) / blk.y, (h.G[2] + blk.z - 1) / blk.z};
+    for (int a = 0; a < 3; ++a) h.dev.nb[a] = nb[a];
+    h.dev.block_off = off;
+    h.dev.nblocks = (long long)nb[0] * nb[1] * nb[2];
+    bi.insert(bi.end(), (size_t)h.dev.nblocks, (uint32_t)i);
+    off += h.dev.nblocks;
+  }
+  if (off > c->Nblk_cap) return TACCHI_ERR_INVALID_ARG;
+  c->Nblk = off;
+  c->b.Nblk = off;
+  std::vector<Instance> tab(c->n_inst());
+  for (int i = 0; i < c->n_inst(); ++i) {
+    tab[i] = c->in[i].dev;
+    tab[i].shape = make_shape(c->in[i]);
+  }
+  CK(cudaMemcpy(c->d_inst, tab.data(), sizeof(Instance) * tab.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(c->d_block_inst, bi.data(), sizeof(uint32_t) * bi.size(), cudaMemcpyHostToDevice));
+  CK(cudaMemsetAsync(c->b.bcount, 0, sizeof(uint32_t) * c->Nblk_cap, c->stream));
+  CK(prepare_transfer(blk));
+  CK(launch_sort(c->b, blk, 1, c->stream));
+  CK(cudaMemsetAsync(c->b.movers, 0, sizeof(int), c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  return TACCHI_OK;
+}
+
 void release(tacchi_ctx *c) {
   if (!c) return;
   if (c->stream) cudaStreamSynchronize(c->stream);
-  for (auto &g : c->graphs) destroy_entry(g);
-  c->graphs.clear();
+  drop_graphs(c);
+  for (auto &h : c->in)
+    if (h.d_hm) cudaFree(h.d_hm);
   void *bufs[] = {c->b.u, c->b.Fm, c->b.v, c->b.C, (void *)c->b.flags, c->b.idx, c->b.key, c->b.bstart,
-                  c->b.bcount, c->b.cursor, c->b.gmm, c->b.gv, c->b.err, c->b.movers, c->d_inst, c->d_offs,
-                  c->d_block_inst, c->d_frames, c->d_hm, c->d_surf, c->d_z0, c->d_cov, c->d_hbuf, c->d_rgb};
+                  c->b.bcount, c->b.cursor, c->b.gmm, c->b.gv, c->b.err, c->b.movers, c->d_inst,
+                  c->d_node_offs, c->d_part_offs, c->d_block_inst, c->d_frames, c->d_surf, c->d_z0,
+                  c->d_cov, c->d_hbuf, c->d_rgb};
   for (void *p : bufs)
     if (p) cudaFree(p);
   if (c->h_stage) cudaFreeHost(c->h_stage);
@@ -460,6 +543,188 @@ void release(tacchi_ctx *c) {
   if (c->cap) cudaStreamDestroy(c->cap);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
+}
+
+size_t stage_bytes(int n_inst) {
+  return sizeof(Instance) * (size_t)n_inst + sizeof(IndenterFrame) * (size_t)n_inst * kMaxChunk;
+}
+
+tacchi_status create_batch(int n, const tacchi_elastomer_desc *descs, void *stream, tacchi_handle *out) {
+  if (!descs || !out || n < 1 || n > kMaxInstances) return TACCHI_ERR_INVALID_ARG;
+  *out = nullptr;
+  std::vector<Geometry> geo(n);
+  double Nd = 0;
+  for (int i = 0; i < n; ++i) {
+    tacchi_status s = validate_desc(descs + i, &geo[i]);
+    if (s != TACCHI_OK) return s;
+    Nd += 8.0 * geo[i].n[0] * geo[i].n[1] * geo[i].n[2];
+  }
+  if (Nd > 2.0e9) return TACCHI_ERR_INVALID_ARG;
+  const tacchi_elastomer_desc &d0 = descs[0];
+  const bool user_block = d0.block[0] != 0 || d0.block[1] != 0 || d0.block[2] != 0;
+
+  tacchi_ctx *c = new (std::nothrow) tacchi_ctx();
+  if (!c) return TACCHI_ERR_OOM;
+  auto fail = [&](tacchi_status s) {
+    release(c);
+    return s;
+  };
+  if (cudaGetDevice(&c->device) != cudaSuccess) return fail(TACCHI_ERR_CUDA);
+  if (stream) {
+    c->stream = (cudaStream_t)stream;
+  } else {
+    if (cudaStreamCreate(&c->stream) != cudaSuccess) return fail(TACCHI_ERR_CUDA);
+    c->own_stream = true;
+  }
+  if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) return fail(TACCHI_ERR_CUDA);
+  if (cudaEventCreateWithFlags(&c->stage_done, cudaEventDisableTiming) != cudaSuccess)
+    return fail(TACCHI_ERR_CUDA);
+
+  // instance geometry and offsets
+  c->in.resize(n);
+  long long part = 0, node = 0, surf = 0, blk_cap = 0;
+  for (int i = 0; i < n; ++i) {
+    const tacchi_elastomer_desc &d = descs[i];
+    const Geometry &g = geo[i];
+    InstHost &h = c->in[i];
+    for (int a = 0; a < 3; ++a) h.n[a] = g.n[a];
+    h.pad_side = g.ps;
+    h.pad_bottom = g.pb;
+    h.pad_top = g.pt;
+    h.G[0] = g.n[0] + 2 * g.ps + 1;
+    h.G[1] = g.n[1] + 2 * g.ps + 1;
+    h.G[2] = g.n[2] + g.pb + g.pt + 1;
+    h.dx = d.dx_m;
+    h.origin[0] = -g.ps * d.dx_m;
+    h.origin[1] = -g.ps * d.dx_m;
+    h.origin[2] = -g.pb * d.dx_m;
+    h.z_top = g.n[2] * d.dx_m;
+    h.N = 8ll * g.n[0] * g.n[1] * g.n[2];
+    h.nodes = (long long)h.G[0] * h.G[1] * h.G[2];
+    h.part_off = part;
+    h.node_off = node;
+    h.Ns = 4 * g.n[0] * g.n[1];
+    h.surf_off = surf;
+    part += h.N;
+    node += h.nodes;
+    surf += h.Ns;
+    long long most = 0;
+    for (const SortBlock &sb : kShapes)
+      most = std::max(most, (long long)((h.G[0] + sb.x - 1) / sb.x) * ((h.G[1] + sb.y - 1) / sb.y) *
+                                ((h.G[2] + sb.z - 1) / sb.z));
+    blk_cap += most;
+    Instance &I = h.dev;
+    for (int a = 0; a < 3; ++a) {
+      I.G[a] = h.G[a];
+      I.gdt[a] = (float)d.gravity[a];
+    }
+    I.pad_bottom = g.pb;
+    I.fix_base = d.free_base ? 0 : 1;
+    I.node_off = h.node_off;
+    I.N = h.N;
+    I.part_off = h.part_off;
+    const double V0 = d.dx_m * d.dx_m * d.dx_m / 8.0;
+    I.dx = (float)d.dx_m;
+    I.inv_dx = (float)(1.0 / d.dx_m);
+    I.m = (float)(d.density * V0);
+    I.V0 = (float)V0;
+    I.mu = (float)(d.E_pa / (2.0 * (1.0 + d.nu)));
+    I.la = (float)(d.E_pa * d.nu / ((1.0 + d.nu) * (1.0 - 2.0 * d.nu)));
+    I.shape = IndenterShape{};
+  }
+  c->Ntot = part;
+  c->Nnodes = node;
+  c->Ns_tot = surf;
+  c->Nblk_cap = blk_cap;
+  SortBlock blk = user_block ? SortBlock{d0.block[0], d0.block[1], d0.block[2]}
+                             : (part / n < 2000000 ? SortBlock{4, 4, 4} : SortBlock{8, 8, 4});
+  for (int i = 0; i < n; ++i) c->in[i].dev.frames = nullptr;
+
+  const long long N = c->Ntot, Nn = c->Nnodes;
+  bool ok = dalloc(c, &c->b.u, 3 * N) == cudaSuccess && dalloc(c, &c->b.Fm, 9 * N) == cudaSuccess &&
+            dalloc(c, &c->b.v, 3 * N) == cudaSuccess && dalloc(c, &c->b.C, 9 * N) == cudaSuccess &&
+            dalloc(c, (uint8_t **)&c->b.flags, N) == cudaSuccess && dalloc(c, &c->b.idx, N) == cudaSuccess &&
+            dalloc(c, &c->b.key, N) == cudaSuccess && dalloc(c, &c->b.bstart, blk_cap + 1) == cudaSuccess &&
+            dalloc(c, &c->b.bcount, blk_cap) == cudaSuccess && dalloc(c, &c->b.cursor, blk_cap) == cudaSuccess &&
+            dalloc(c, &c->b.gmm, Nn) == cudaSuccess && dalloc(c, &c->b.gv, Nn) == cudaSuccess &&
+            dalloc(c, &c->b.err, 1) == cudaSuccess && dalloc(c, &c->b.movers, 1) == cudaSuccess &&
+            dalloc(c, &c->d_inst, n) == cudaSuccess && dalloc(c, &c->d_node_offs, n) == cudaSuccess &&
+            dalloc(c, &c->d_part_offs, n) == cudaSuccess && dalloc(c, &c->d_block_inst, blk_cap) == cudaSuccess &&
+            dalloc(c, &c->d_frames, (size_t)n * kMaxChunk) == cudaSuccess &&
+            dalloc(c, &c->d_surf, surf) == cudaSuccess && dalloc(c, &c->d_z0, surf) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    return fail(TACCHI_ERR_OOM);
+  }
+  if (cudaMallocHost((void **)&c->h_stage, stage_bytes(n)) != cudaSuccess ||
+      cudaMallocHost((void **)&c->h_err, sizeof(int)) != cudaSuccess)
+    return fail(TACCHI_ERR_OOM);
+  *c->h_err = 0;
+  for (int i = 0; i < n; ++i) c->in[i].dev.frames = c->d_frames + (size_t)i * kMaxChunk;
+
+  // initial particles (Eq. 1): lattice positions, v = 0, C = 0, F = I
+  std::vector<float> hu;
+  std::vector<uint8_t> hf;
+  std::vector<uint32_t> hs;
+  std::vector<float> hz;
+  std::vector<long long> noffs(n), poffs(n);
+  try {
+    hu.resize(3 * N);
+    hf.resize(N);
+    hs.reserve(surf);
+    hz.reserve(surf);
+  } catch (...) {
+    return fail(TACCHI_ERR_OOM);
+  }
+  for (int i = 0; i < n; ++i) {
+    const InstHost &h = c->in[i];
+    make_lattice(h.n[0], h.n[1], h.n[2], h.pad_side, h.pad_bottom, descs[i].seed, descs[i].jitter,
+                 hu.data() + h.part_off, N, hf.data() + h.part_off);
+    for (long long p = h.part_off; p < h.part_off + h.N; ++p)
+      if (hf[p] & 2) {
+        hs.push_back((uint32_t)p);
+        hz.push_back(hu[2 * N + p]);
+      }
+    noffs[i] = h.node_off;
+    poffs[i] = h.part_off;
+  }
+  c->b.inst = c->d_inst;
+  c->b.node_offs = c->d_node_offs;
+  c->b.part_offs = c->d_part_offs;
+  c->b.block_inst = c->d_block_inst;
+  c->b.n_inst = n;
+  c->b.Ntot = N;
+  c->b.Nnodes = Nn;
+
+  cudaStream_t st = c->stream;
+  bool up = cudaMemcpy(c->b.u, hu.data(), sizeof(float) * 3 * N, cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy((void *)c->b.flags, hf.data(), N, cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(c->d_surf, hs.data(), sizeof(uint32_t) * hs.size(), cudaMemcpyHostToDevice) ==
+                cudaSuccess &&
+            cudaMemcpy(c->d_z0, hz.data(), sizeof(float) * hz.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(c->d_node_offs, noffs.data(), sizeof(long long) * n, cudaMemcpyHostToDevice) ==
+                cudaSuccess &&
+            cudaMemcpy(c->d_part_offs, poffs.data(), sizeof(long long) * n, cudaMemcpyHostToDevice) ==
+                cudaSuccess &&
+            cudaMemsetAsync(c->b.Fm, 0, sizeof(float) * 9 * N, st) == cudaSuccess &&
+            cudaMemsetAsync(c->b.v, 0, sizeof(float) * 3 * N, st) == cudaSuccess &&
+            cudaMemsetAsync(c->b.C, 0, sizeof(float) * 9 * N, st) == cudaSuccess &&
+            cudaMemsetAsync(c->b.gmm, 0, sizeof(float4) * Nn, st) == cudaSuccess &&
+            cudaMemsetAsync(c->b.gv, 0, sizeof(float4) * Nn, st) == cudaSuccess &&
+            cudaMemsetAsync(c->b.err, 0, sizeof(int), st) == cudaSuccess;
+  if (!up) {
+    cudaGetLastError();
+    return fail(TACCHI_ERR_CUDA);
+  }
+  tacchi_status s = apply_blocks(c, blk);
+  if (s != TACCHI_OK) return fail(s);
+  *out = c;
+  return TACCHI_OK;
+}
+
+tacchi_status check_index(tacchi_handle c, int i) {
+  if (!c || i < 0 || i >= c->n_inst()) return TACCHI_ERR_INVALID_ARG;
+  return TACCHI_OK;
 }
 
 }  // namespace
@@ -482,215 +747,65 @@ const char *tacchi_status_string(tacchi_status s) {
   return "unknown status";
 }
 
-int tacchi_version(void) { return 100; }
+int tacchi_version(void) { return 200; }
 
 tacchi_status tacchi_init_lattice(int nx, int ny, int nz, int pad_side, int pad_bottom, uint64_t seed,
                                   int jitter, float *u, uint8_t *flags) {
   if (nx < 1 || ny < 1 || nz < 1 || pad_side < 0 || pad_bottom < 0 || !u || !flags)
     return TACCHI_ERR_INVALID_ARG;
   if (8.0 * nx * ny * nz > 2.0e9) return TACCHI_ERR_INVALID_ARG;
-  make_lattice(nx, ny, nz, pad_side, pad_bottom, seed, jitter, u, flags);
+  make_lattice(nx, ny, nz, pad_side, pad_bottom, seed, jitter, u, 8ll * nx * ny * nz, flags);
   return TACCHI_OK;
 }
 
 tacchi_status tacchi_create(const tacchi_elastomer_desc *d, void *stream, tacchi_handle *out) {
-  if (!d || !out) return TACCHI_ERR_INVALID_ARG;
-  *out = nullptr;
-  if (!(d->dx_m > 0) || !std::isfinite(d->dx_m) || !finite3(d->extent_m, 3) || !finite3(d->gravity, 3))
-    return TACCHI_ERR_INVALID_ARG;
-  if (!(d->E_pa > 0) || !(d->nu > -1.0 && d->nu < 0.5) || !(d->density > 0) || !std::isfinite(d->E_pa) ||
-      !std::isfinite(d->density))
-    return TACCHI_ERR_INVALID_ARG;
-  int n[3];
-  for (int a = 0; a < 3; ++a) {
-    const double r = d->extent_m[a] / d->dx_m;
-    n[a] = (int)std::llround(r);
-    if (n[a] < 1 || std::fabs(r - n[a]) > 1e-6 * std::max(1.0, r)) return TACCHI_ERR_INVALID_ARG;
-  }
-  const int ps = d->pad_side ? d->pad_side : 4;
-  const int pb = d->pad_bottom ? d->pad_bottom : 3;
-  const int pt = d->pad_top ? d->pad_top : 4;
-  if (ps < 3 || pb < 3 || pt < 3) return TACCHI_ERR_INVALID_ARG;
-  const double Nd = 8.0 * n[0] * n[1] * n[2];
-  if (Nd > 2.0e9) return TACCHI_ERR_INVALID_ARG;
-  const bool user_block = d->block[0] != 0 || d->block[1] != 0 || d->block[2] != 0;
-  if (user_block && !block_supported(SortBlock{d->block[0], d->block[1], d->block[2]}))
-    return TACCHI_ERR_INVALID_ARG;
+  return create_batch(1, d, stream, out);
+}
 
-  tacchi_ctx *c = new (std::nothrow) tacchi_ctx();
-  if (!c) return TACCHI_ERR_OOM;
-  auto fail = [&](tacchi_status s) {
-    release(c);
-    return s;
-  };
-  if (cudaGetDevice(&c->device) != cudaSuccess) return fail(TACCHI_ERR_CUDA);
-  if (stream) {
-    c->stream = (cudaStream_t)stream;
-  } else {
-    if (cudaStreamCreate(&c->stream) != cudaSuccess) return fail(TACCHI_ERR_CUDA);
-    c->own_stream = true;
-  }
-  if (cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking) != cudaSuccess) return fail(TACCHI_ERR_CUDA);
-  if (cudaEventCreateWithFlags(&c->stage_done, cudaEventDisableTiming) != cudaSuccess)
-    return fail(TACCHI_ERR_CUDA);
-
-  c->nx = n[0];
-  c->ny = n[1];
-  c->nz = n[2];
-  c->pad_side = ps;
-  c->pad_bottom = pb;
-  c->pad_top = pt;
-  c->G[0] = n[0] + 2 * ps + 1;
-  c->G[1] = n[1] + 2 * ps + 1;
-  c->G[2] = n[2] + pb + pt + 1;
-  c->dx = d->dx_m;
-  c->origin[0] = -ps * d->dx_m;
-  c->origin[1] = -ps * d->dx_m;
-  c->origin[2] = -pb * d->dx_m;
-  c->z_top = n[2] * d->dx_m;
-  c->N = (long long)Nd;
-  c->nodes = (long long)c->G[0] * c->G[1] * c->G[2];
-  if (user_block) {
-    c->blk = SortBlock{d->block[0], d->block[1], d->block[2]};
-  } else {
-    c->blk = c->N < 2000000 ? SortBlock{4, 4, 4} : SortBlock{8, 8, 4};
-  }
-  int nb[3] = {(c->G[0] + c->blk.x - 1) / c->blk.x, (c->G[1] + c->blk.y - 1) / c->blk.y,
-               (c->G[2] + c->blk.z - 1) / c->blk.z};
-  c->nblocks = (long long)nb[0] * nb[1] * nb[2];
-
-  // instance constants
-  Instance &I = c->inst;
-  for (int a = 0; a < 3; ++a) {
-    I.G[a] = c->G[a];
-    I.nb[a] = nb[a];
-    I.gdt[a] = (float)d->gravity[a];
-  }
-  I.pad_bottom = pb;
-  I.fix_base = d->free_base ? 0 : 1;
-  I.node_off = 0;
-  I.N = c->N;
-  I.part_off = 0;
-  I.block_off = 0;
-  I.nblocks = c->nblocks;
-  const double V0 = d->dx_m * d->dx_m * d->dx_m / 8.0;
-  I.dx = (float)d->dx_m;
-  I.inv_dx = (float)(1.0 / d->dx_m);
-  I.m = (float)(d->density * V0);
-  I.V0 = (float)V0;
-  I.mu = (float)(d->E_pa / (2.0 * (1.0 + d->nu)));
-  I.la = (float)(d->E_pa * d->nu / ((1.0 + d->nu) * (1.0 - 2.0 * d->nu)));
-  I.shape = IndenterShape{};
-
-  const long long N = c->N, Nn = c->nodes;
-  bool ok = dalloc(c, &c->b.u, 3 * N) == cudaSuccess && dalloc(c, &c->b.Fm, 9 * N) == cudaSuccess &&
-            dalloc(c, &c->b.v, 3 * N) == cudaSuccess && dalloc(c, &c->b.C, 9 * N) == cudaSuccess &&
-            dalloc(c, (uint8_t **)&c->b.flags, N) == cudaSuccess && dalloc(c, &c->b.idx, N) == cudaSuccess &&
-            dalloc(c, &c->b.key, N) == cudaSuccess && dalloc(c, &c->b.bstart, c->nblocks + 1) == cudaSuccess &&
-            dalloc(c, &c->b.bcount, c->nblocks) == cudaSuccess &&
-            dalloc(c, &c->b.cursor, c->nblocks) == cudaSuccess && dalloc(c, &c->b.gmm, Nn) == cudaSuccess &&
-            dalloc(c, &c->b.gv, Nn) == cudaSuccess && dalloc(c, &c->b.err, 1) == cudaSuccess &&
-            dalloc(c, &c->b.movers, 1) == cudaSuccess && dalloc(c, &c->d_inst, 1) == cudaSuccess &&
-            dalloc(c, &c->d_offs, 2) == cudaSuccess && dalloc(c, &c->d_block_inst, c->nblocks) == cudaSuccess &&
-            dalloc(c, &c->d_frames, kMaxChunk) == cudaSuccess;
-  if (!ok) {
-    cudaGetLastError();
-    return fail(TACCHI_ERR_OOM);
-  }
-  if (cudaMallocHost((void **)&c->h_stage, sizeof(tacchi_ctx::Stage)) != cudaSuccess ||
-      cudaMallocHost((void **)&c->h_err, sizeof(int)) != cudaSuccess)
-    return fail(TACCHI_ERR_OOM);
-  *c->h_err = 0;
-  I.frames = c->d_frames;
-
-  // initial particles (Eq. 1): lattice positions, v = 0, C = 0, F = I
-  std::vector<float> hu;
-  std::vector<uint8_t> hf;
-  try {
-    hu.resize(3 * N);
-    hf.resize(N);
-  } catch (...) {
-    return fail(TACCHI_ERR_OOM);
-  }
-  make_lattice(n[0], n[1], n[2], ps, pb, d->seed, d->jitter, hu.data(), hf.data());
-  std::vector<uint32_t> surf;
-  std::vector<float> z0;
-  for (long long p = 0; p < N; ++p)
-    if (hf[p] & 2) {
-      surf.push_back((uint32_t)p);
-      z0.push_back(hu[2 * N + p]);
-    }
-  c->Ns = (int)surf.size();
-  if (dalloc(c, &c->d_surf, surf.size()) != cudaSuccess || dalloc(c, &c->d_z0, z0.size()) != cudaSuccess)
-    return fail(TACCHI_ERR_OOM);
-
-  c->b.inst = c->d_inst;
-  c->b.node_offs = c->d_offs;
-  c->b.part_offs = c->d_offs + 1;
-  c->b.block_inst = c->d_block_inst;
-  c->b.n_inst = 1;
-  c->b.Ntot = N;
-  c->b.Nnodes = Nn;
-  c->b.Nblk = c->nblocks;
-
-  const long long zero2[2] = {0, 0};
-  cudaStream_t st = c->stream;
-  bool up = cudaMemcpy(c->b.u, hu.data(), sizeof(float) * 3 * N, cudaMemcpyHostToDevice) == cudaSuccess &&
-            cudaMemcpy((void *)c->b.flags, hf.data(), N, cudaMemcpyHostToDevice) == cudaSuccess &&
-            cudaMemcpy(c->d_surf, surf.data(), sizeof(uint32_t) * surf.size(), cudaMemcpyHostToDevice) ==
-                cudaSuccess &&
-            cudaMemcpy(c->d_z0, z0.data(), sizeof(float) * z0.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
-            cudaMemcpy(c->d_offs, zero2, sizeof(zero2), cudaMemcpyHostToDevice) == cudaSuccess &&
-            cudaMemcpy(c->d_inst, &c->inst, sizeof(Instance), cudaMemcpyHostToDevice) == cudaSuccess &&
-            cudaMemsetAsync(c->b.Fm, 0, sizeof(float) * 9 * N, st) == cudaSuccess &&
-            cudaMemsetAsync(c->b.v, 0, sizeof(float) * 3 * N, st) == cudaSuccess &&
-            cudaMemsetAsync(c->b.C, 0, sizeof(float) * 9 * N, st) == cudaSuccess &&
-            cudaMemsetAsync(c->d_block_inst, 0, sizeof(uint32_t) * c->nblocks, st) == cudaSuccess &&
-            cudaMemsetAsync(c->b.bcount, 0, sizeof(uint32_t) * c->nblocks, st) == cudaSuccess &&
-            cudaMemsetAsync(c->b.gmm, 0, sizeof(float4) * Nn, st) == cudaSuccess &&
-            cudaMemsetAsync(c->b.gv, 0, sizeof(float4) * Nn, st) == cudaSuccess &&
-            cudaMemsetAsync(c->b.err, 0, sizeof(int), st) == cudaSuccess &&
-            cudaMemsetAsync(c->b.movers, 0, sizeof(int), st) == cudaSuccess &&
-            prepare_transfer(c->blk) == cudaSuccess && launch_sort(c->b, c->blk, 1, st) == cudaSuccess &&
-            cudaStreamSynchronize(st) == cudaSuccess;
-  if (!up) {
-    cudaGetLastError();
-    return fail(TACCHI_ERR_CUDA);
-  }
-  *out = c;
-  return TACCHI_OK;
+tacchi_status tacchi_batch_create(int n, const tacchi_elastomer_desc *descs, void *stream, tacchi_handle *out) {
+  return create_batch(n, descs, stream, out);
 }
 
 void tacchi_destroy(tacchi_handle h) { release(h); }
 
-tacchi_status tacchi_info(tacchi_handle c, tacchi_info_t *o) {
-  if (!c || !o) return TACCHI_ERR_INVALID_ARG;
-  o->n_particles = c->N;
-  o->n_surface = c->Ns;
+tacchi_status tacchi_batch_size(tacchi_handle c, int *out) {
+  if (!c || !out) return TACCHI_ERR_INVALID_ARG;
+  *out = c->n_inst();
+  return TACCHI_OK;
+}
+
+tacchi_status tacchi_batch_info(tacchi_handle c, int i, tacchi_info_t *o) {
+  if (check_index(c, i) != TACCHI_OK || !o) return TACCHI_ERR_INVALID_ARG;
+  const InstHost &h = c->in[i];
+  o->n_particles = h.N;
+  o->n_surface = h.Ns;
   for (int a = 0; a < 3; ++a) {
-    o->grid[a] = c->G[a];
-    o->origin_m[a] = c->origin[a];
+    o->grid[a] = h.G[a];
+    o->origin_m[a] = h.origin[a];
   }
-  o->n_nodes = c->nodes;
-  o->dx_m = c->dx;
-  o->z_top_m = c->z_top;
+  o->n_nodes = h.nodes;
+  o->dx_m = h.dx;
+  o->z_top_m = h.z_top;
   o->block[0] = c->blk.x;
   o->block[1] = c->blk.y;
   o->block[2] = c->blk.z;
-  o->n_blocks = c->nblocks;
+  o->n_blocks = h.dev.nblocks;
   o->device_bytes = c->device_bytes;
   return TACCHI_OK;
 }
 
-tacchi_status tacchi_set_indenter(tacchi_handle c, const tacchi_indenter_desc *d, const double pose[7],
-                                  const double vel[6]) {
-  if (!c) return TACCHI_ERR_INVALID_ARG;
-  if (pose && !finite3(pose, 7)) return TACCHI_ERR_INVALID_ARG;
+tacchi_status tacchi_info(tacchi_handle c, tacchi_info_t *o) { return tacchi_batch_info(c, 0, o); }
+
+tacchi_status tacchi_batch_set_indenter(tacchi_handle c, int i, const tacchi_indenter_desc *d,
+                                        const double pose[7], const double vel[6]) {
+  if (check_index(c, i) != TACCHI_OK) return TACCHI_ERR_INVALID_ARG;
+  InstHost &h = c->in[i];
+  if (pose && !finite_all(pose, 7)) return TACCHI_ERR_INVALID_ARG;
   if (pose && !(pose[3] * pose[3] + pose[4] * pose[4] + pose[5] * pose[5] + pose[6] * pose[6] > 0))
     return TACCHI_ERR_INVALID_ARG;
-  if (vel && !finite3(vel, 6)) return TACCHI_ERR_INVALID_ARG;
+  if (vel && !finite_all(vel, 6)) return TACCHI_ERR_INVALID_ARG;
   if (d) {
-    if (d->kind < IND_NONE || d->kind > IND_HEIGHTMAP || !finite3(d->params, 8)) return TACCHI_ERR_INVALID_ARG;
+    if (d->kind < IND_NONE || d->kind > IND_HEIGHTMAP || !finite_all(d->params, 8)) return TACCHI_ERR_INVALID_ARG;
     const double *P = d->params;
     switch (d->kind) {
       case IND_SPHERE:
@@ -713,41 +828,51 @@ tacchi_status tacchi_set_indenter(tacchi_handle c, const tacchi_indenter_desc *d
         std::vector<float> cells(n);
         for (long long e = 0; e < n; ++e) {
           if (!std::isfinite(d->hm[e])) return TACCHI_ERR_INVALID_ARG;
-          cells[e] = (float)((double)d->hm[e] / c->dx);
+          cells[e] = (float)((double)d->hm[e] / h.dx);
         }
         // queued work may still read the old map: free it in stream order
-        if (c->d_hm) CK(cudaFreeAsync(c->d_hm, c->stream));
-        c->d_hm = nullptr;
-        CK(cudaMallocAsync((void **)&c->d_hm, sizeof(float) * n, c->stream));
-        CK(cudaMemcpyAsync(c->d_hm, cells.data(), sizeof(float) * n, cudaMemcpyHostToDevice, c->stream));
-        CK(cudaStreamSynchronize(c->stream));  // host vector goes out of scope
-        c->hm_w = d->hm_w;
-        c->hm_h = d->hm_h;
-        c->hm_pixel = d->hm_pixel_m;
+        if (h.d_hm) CK(cudaFreeAsync(h.d_hm, c->stream));
+        h.d_hm = nullptr;
+        CK(cudaMallocAsync((void **)&h.d_hm, sizeof(float) * n, c->stream));
+        CK(cudaMemcpyAsync(h.d_hm, cells.data(), sizeof(float) * n, cudaMemcpyHostToDevice, c->stream));
+        CK(cudaStreamSynchronize(c->stream));  // the host vector goes out of scope
+        h.hm_w = d->hm_w;
+        h.hm_h = d->hm_h;
+        h.hm_pixel = d->hm_pixel_m;
         break;
       }
       default:
         break;
     }
-    c->ind_kind = d->kind;
-    for (int e = 0; e < 8; ++e) c->ind_params[e] = P[e];
+    h.ind_kind = d->kind;
+    for (int e = 0; e < 8; ++e) h.ind_params[e] = P[e];
   }
   if (pose)
-    for (int e = 0; e < 7; ++e) c->pose[e] = pose[e];
+    for (int e = 0; e < 7; ++e) h.pose[e] = pose[e];
   if (vel)
-    for (int e = 0; e < 6; ++e) c->vel[e] = vel[e];
+    for (int e = 0; e < 6; ++e) h.vel[e] = vel[e];
+  return TACCHI_OK;
+}
+
+tacchi_status tacchi_set_indenter(tacchi_handle c, const tacchi_indenter_desc *d, const double pose[7],
+                                  const double vel[6]) {
+  return tacchi_batch_set_indenter(c, 0, d, pose, vel);
+}
+
+tacchi_status tacchi_batch_get_indenter_pose(tacchi_handle c, int i, double pose[7]) {
+  if (check_index(c, i) != TACCHI_OK || !pose) return TACCHI_ERR_INVALID_ARG;
+  for (int e = 0; e < 7; ++e) pose[e] = c->in[i].pose[e];
   return TACCHI_OK;
 }
 
 tacchi_status tacchi_get_indenter_pose(tacchi_handle c, double pose[7]) {
-  if (!c || !pose) return TACCHI_ERR_INVALID_ARG;
-  for (int e = 0; e < 7; ++e) pose[e] = c->pose[e];
-  return TACCHI_OK;
+  return tacchi_batch_get_indenter_pose(c, 0, pose);
 }
 
 tacchi_status tacchi_step(tacchi_handle c, int n_substeps, double dt) {
   if (!c || n_substeps < 1 || !(dt > 0) || !std::isfinite(dt)) return TACCHI_ERR_INVALID_ARG;
   const float fdt = (float)dt;
+  const int ni = c->n_inst();
   int left = n_substeps;
   while (left > 0) {
     const int n = std::min(left, kMaxChunk);
@@ -755,16 +880,22 @@ tacchi_status tacchi_step(tacchi_handle c, int n_substeps, double dt) {
     CK(graph_for(c, n, fdt, &ge));
     // the previous upload must have left the pinned staging buffer
     CK(cudaEventSynchronize(c->stage_done));
-    tacchi_ctx::Stage *s = c->h_stage;
-    s->inst = c->inst;
-    s->inst.shape = make_shape(c);
-    s->inst.frames = c->d_frames;
-    for (int k = 0; k < n; ++k) {
-      s->frames[k] = frame_of(c, c->pose, c->vel);
-      advance_pose(c->pose, c->vel, dt);
+    Instance *tab = reinterpret_cast<Instance *>(c->h_stage);
+    IndenterFrame *fr = reinterpret_cast<IndenterFrame *>(c->h_stage + sizeof(Instance) * (size_t)ni);
+    for (int i = 0; i < ni; ++i) {
+      InstHost &h = c->in[i];
+      tab[i] = h.dev;
+      tab[i].shape = make_shape(h);
+      tab[i].frames = c->d_frames + (size_t)i * n;  // frames packed [instance][substep]
+      IndenterFrame *f = fr + (size_t)i * n;
+      for (int k = 0; k < n; ++k) {
+        f[k] = frame_of(h, h.pose, h.vel);
+        advance_pose(h.pose, h.vel, dt);
+      }
     }
-    CK(cudaMemcpyAsync(c->d_inst, &s->inst, sizeof(Instance), cudaMemcpyHostToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->d_frames, s->frames, sizeof(IndenterFrame) * n, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_inst, tab, sizeof(Instance) * ni, cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->d_frames, fr, sizeof(IndenterFrame) * (size_t)ni * n, cudaMemcpyHostToDevice,
+                       c->stream));
     CK(cudaEventRecord(c->stage_done, c->stream));
     CK(cudaGraphLaunch(ge->exec, c->stream));
     if (ge->profiled) CK(collect_profile(c, ge));
@@ -774,9 +905,9 @@ tacchi_status tacchi_step(tacchi_handle c, int n_substeps, double dt) {
   return TACCHI_OK;
 }
 
-tacchi_status tacchi_heightmap(tacchi_handle c, int w, int h, const double window_m[4], int fill_radius,
-                               float *out) {
-  if (!c || !out) return TACCHI_ERR_INVALID_ARG;
+tacchi_status tacchi_batch_heightmap(tacchi_handle c, int i, int w, int h, const double window_m[4],
+                                     int fill_radius, float *out) {
+  if (check_index(c, i) != TACCHI_OK || !out) return TACCHI_ERR_INVALID_ARG;
   tacchi_status s = validate_window(w, h, window_m, fill_radius);
   if (s != TACCHI_OK) return s;
   const bool dev = is_device_ptr(out);
@@ -785,7 +916,7 @@ tacchi_status tacchi_heightmap(tacchi_handle c, int w, int h, const double windo
     CK(ensure(c, &c->d_hbuf, &c->hbuf_cap, (size_t)w * h));
     dst = c->d_hbuf;
   }
-  s = run_heightmap(c, w, h, window_m, fill_radius, dst);
+  s = run_heightmap(c, i, w, h, window_m, fill_radius, dst);
   if (s != TACCHI_OK) return s;
   if (!dev) {
     CK(cudaMemcpyAsync(out, dst, sizeof(float) * w * h, cudaMemcpyDeviceToHost, c->stream));
@@ -794,13 +925,19 @@ tacchi_status tacchi_heightmap(tacchi_handle c, int w, int h, const double windo
   return TACCHI_OK;
 }
 
-tacchi_status tacchi_render(tacchi_handle c, const tacchi_render_params *rp, int w, int h,
-                            const double window_m[4], int fill_radius, float *out_rgb, float *out_height) {
-  if (!c || !out_rgb) return TACCHI_ERR_INVALID_ARG;
+tacchi_status tacchi_heightmap(tacchi_handle c, int w, int h, const double window_m[4], int fill_radius,
+                               float *out) {
+  return tacchi_batch_heightmap(c, 0, w, h, window_m, fill_radius, out);
+}
+
+tacchi_status tacchi_batch_render(tacchi_handle c, int i, const tacchi_render_params *rp, int w, int h,
+                                  const double window_m[4], int fill_radius, float *out_rgb, float *out_height) {
+  if (check_index(c, i) != TACCHI_OK || !out_rgb) return TACCHI_ERR_INVALID_ARG;
   tacchi_status s = validate_window(w, h, window_m, fill_radius);
   if (s != TACCHI_OK) return s;
   ShadeArgs sa;
-  s = fill_shade_args(rp, w, h, (window_m[2] - window_m[0]) / w, (window_m[3] - window_m[1]) / h, c->z_top, &sa);
+  s = fill_shade_args(rp, w, h, (window_m[2] - window_m[0]) / w, (window_m[3] - window_m[1]) / h, c->in[i].z_top,
+                      &sa);
   if (s != TACCHI_OK) return s;
   const bool rgb_dev = is_device_ptr(out_rgb);
   const bool h_dev = out_height && is_device_ptr(out_height);
@@ -814,7 +951,7 @@ tacchi_status tacchi_render(tacchi_handle c, const tacchi_render_params *rp, int
     CK(ensure(c, &c->d_rgb, &c->rgb_cap, (size_t)w * h * 3));
     rgb = c->d_rgb;
   }
-  s = run_heightmap(c, w, h, window_m, fill_radius, H);
+  s = run_heightmap(c, i, w, h, window_m, fill_radius, H);
   if (s != TACCHI_OK) return s;
   CK(launch_shade(sa, H, rgb, c->stream));
   bool need_sync = false;
@@ -829,6 +966,11 @@ tacchi_status tacchi_render(tacchi_handle c, const tacchi_render_params *rp, int
   return need_sync ? sync_and_check(c) : TACCHI_OK;
 }
 
+tacchi_status tacchi_render(tacchi_handle c, const tacchi_render_params *rp, int w, int h,
+                            const double window_m[4], int fill_radius, float *out_rgb, float *out_height) {
+  return tacchi_batch_render(c, 0, rp, w, h, window_m, fill_radius, out_rgb, out_height);
+}
+
 tacchi_status tacchi_shade(const tacchi_render_params *rp, const float *H_dev, int w, int h, double pixel_x_m,
                            double pixel_y_m, double z_top_m, float *rgb_dev, void *stream) {
   if (!H_dev || !rgb_dev || (long long)w * h > (1ll << 28)) return TACCHI_ERR_INVALID_ARG;
@@ -839,30 +981,46 @@ tacchi_status tacchi_shade(const tacchi_render_params *rp, const float *H_dev, i
   return TACCHI_OK;
 }
 
-tacchi_status tacchi_get_state(tacchi_handle c, float *u, float *v, float *C, float *Fm, uint8_t *flags) {
-  if (!c) return TACCHI_ERR_INVALID_ARG;
-  const long long N = c->N;
+tacchi_status tacchi_batch_get_state(tacchi_handle c, int i, float *u, float *v, float *C, float *Fm,
+                                     uint8_t *flags) {
+  if (check_index(c, i) != TACCHI_OK) return TACCHI_ERR_INVALID_ARG;
+  const InstHost &h = c->in[i];
+  const long long N = h.N, T = c->Ntot, o = h.part_off;
   const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
-  if (u) CK(cudaMemcpyAsync(u, c->b.u, sizeof(float) * 3 * N, k, c->stream));
-  if (v) CK(cudaMemcpyAsync(v, c->b.v, sizeof(float) * 3 * N, k, c->stream));
-  if (C) CK(cudaMemcpyAsync(C, c->b.C, sizeof(float) * 9 * N, k, c->stream));
-  if (Fm) CK(cudaMemcpyAsync(Fm, c->b.Fm, sizeof(float) * 9 * N, k, c->stream));
-  if (flags) CK(cudaMemcpyAsync(flags, c->b.flags, N, k, c->stream));
+  for (int a = 0; a < 3; ++a) {
+    if (u) CK(cudaMemcpyAsync(u + a * N, c->b.u + a * T + o, sizeof(float) * N, k, c->stream));
+    if (v) CK(cudaMemcpyAsync(v + a * N, c->b.v + a * T + o, sizeof(float) * N, k, c->stream));
+  }
+  for (int e = 0; e < 9; ++e) {
+    if (C) CK(cudaMemcpyAsync(C + e * N, c->b.C + e * T + o, sizeof(float) * N, k, c->stream));
+    if (Fm) CK(cudaMemcpyAsync(Fm + e * N, c->b.Fm + e * T + o, sizeof(float) * N, k, c->stream));
+  }
+  if (flags) CK(cudaMemcpyAsync(flags, c->b.flags + o, N, k, c->stream));
   return sync_and_check(c);
 }
 
-tacchi_status tacchi_set_state(tacchi_handle c, const float *u, const float *v, const float *C, const float *Fm) {
-  if (!c || !u) return TACCHI_ERR_INVALID_ARG;
-  const long long N = c->N;
+tacchi_status tacchi_get_state(tacchi_handle c, float *u, float *v, float *C, float *Fm, uint8_t *flags) {
+  return tacchi_batch_get_state(c, 0, u, v, C, Fm, flags);
+}
+
+tacchi_status tacchi_batch_set_state(tacchi_handle c, int i, const float *u, const float *v, const float *C,
+                                     const float *Fm) {
+  if (check_index(c, i) != TACCHI_OK || !u) return TACCHI_ERR_INVALID_ARG;
+  const InstHost &h = c->in[i];
+  const long long N = h.N, T = c->Ntot, o = h.part_off;
   const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
   cudaStream_t st = c->stream;
-  CK(cudaMemcpyAsync(c->b.u, u, sizeof(float) * 3 * N, k, st));
-  if (v) CK(cudaMemcpyAsync(c->b.v, v, sizeof(float) * 3 * N, k, st));
-  else CK(cudaMemsetAsync(c->b.v, 0, sizeof(float) * 3 * N, st));
-  if (C) CK(cudaMemcpyAsync(c->b.C, C, sizeof(float) * 9 * N, k, st));
-  else CK(cudaMemsetAsync(c->b.C, 0, sizeof(float) * 9 * N, st));
-  if (Fm) CK(cudaMemcpyAsync(c->b.Fm, Fm, sizeof(float) * 9 * N, k, st));
-  else CK(cudaMemsetAsync(c->b.Fm, 0, sizeof(float) * 9 * N, st));
+  for (int a = 0; a < 3; ++a) {
+    CK(cudaMemcpyAsync(c->b.u + a * T + o, u + a * N, sizeof(float) * N, k, st));
+    if (v) CK(cudaMemcpyAsync(c->b.v + a * T + o, v + a * N, sizeof(float) * N, k, st));
+    else CK(cudaMemsetAsync(c->b.v + a * T + o, 0, sizeof(float) * N, st));
+  }
+  for (int e = 0; e < 9; ++e) {
+    if (C) CK(cudaMemcpyAsync(c->b.C + e * T + o, C + e * N, sizeof(float) * N, k, st));
+    else CK(cudaMemsetAsync(c->b.C + e * T + o, 0, sizeof(float) * N, st));
+    if (Fm) CK(cudaMemcpyAsync(c->b.Fm + e * T + o, Fm + e * N, sizeof(float) * N, k, st));
+    else CK(cudaMemsetAsync(c->b.Fm + e * T + o, 0, sizeof(float) * N, st));
+  }
   CK(cudaMemsetAsync(c->b.err, 0, sizeof(int), st));
   CK(launch_sort(c->b, c->blk, 1, st));
   CK(cudaMemsetAsync(c->b.movers, 0, sizeof(int), st));
@@ -870,11 +1028,88 @@ tacchi_status tacchi_set_state(tacchi_handle c, const float *u, const float *v, 
   return TACCHI_OK;
 }
 
+tacchi_status tacchi_set_state(tacchi_handle c, const float *u, const float *v, const float *C, const float *Fm) {
+  return tacchi_batch_set_state(c, 0, u, v, C, Fm);
+}
+
 tacchi_status tacchi_get_grid(tacchi_handle c, float *out) {
   if (!c || !out) return TACCHI_ERR_INVALID_ARG;
   if (!c->stepped) return TACCHI_ERR_STATE;
-  CK(cudaMemcpyAsync(out, c->b.gmm, sizeof(float4) * c->nodes, cudaMemcpyDeviceToDevice, c->stream));
+  const InstHost &h = c->in[0];
+  CK(cudaMemcpyAsync(out, c->b.gmm + h.node_off, sizeof(float4) * h.nodes, cudaMemcpyDeviceToDevice, c->stream));
   return TACCHI_OK;
+}
+
+tacchi_status tacchi_set_block(tacchi_handle c, int bx, int by, int bz) {
+  if (!c) return TACCHI_ERR_INVALID_ARG;
+  return apply_blocks(c, SortBlock{bx, by, bz});
+}
+
+tacchi_status tacchi_autotune(tacchi_handle c, int n_substeps, double dt, int best[3], double ms_per_substep[4]) {
+  if (!c || !best || n_substeps < 1 || n_substeps > kMaxChunk || !(dt > 0) || !std::isfinite(dt))
+    return TACCHI_ERR_INVALID_ARG;
+  // save the particle state and the indenter poses
+  const long long T = c->Ntot;
+  float *save = nullptr;
+  CK(cudaMalloc((void **)&save, sizeof(float) * 24 * T));
+  auto restore = [&]() -> tacchi_status {
+    CK(cudaMemcpyAsync(c->b.u, save, sizeof(float) * 3 * T, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->b.v, save + 3 * T, sizeof(float) * 3 * T, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->b.C, save + 6 * T, sizeof(float) * 9 * T, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->b.Fm, save + 15 * T, sizeof(float) * 9 * T, cudaMemcpyDeviceToDevice, c->stream));
+    CK(launch_sort(c->b, c->blk, 1, c->stream));  // the sort must match the restored positions
+    CK(cudaMemsetAsync(c->b.movers, 0, sizeof(int), c->stream));
+    CK(cudaMemsetAsync(c->b.err, 0, sizeof(int), c->stream));
+    return TACCHI_OK;
+  };
+  tacchi_status st = TACCHI_OK;
+  if (cudaMemcpyAsync(save, c->b.u, sizeof(float) * 3 * T, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(save + 3 * T, c->b.v, sizeof(float) * 3 * T, cudaMemcpyDeviceToDevice, c->stream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(save + 6 * T, c->b.C, sizeof(float) * 9 * T, cudaMemcpyDeviceToDevice, c->stream) !=
+          cudaSuccess ||
+      cudaMemcpyAsync(save + 15 * T, c->b.Fm, sizeof(float) * 9 * T, cudaMemcpyDeviceToDevice, c->stream) !=
+          cudaSuccess)
+    st = TACCHI_ERR_CUDA;
+  std::vector<std::vector<double>> poses(c->n_inst());
+  for (int i = 0; i < c->n_inst(); ++i) poses[i].assign(c->in[i].pose, c->in[i].pose + 7);
+  const bool prof = c->profiling;
+  c->profiling = false;
+  double best_ms = 1e300;
+  int best_k = -1;
+  for (int k = 0; k < 4 && st == TACCHI_OK; ++k) {
+    st = apply_blocks(c, kShapes[k]);
+    if (st != TACCHI_OK) break;
+    double ms = 0;
+    for (int rep = 0; rep < 2 && st == TACCHI_OK; ++rep) {  // the first run builds the graph
+      st = restore();
+      if (st != TACCHI_OK) break;
+      for (int i = 0; i < c->n_inst(); ++i) std::copy(poses[i].begin(), poses[i].end(), c->in[i].pose);
+      st = cuda_status(cudaStreamSynchronize(c->stream));
+      const auto t0 = std::chrono::steady_clock::now();
+      if (st == TACCHI_OK) st = tacchi_step(c, n_substeps, dt);
+      if (st == TACCHI_OK) st = sync_and_check(c);
+      ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    }
+    if (st != TACCHI_OK) break;
+    if (ms_per_substep) ms_per_substep[k] = ms / n_substeps;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best_k = k;
+    }
+  }
+  c->profiling = prof;
+  if (st == TACCHI_OK) st = restore();
+  for (int i = 0; i < c->n_inst(); ++i) std::copy(poses[i].begin(), poses[i].end(), c->in[i].pose);
+  if (st == TACCHI_OK && best_k >= 0) st = apply_blocks(c, kShapes[best_k]);
+  cudaFree(save);
+  if (st == TACCHI_OK) {
+    best[0] = c->blk.x;
+    best[1] = c->blk.y;
+    best[2] = c->blk.z;
+    c->stepped = false;
+  }
+  return st;
 }
 
 tacchi_status tacchi_set_profiling(tacchi_handle c, int on) {

@@ -209,3 +209,43 @@ def c1_indenters():
         hm = maps[name]
         out.append(("heightmap:" + name, (2e-3,), hm, float(hm.max())))
     return out
+
+
+# --------------------------------------------------------------------------
+# Batched workload: independent sensors of uneven sizes (C2).
+C2_DX = 0.25e-3
+C2_DT = 2.0e-6  # CFL about 0.27 at dx = 0.25 mm (P-wave speed 33.7 m/s)
+
+
+def c2_instances(n=256, seed_base=1000):
+    """n sensors: sides U[8, 16] mm, thickness U[2, 4] mm at dx = 0.25 mm,
+    8 particles per cell; per instance an analytic indenter (sphere,
+    cylinder, cone or prism) with random size, yaw U[0, pi), xy offset
+    U[-1, 1] mm and depth U[0.1, 1.0] mm, all from numpy's PCG64 seeded with
+    seed_base + i.  Returns [(Block, indenter dict)]."""
+    out = []
+    for i in range(n):
+        rng = np.random.default_rng(seed_base + i)
+        nx = int(round(rng.uniform(8e-3, 16e-3) / C2_DX))
+        ny = int(round(rng.uniform(8e-3, 16e-3) / C2_DX))
+        nz = int(round(rng.uniform(2e-3, 4e-3) / C2_DX))
+        blk = Block(nx, ny, nz, C2_DX, pad_side=6, pad_top=8, seed=seed_base + i)
+        kind = ["sphere", "cylinder", "cone", "prism"][int(rng.integers(4))]
+        yaw = rng.uniform(0.0, math.pi)
+        off = rng.uniform(-1e-3, 1e-3, 2)
+        depth = rng.uniform(0.1e-3, 1.0e-3)
+        if kind == "sphere":
+            params, tip = (rng.uniform(2e-3, 4e-3),), None
+            tip = params[0]
+        elif kind == "cylinder":
+            params = (rng.uniform(1e-3, 2e-3), rng.uniform(2e-3, 4e-3))
+            tip = params[0]
+        elif kind == "cone":
+            params, tip = (math.radians(rng.uniform(25.0, 45.0)), 3e-3), 0.0
+        else:
+            params, tip = (math.radians(rng.uniform(30.0, 60.0)), rng.uniform(1.5e-3, 3e-3), 3e-3), 0.0
+        z_top = nz * C2_DX
+        pose = (nx * C2_DX / 2 + off[0], ny * C2_DX / 2 + off[1], z_top + tip,
+                math.cos(yaw / 2), 0.0, 0.0, math.sin(yaw / 2))
+        out.append((blk, dict(kind=kind, params=params, pose=pose, depth=depth)))
+    return out
