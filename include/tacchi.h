@@ -320,6 +320,46 @@ tacchi_status tacchi_set_block(tacchi_handle h, int bx, int by, int bz);
 tacchi_status tacchi_autotune(tacchi_handle h, int n_substeps, double dt, int best[3],
                               double ms_per_substep[4]);
 
+/* ---- Learned surrogate ------------------------------------------------------
+ * A U-Net that maps per-pixel inputs (the indenter's penetration map over the
+ * top face and the press depth) to per-pixel outputs (the top-surface
+ * displacement), trained and run by the library's BF16 tensor-core kernels
+ * with FP32 accumulation.  The paper has no surrogate; the MPM above stays
+ * the reference and the fallback.
+ * Architecture: encoder levels l = 0..levels-1 of width widths[l] with two
+ * 3x3 conv+ReLU and 2x2 average pooling between levels; decoder levels with
+ * nearest 2x upsampling, concatenation with the encoder output of the same
+ * level and two 3x3 conv+ReLU; a 1x1 head.  Loss: mean squared error.
+ * Parameters (FP32, host order): for each 3x3 conv in execution order
+ * (enc0a, enc0b, ..., enc{L-1}b, dec{L-2}a, dec{L-2}b, ..., dec0b) the
+ * weights [3][3][c_in][c_out] then the bias [c_out]; then the head
+ * [widths[0]][out_channels] and its bias. */
+typedef struct tacchi_nn *tacchi_nn_handle;
+
+/* Create a network for height x width images (multiples of 2^(levels-1)),
+ * in_channels <= 32, out_channels <= 16, widths multiples of 32, at most
+ * max_batch images per call; weights He-normal from splitmix64(seed).
+ * stream: cudaStream_t for all its work.  Errors: INVALID_ARG, OOM, CUDA. */
+tacchi_status tacchi_nn_create(int levels, const int *widths, int in_channels, int out_channels, int height,
+                               int width, int max_batch, uint64_t seed, void *stream, tacchi_nn_handle *out);
+void tacchi_nn_destroy(tacchi_nn_handle n);
+tacchi_status tacchi_nn_num_params(tacchi_nn_handle n, int64_t *out);
+/* Copy the parameters (which = 0) or the last gradients (which = 1) to host
+ * memory (float [num_params]), or set the parameters (resets Adam). */
+tacchi_status tacchi_nn_get_params(tacchi_nn_handle n, int which, float *host);
+tacchi_status tacchi_nn_set_params(tacchi_nn_handle n, const float *host);
+/* y_dev (dev, float [batch][height][width][out_channels]) = network(x_dev),
+ * x_dev (dev, float [batch][height][width][in_channels]).  Asynchronous. */
+tacchi_status tacchi_nn_forward(tacchi_nn_handle n, int batch, const float *x_dev, float *y_dev);
+/* Forward and backward: the gradients of the mean squared error against
+ * target_dev (layout of y); loss_host (optional) receives the loss. */
+tacchi_status tacchi_nn_gradients(tacchi_nn_handle n, int batch, const float *x_dev, const float *target_dev,
+                                  float *loss_host);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8) at learning rate lr on
+ * that loss.  loss_host (optional) receives the loss before the step. */
+tacchi_status tacchi_nn_train_step(tacchi_nn_handle n, int batch, const float *x_dev, const float *target_dev,
+                                   float lr, float *loss_host);
+
 /* Short English description of a status. */
 const char *tacchi_status_string(tacchi_status s);
 

@@ -386,3 +386,73 @@ class TacchiBatch:
         check(lib().tacchi_batch_set_state(self._h, i, ptr(tu), ptr(tv), ptr(tC), ptr(tF)),
               "tacchi_batch_set_state")
         check(lib().tacchi_sync(self._h), "tacchi_batch_set_state")
+
+
+class SurrogateNet:
+    """The learned surrogate (a tacchi_nn handle): U-Net trained and run by
+    the library's BF16 tensor-core kernels; inputs/outputs are FP32 NHWC
+    device tensors."""
+
+    def __init__(self, widths=(32, 64, 128, 256), in_channels=2, out_channels=3, size=64,
+                 max_batch=256, seed=0, stream=None):
+        torch = _torch()
+        self._torch = torch
+        self.widths = tuple(widths)
+        self.cin, self.cout, self.size, self.max_batch = in_channels, out_channels, size, max_batch
+        self._stream = stream if stream is not None else torch.cuda.current_stream()
+        w = (C.c_int * len(widths))(*widths)
+        h = C.c_void_p()
+        self._h = None
+        check(lib().tacchi_nn_create(len(widths), w, in_channels, out_channels, size, size, max_batch,
+                                     seed, C.c_void_p(self._stream.cuda_stream), C.byref(h)),
+              "tacchi_nn_create")
+        self._h = h
+        n = C.c_int64()
+        check(lib().tacchi_nn_num_params(self._h, C.byref(n)), "tacchi_nn_num_params")
+        self.num_params = int(n.value)
+        self.device = torch.device("cuda", torch.cuda.current_device())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().tacchi_nn_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self, grads=False):
+        out = np.zeros(self.num_params, np.float32)
+        check(lib().tacchi_nn_get_params(self._h, int(bool(grads)), out.ctypes.data_as(C.POINTER(C.c_float))),
+              "tacchi_nn_get_params")
+        return out
+
+    def set_params(self, vec):
+        v = np.ascontiguousarray(vec, np.float32)
+        assert v.size == self.num_params
+        check(lib().tacchi_nn_set_params(self._h, v.ctypes.data_as(C.POINTER(C.c_float))), "tacchi_nn_set_params")
+
+    def _dev(self, t):
+        return self._torch.as_tensor(t, dtype=self._torch.float32, device=self.device).contiguous()
+
+    def forward(self, x, out=None):
+        x = self._dev(x)
+        b = x.shape[0]
+        out = out if out is not None else self._torch.empty((b, self.size, self.size, self.cout), device=self.device)
+        check(lib().tacchi_nn_forward(self._h, b, ptr(x), ptr(out)), "tacchi_nn_forward")
+        return out
+
+    def gradients(self, x, target):
+        x, t = self._dev(x), self._dev(target)
+        loss = C.c_float()
+        check(lib().tacchi_nn_gradients(self._h, x.shape[0], ptr(x), ptr(t), C.byref(loss)), "tacchi_nn_gradients")
+        return float(loss.value)
+
+    def train_step(self, x, target, lr, want_loss=True):
+        x, t = self._dev(x), self._dev(target)
+        loss = C.c_float()
+        check(lib().tacchi_nn_train_step(self._h, x.shape[0], ptr(x), ptr(t), float(lr),
+                                         C.byref(loss) if want_loss else None), "tacchi_nn_train_step")
+        return float(loss.value) if want_loss else None

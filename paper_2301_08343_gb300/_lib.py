@@ -95,6 +95,15 @@ EXTRA_SIGNATURES = {
     "tacchi_batch_set_state": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp]),
     "tacchi_set_block": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int]),
     "tacchi_autotune": (C.c_int, [_vp, C.c_int, C.c_double, C.POINTER(C.c_int), _dp]),
+    "tacchi_nn_create": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
+                                   C.c_uint64, _vp, C.POINTER(_vp)]),
+    "tacchi_nn_destroy": (None, [_vp]),
+    "tacchi_nn_num_params": (C.c_int, [_vp, C.POINTER(C.c_int64)]),
+    "tacchi_nn_get_params": (C.c_int, [_vp, C.c_int, _fp]),
+    "tacchi_nn_set_params": (C.c_int, [_vp, _fp]),
+    "tacchi_nn_forward": (C.c_int, [_vp, C.c_int, _vp, _vp]),
+    "tacchi_nn_gradients": (C.c_int, [_vp, C.c_int, _vp, _vp, C.POINTER(C.c_float)]),
+    "tacchi_nn_train_step": (C.c_int, [_vp, C.c_int, _vp, _vp, C.c_float, C.POINTER(C.c_float)]),
     "tacchi_heightmap_static": (C.c_int, [_vp, C.c_int64, _vp, _vp, C.c_int, C.c_double, _dp,
                                           C.c_double, C.c_int, C.c_int, _dp, C.c_int, _vp, _vp]),
 }

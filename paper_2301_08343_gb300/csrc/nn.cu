@@ -1,0 +1,922 @@
+// nn.cu -- the learned surrogate: a U-Net trained and run with hand-written
+// BF16 tensor-core kernels (FP32 accumulation) on sm_103a.
+//
+// The paper has no surrogate; it is this library's addition: a network that
+// maps the indenter's penetration map over the top face (and the depth) to
+// the top-surface displacement field that the MPM would produce.
+//
+// Network (NHWC activations in BF16, parameters in FP32 with BF16 copies):
+//   encoder levels l = 0..L-1: conv3x3+ReLU, conv3x3+ReLU, 2x2 average pool
+//   (not after the last level); decoder levels l = L-2..0: nearest 2x
+//   upsampling, concatenation [upsampled, skip], conv3x3+ReLU twice; head:
+//   1x1 convolution to the output channels (FP32).  Loss: mean squared error.
+//
+// Kernels:
+//   k_conv3x3      implicit-GEMM 3x3 convolution, rows = pixels, columns =
+//                  output channels, K = 9 x C_in; mma.sync m16n8k16 BF16 with
+//                  FP32 accumulators, cp.async double buffering, bias+ReLU
+//                  epilogue.  The data gradient runs the same kernel on the
+//                  output gradient with the weights flipped and transposed.
+//   k_conv3x3_wgrad  weight gradient: rows = (tap, C_in), columns = C_out,
+//                  K = pixels, split over pixel chunks with FP32 atomics.
+//   elementwise kernels for ReLU masks, pooling, upsampling, concatenation,
+//   bias gradients, the 1x1 head, the loss and Adam.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "tacchi.h"
+
+namespace {
+
+using bf16 = __nv_bfloat16;
+
+// ---------------------------------------------------------------------------
+// PTX helpers
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool valid) {
+  const int sz = valid ? 16 : 0;  // 0: fill the 16 bytes with zeros
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_addr(smem)), "l"(gmem), "r"(sz));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+__device__ __forceinline__ void ldsm_x4(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3, const void *p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(smem_addr(p)));
+}
+__device__ __forceinline__ void ldsm_x4_t(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3, const void *p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(smem_addr(p)));
+}
+// D = A (16x16, row) * B (16x8, col) + D, BF16 inputs, FP32 accumulators
+__device__ __forceinline__ void mma_bf16(float d[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// ---------------------------------------------------------------------------
+// Y[m][co] = act(b[co] + sum_k A[m][k] Wt[k][co]); A[m][k] = X at pixel m
+// shifted by tap(k), channel ci(k); k = tap * Cin + ci, tap = 3 dy + dx.
+// Requires Cin % 32 == 0 and Cout % BN == 0.
+template <int BN>
+__global__ void __launch_bounds__((BN / 32) * 4 * 32) k_conv3x3(const bf16 *__restrict__ X, const bf16 *__restrict__ Wt,
+                                                              const float *__restrict__ bias, bf16 *__restrict__ Y,
+                                                              int nimg, int H, int W, int Cin, int Cout, int relu) {
+  constexpr int BM = 128, BK = 32, WARPS_M = 4, THREADS = (BN / 32) * WARPS_M * 32;
+  constexpr int AS = BK + 8, BS = BN + 8;
+  __shared__ __align__(16) bf16 sA[2][BM * AS];
+  __shared__ __align__(16) bf16 sB[2][BK * BS];
+  const int M = nimg * H * W;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+  const int nk = 9 * Cin / BK;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = warp % WARPS_M, wn = warp / WARPS_M;
+
+  auto load_stage = [&](int kk, int buf) {
+    const int k0 = kk * BK;
+    const int tap = k0 / Cin, ci0 = k0 % Cin;
+    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+    for (int c = tid; c < BM * 4; c += THREADS) {
+      const int r = c >> 2, part = c & 3;
+      const int m = m0 + r;
+      bool valid = false;
+      const bf16 *src = X;
+      if (m < M) {
+        const int x = m % W, y = (m / W) % H, n = m / (W * H);
+        const int ys = y + dy, xs = x + dx;
+        if (ys >= 0 && ys < H && xs >= 0 && xs < W) {
+          valid = true;
+          src = X + (((long long)n * H + ys) * W + xs) * Cin + ci0 + part * 8;
+        }
+      }
+      cp_async16(&sA[buf][r * AS + part * 8], src, valid);
+    }
+    for (int c = tid; c < BK * (BN / 8); c += THREADS) {
+      const int r = c / (BN / 8), part = c % (BN / 8);
+      cp_async16(&sB[buf][r * BS + part * 8], Wt + (long long)(k0 + r) * Cout + n0 + part * 8, true);
+    }
+    cp_async_commit();
+  };
+
+  float acc[2][4][4];
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+
+  load_stage(0, 0);
+  for (int kk = 0; kk < nk; ++kk) {
+    if (kk + 1 < nk) {
+      load_stage(kk + 1, (kk + 1) & 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const bf16 *a = sA[kk & 1];
+    const bf16 *b = sB[kk & 1];
+#pragma unroll
+    for (int ks = 0; ks < BK; ks += 16) {
+      uint32_t af[2][4], bfr[4][2];
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+        ldsm_x4(af[i][0], af[i][1], af[i][2], af[i][3],
+                a + (wm * 32 + i * 16 + (lane & 15)) * AS + ks + (lane >> 4) * 8);
+#pragma unroll
+      for (int j = 0; j < 4; j += 2)
+        ldsm_x4_t(bfr[j][0], bfr[j][1], bfr[j + 1][0], bfr[j + 1][1],
+                  b + (ks + (lane & 7) + ((lane >> 3) & 1) * 8) * BS + wn * 32 + j * 8 + (lane >> 4) * 8);
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bfr[j][0], bfr[j][1]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = n0 + wn * 32 + j * 8 + (lane & 3) * 2;
+      const float b0 = bias ? bias[c] : 0.f, b1 = bias ? bias[c + 1] : 0.f;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int r = m0 + wm * 32 + i * 16 + (lane >> 2) + h * 8;
+        if (r >= M) continue;
+        float v0 = acc[i][j][2 * h] + b0, v1 = acc[i][j][2 * h + 1] + b1;
+        if (relu) {
+          v0 = fmaxf(v0, 0.f);
+          v1 = fmaxf(v1, 0.f);
+        }
+        *reinterpret_cast<__nv_bfloat162 *>(Y + (long long)r * Cout + c) = __floats2bfloat162_rn(v0, v1);
+      }
+    }
+}
+
+// dW[tap*Cin + ci][co] += sum over a chunk of pixels of X(shifted)[ci] * G[co].
+template <int BN>
+__global__ void __launch_bounds__((BN / 16) * 32) k_conv3x3_wgrad(const bf16 *__restrict__ X, const bf16 *__restrict__ G,
+                                                                float *__restrict__ dW, int nimg, int H, int W, int Cin,
+                                                                int Cout, int chunk) {
+  constexpr int BMk = 32, BKp = 32, THREADS = (BN / 16) * 32;
+  constexpr int XS = BMk + 8, GS = BN + 8;
+  __shared__ __align__(16) bf16 sX[2][BKp * XS];
+  __shared__ __align__(16) bf16 sG[2][BKp * GS];
+  const int M = nimg * H * W;
+  const int kblk = blockIdx.x;  // (tap, 32-channel block)
+  const int tap = (kblk * BMk) / Cin, ci0 = (kblk * BMk) % Cin;
+  const int dy = tap / 3 - 1, dx = tap % 3 - 1;
+  const int n0 = blockIdx.y * BN;
+  const int p_begin = blockIdx.z * chunk;
+  const int p_end = min(M, p_begin + chunk);
+  if (p_begin >= p_end) return;
+  const int nsteps = (p_end - p_begin + BKp - 1) / BKp;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+  auto load_stage = [&](int s, int buf) {
+    const int p0 = p_begin + s * BKp;
+    for (int c = tid; c < BKp * 4; c += THREADS) {
+      const int r = c >> 2, part = c & 3;
+      const int m = p0 + r;
+      bool valid = false;
+      const bf16 *src = X;
+      if (m < p_end) {
+        const int x = m % W, y = (m / W) % H, n = m / (W * H);
+        const int ys = y + dy, xs = x + dx;
+        if (ys >= 0 && ys < H && xs >= 0 && xs < W) {
+          valid = true;
+          src = X + (((long long)n * H + ys) * W + xs) * Cin + ci0 + part * 8;
+        }
+      }
+      cp_async16(&sX[buf][r * XS + part * 8], src, valid);
+    }
+    for (int c = tid; c < BKp * (BN / 8); c += THREADS) {
+      const int r = c / (BN / 8), part = c % (BN / 8);
+      const int m = p0 + r;
+      const bool valid = m < p_end;
+      cp_async16(&sG[buf][r * GS + part * 8], valid ? G + (long long)m * Cout + n0 + part * 8 : G, valid);
+    }
+    cp_async_commit();
+  };
+
+  float acc[2][2][4];  // [m16 tile (channels)][n8 tile][4]
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
+
+  load_stage(0, 0);
+  for (int s = 0; s < nsteps; ++s) {
+    if (s + 1 < nsteps) {
+      load_stage(s + 1, (s + 1) & 1);
+      cp_async_wait<1>();
+    } else {
+      cp_async_wait<0>();
+    }
+    __syncthreads();
+    const bf16 *xs_ = sX[s & 1];
+    const bf16 *gs_ = sG[s & 1];
+#pragma unroll
+    for (int ks = 0; ks < BKp; ks += 16) {
+      uint32_t af[2][4], bfr[2][2];
+      // A' = X^T (channels x pixels): transposed 8x8 loads of sX [pixel][ch]
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+        ldsm_x4_t(af[i][0], af[i][1], af[i][2], af[i][3],
+                  xs_ + (ks + (lane & 7) + ((lane >> 4) & 1) * 8) * XS + i * 16 + ((lane >> 3) & 1) * 8);
+      ldsm_x4_t(bfr[0][0], bfr[0][1], bfr[1][0], bfr[1][1],
+                gs_ + (ks + (lane & 7) + ((lane >> 3) & 1) * 8) * GS + warp * 16 + (lane >> 4) * 8);
+#pragma unroll
+      for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < 2; ++j) mma_bf16(acc[i][j], af[i], bfr[j][0], bfr[j][1]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const int c = n0 + warp * 16 + j * 8 + (lane & 3) * 2;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int r = tap * Cin + ci0 + i * 16 + (lane >> 2) + h * 8;
+        atomicAdd(dW + (long long)r * Cout + c, acc[i][j][2 * h]);
+        atomicAdd(dW + (long long)r * Cout + c + 1, acc[i][j][2 * h + 1]);
+      }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// elementwise kernels (grid-stride)
+#define GRID_STRIDE(i, n) for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (n); \
+                               i += (long long)gridDim.x * blockDim.x)
+
+// x fp32 [P][cin] -> bf16 [P][cpad] (zero padded channels)
+__global__ void k_pack_input(const float *x, bf16 *y, long long P, int cin, int cpad) {
+  GRID_STRIDE(e, P * cpad) {
+    const long long p = e / cpad;
+    const int c = (int)(e % cpad);
+    y[e] = __float2bfloat16_rn(c < cin ? x[p * cin + c] : 0.f);
+  }
+}
+// g = g * (y > 0)
+__global__ void k_relu_mask(bf16 *g, const bf16 *y, long long n) {
+  GRID_STRIDE(e, n) {
+    if (!(__bfloat162float(y[e]) > 0.f)) g[e] = __float2bfloat16_rn(0.f);
+  }
+}
+__global__ void k_avgpool(const bf16 *x, bf16 *y, int nimg, int H, int W, int C) {
+  const int Ho = H / 2, Wo = W / 2;
+  GRID_STRIDE(e, (long long)nimg * Ho * Wo * C) {
+    const int c = (int)(e % C);
+    long long p = e / C;
+    const int xo = (int)(p % Wo), yo = (int)((p / Wo) % Ho);
+    const long long n = p / ((long long)Wo * Ho);
+    const long long b = ((n * H + 2 * yo) * W + 2 * xo) * C + c;
+    const float s = __bfloat162float(x[b]) + __bfloat162float(x[b + C]) + __bfloat162float(x[b + (long long)W * C]) +
+                    __bfloat162float(x[b + (long long)W * C + C]);
+    y[e] = __float2bfloat16_rn(0.25f * s);
+  }
+}
+// gradient of avgpool, added into gx (which already holds the skip gradient)
+__global__ void k_avgpool_bwd_add(const bf16 *gy, bf16 *gx, int nimg, int H, int W, int C) {
+  const int Ho = H / 2, Wo = W / 2;
+  GRID_STRIDE(e, (long long)nimg * H * W * C) {
+    const int c = (int)(e % C);
+    long long p = e / C;
+    const int x = (int)(p % W), y = (int)((p / W) % H);
+    const long long n = p / ((long long)W * H);
+    const float g = 0.25f * __bfloat162float(gy[((n * Ho + y / 2) * Wo + x / 2) * C + c]);
+    gx[e] = __float2bfloat16_rn(__bfloat162float(gx[e]) + g);
+  }
+}
+// out [n][2H][2W][C1 + C2] = [upsample(a) (C1) | skip (C2)]
+__global__ void k_upsample_concat(const bf16 *a, const bf16 *skip, bf16 *out, int nimg, int H, int W, int C1, int C2) {
+  const int Ho = 2 * H, Wo = 2 * W, C = C1 + C2;
+  GRID_STRIDE(e, (long long)nimg * Ho * Wo * C) {
+    const int c = (int)(e % C);
+    long long p = e / C;
+    const int x = (int)(p % Wo), y = (int)((p / Wo) % Ho);
+    const long long n = p / ((long long)Wo * Ho);
+    out[e] = c < C1 ? a[((n * H + y / 2) * W + x / 2) * C1 + c] : skip[((n * Ho + y) * Wo + x) * C2 + (c - C1)];
+  }
+}
+// split the gradient of the concatenation: ga = upsample^T of the first C1
+// channels (H x W output), gs = the remaining C2 channels
+__global__ void k_upsample_concat_bwd(const bf16 *g, bf16 *ga, bf16 *gs, int nimg, int H, int W, int C1, int C2) {
+  const int Ho = 2 * H, Wo = 2 * W, C = C1 + C2;
+  GRID_STRIDE(e, (long long)nimg * H * W * C1) {
+    const int c = (int)(e % C1);
+    long long p = e / C1;
+    const int x = (int)(p % W), y = (int)((p / W) % H);
+    const long long n = p / ((long long)W * H);
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+      s += __bfloat162float(g[((n * Ho + 2 * y + (q >> 1)) * Wo + 2 * x + (q & 1)) * C + c]);
+    ga[e] = __float2bfloat16_rn(s);
+  }
+  GRID_STRIDE(e2, (long long)nimg * Ho * Wo * C2) {
+    const int c = (int)(e2 % C2);
+    const long long p = e2 / C2;
+    gs[e2] = g[p * C + C1 + c];
+  }
+}
+// db[c] += sum over pixels of g[p][c]
+__global__ void k_bias_grad(const bf16 *g, float *db, long long P, int C) {
+  extern __shared__ float red[];
+  const int c = threadIdx.x % C, lanes = blockDim.x / C;
+  const int r = threadIdx.x / C;
+  float s = 0.f;
+  if (r < lanes)
+    for (long long p = blockIdx.x * (long long)lanes + r; p < P; p += (long long)gridDim.x * lanes)
+      s += __bfloat162float(g[p * C + c]);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  if (threadIdx.x < C) {
+    float t = 0.f;
+    for (int q = 0; q < lanes; ++q) t += red[q * C + threadIdx.x];
+    atomicAdd(db + threadIdx.x, t);
+  }
+}
+// head: y[p][o] = b[o] + sum_i W[i][o] x[p][i] (FP32 out)
+__global__ void k_head_fwd(const bf16 *x, const float *Wh, const float *bh, float *y, long long P, int Ci, int Co) {
+  GRID_STRIDE(e, P * Co) {
+    const long long p = e / Co;
+    const int o = (int)(e % Co);
+    float s = bh[o];
+    for (int i = 0; i < Ci; ++i) s += Wh[i * Co + o] * __bfloat162float(x[p * Ci + i]);
+    y[e] = s;
+  }
+}
+// loss: sum of squared errors (atomic) and gy = 2 (y - t) / count
+__global__ void k_mse(const float *y, const float *t, float *gy, long long n, float *loss_sum) {
+  float s = 0.f;
+  const float sc = 2.0f / (float)n;
+  GRID_STRIDE(e, n) {
+    const float d = y[e] - t[e];
+    s += d * d;
+    gy[e] = sc * d;
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss_sum, s);
+}
+// head backward: gx[p][i] = sum_o W[i][o] gy[p][o] (bf16); dW, db summed in
+// registers (every thread keeps one input channel i, since the total thread
+// count is a multiple of Ci), then per block, then atomically.
+__global__ void k_head_bwd(const bf16 *x, const float *gy, const float *Wh, bf16 *gx, float *dWh, float *dbh,
+                           long long P, int Ci, int Co) {
+  extern __shared__ float part[];  // [Ci * Co + Co]
+  for (int t = threadIdx.x; t < Ci * Co + Co; t += blockDim.x) part[t] = 0.f;
+  __syncthreads();
+  float aw[16], ab[16];
+#pragma unroll
+  for (int o = 0; o < 16; ++o) aw[o] = ab[o] = 0.f;
+  const int i = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) % Ci);
+  GRID_STRIDE(e, P * Ci) {
+    const long long p = e / Ci;
+    const float xv = __bfloat162float(x[e]);
+    float s = 0.f;
+#pragma unroll
+    for (int o = 0; o < 16; ++o) {
+      if (o < Co) {
+        const float g = gy[p * Co + o];
+        s += Wh[i * Co + o] * g;
+        aw[o] += xv * g;
+        ab[o] += g;
+      }
+    }
+    gx[e] = __float2bfloat16_rn(s);
+  }
+#pragma unroll
+  for (int o = 0; o < 16; ++o) {
+    if (o < Co) {
+      atomicAdd(&part[i * Co + o], aw[o]);
+      if (i == 0) atomicAdd(&part[Ci * Co + o], ab[o]);
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < Ci * Co; t += blockDim.x) atomicAdd(dWh + t, part[t]);
+  for (int t = threadIdx.x; t < Co; t += blockDim.x) atomicAdd(dbh + t, part[Ci * Co + t]);
+}
+// Adam (Kingma & Ba) on FP32 parameters; bias corrections c1 = 1 - b1^t,
+// c2 = 1 - b2^t passed in
+__global__ void k_adam(float *p, const float *g, float *m, float *v, long long n, float lr, float b1, float b2,
+                       float eps, float c1, float c2) {
+  GRID_STRIDE(e, n) {
+    const float ge = g[e];
+    const float mn = b1 * m[e] + (1.f - b1) * ge;
+    const float vn = b2 * v[e] + (1.f - b2) * ge * ge;
+    m[e] = mn;
+    v[e] = vn;
+    p[e] -= lr * (mn / c1) / (sqrtf(vn / c2) + eps);
+  }
+}
+// BF16 copies of a conv layer's weights: forward [tap][ci][co] (same order as
+// the FP32 master) and data-gradient [tap'][co][ci] with tap' = 8 - tap.
+__global__ void k_weights_bf16(const float *w, bf16 *wf, bf16 *wd, int Cin_real, int Cin, int Cout) {
+  GRID_STRIDE(e, 9LL * Cin * Cout) {
+    const int co = (int)(e % Cout);
+    const int ci = (int)((e / Cout) % Cin);
+    const int tap = (int)(e / ((long long)Cout * Cin));
+    const float val = ci < Cin_real ? w[((long long)tap * Cin_real + ci) * Cout + co] : 0.f;
+    const bf16 b = __float2bfloat16_rn(val);
+    wf[e] = b;
+    wd[((long long)(8 - tap) * Cout + co) * Cin + ci] = b;
+  }
+}
+// gradient of the padded first layer back to the real input channels
+__global__ void k_unpad_wgrad(const float *gpad, float *g, int Cin_real, int Cin, int Cout) {
+  GRID_STRIDE(e, 9LL * Cin_real * Cout) {
+    const int co = (int)(e % Cout);
+    const int ci = (int)((e / Cout) % Cin_real);
+    const int tap = (int)(e / ((long long)Cout * Cin_real));
+    g[e] = gpad[((long long)tap * Cin + ci) * Cout + co];
+  }
+}
+
+unsigned grid_for(long long n, int threads = 256) {
+  long long b = (n + threads - 1) / threads;
+  return (unsigned)(b < 1 ? 1 : (b > 65535 * 8 ? 65535 * 8 : b));
+}
+
+}  // namespace
+
+// ===========================================================================
+// Host-side network object.
+struct ConvLayer {
+  int cin_real, cin, cout;
+  long long w_off, b_off;    // in the FP32 parameter vector
+  long long wpad_elems;      // 9 * cin * cout
+  bf16 *wf = nullptr, *wd = nullptr;
+  float *dwpad = nullptr;    // FP32 weight gradient in padded layout (first layer)
+};
+
+struct tacchi_nn {
+  cudaStream_t stream = nullptr;
+  int L = 0;
+  std::vector<int> widths;
+  int cin_real = 0, cin = 0, cout = 0, H = 0, W = 0, max_batch = 0;
+  std::vector<ConvLayer> convs;  // execution order (enc0a, enc0b, ..., dec0b)
+  long long head_w = 0, head_b = 0, nparams = 0;
+  float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;  // FP32 params, grads, Adam moments
+  int t = 0;
+  // activations (bf16) and their gradients, per conv layer input/output
+  std::vector<bf16 *> act;    // act[0] = packed input; act[k+1] = output of conv k
+  std::vector<bf16 *> gact;   // gradients, same shapes
+  std::vector<long long> act_elems;
+  std::vector<int> act_h, act_c;
+  std::vector<bf16 *> pooled, gpooled;  // per encoder level < L-1
+  std::vector<bf16 *> cat, gcat, gup;   // per decoder level
+  float *out = nullptr, *gout = nullptr, *loss = nullptr, *h_loss = nullptr;
+  size_t device_bytes = 0;
+};
+
+namespace {
+
+template <typename T>
+cudaError_t nalloc(tacchi_nn *n, T **ptr, size_t count) {
+  cudaError_t e = cudaMalloc((void **)ptr, sizeof(T) * std::max<size_t>(count, 1));
+  if (e == cudaSuccess) n->device_bytes += sizeof(T) * count;
+  return e;
+}
+
+tacchi_status st_of(cudaError_t e) { return e == cudaSuccess ? TACCHI_OK : TACCHI_ERR_CUDA; }
+#define NCK(x)                                 \
+  do {                                         \
+    cudaError_t e_ = (x);                      \
+    if (e_ != cudaSuccess) return st_of(e_);   \
+  } while (0)
+
+cudaError_t conv_fwd(const bf16 *X, const bf16 *Wt, const float *bias, bf16 *Y, int nimg, int H, int W, int Cin,
+                     int Cout, int relu, cudaStream_t s) {
+  const int M = nimg * H * W;
+  if (Cout % 64 == 0) {
+    dim3 grid((M + 127) / 128, Cout / 64);
+    k_conv3x3<64><<<grid, 256, 0, s>>>(X, Wt, bias, Y, nimg, H, W, Cin, Cout, relu);
+  } else {
+    dim3 grid((M + 127) / 128, Cout / 32);
+    k_conv3x3<32><<<grid, 128, 0, s>>>(X, Wt, bias, Y, nimg, H, W, Cin, Cout, relu);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t conv_wgrad(const bf16 *X, const bf16 *G, float *dW, int nimg, int H, int W, int Cin, int Cout,
+                       cudaStream_t s) {
+  const int M = nimg * H * W;
+  const int kblocks = 9 * Cin / 32;
+  const int nb = Cout % 64 == 0 ? Cout / 64 : Cout / 32;
+  // enough pixel chunks to give the GPU about 2048 CTAs
+  long long want = 2048 / std::max(1, kblocks * nb);
+  if (want < 1) want = 1;
+  int chunk = (int)((M + want - 1) / want);
+  chunk = ((chunk + 31) / 32) * 32;
+  if (chunk < 256) chunk = 256;
+  dim3 grid(kblocks, nb, (M + chunk - 1) / chunk);
+  if (Cout % 64 == 0)
+    k_conv3x3_wgrad<64><<<grid, 128, 0, s>>>(X, G, dW, nimg, H, W, Cin, Cout, chunk);
+  else
+    k_conv3x3_wgrad<32><<<grid, 64, 0, s>>>(X, G, dW, nimg, H, W, Cin, Cout, chunk);
+  return cudaGetLastError();
+}
+
+cudaError_t bias_grad(const bf16 *G, float *db, long long P, int C, cudaStream_t s) {
+  const int lanes = 256 / C > 0 ? 256 / C : 1;
+  const int threads = lanes * C;
+  k_bias_grad<<<512, threads, threads * sizeof(float), s>>>(G, db, P, C);
+  return cudaGetLastError();
+}
+
+cudaError_t refresh_weights(tacchi_nn *n) {
+  for (auto &cl : n->convs) {
+    k_weights_bf16<<<grid_for(cl.wpad_elems), 256, 0, n->stream>>>(n->p + cl.w_off, cl.wf, cl.wd, cl.cin_real,
+                                                                   cl.cin, cl.cout);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+void release_nn(tacchi_nn *n) {
+  if (!n) return;
+  if (n->stream) cudaStreamSynchronize(n->stream);
+  for (auto &cl : n->convs) {
+    cudaFree(cl.wf);
+    cudaFree(cl.wd);
+    cudaFree(cl.dwpad);
+  }
+  for (auto *q : n->act) cudaFree(q);
+  for (auto *q : n->gact) cudaFree(q);
+  for (auto *q : n->pooled) cudaFree(q);
+  for (auto *q : n->gpooled) cudaFree(q);
+  for (auto *q : n->cat) cudaFree(q);
+  for (auto *q : n->gcat) cudaFree(q);
+  for (auto *q : n->gup) cudaFree(q);
+  cudaFree(n->p);
+  cudaFree(n->g);
+  cudaFree(n->m);
+  cudaFree(n->v);
+  cudaFree(n->out);
+  cudaFree(n->gout);
+  cudaFree(n->loss);
+  if (n->h_loss) cudaFreeHost(n->h_loss);
+  delete n;
+}
+
+// Forward pass for `batch` images; x fp32 [batch][H][W][cin_real] (device).
+tacchi_status forward(tacchi_nn *n, int batch, const float *x) {
+  cudaStream_t s = n->stream;
+  const long long P0 = (long long)batch * n->H * n->W;
+  k_pack_input<<<grid_for(P0 * n->cin), 256, 0, s>>>(x, n->act[0], P0, n->cin_real, n->cin);
+  NCK(cudaGetLastError());
+  int k = 0;
+  int H = n->H, W = n->W;
+  const bf16 *in = n->act[0];
+  for (int l = 0; l < n->L; ++l) {
+    for (int q = 0; q < 2; ++q, ++k) {
+      ConvLayer &cl = n->convs[k];
+      NCK(conv_fwd(in, cl.wf, n->p + cl.b_off, n->act[k + 1], batch, H, W, cl.cin, cl.cout, 1, s));
+      in = n->act[k + 1];
+    }
+    if (l < n->L - 1) {
+      k_avgpool<<<grid_for((long long)batch * H * W * n->widths[l] / 4), 256, 0, s>>>(in, n->pooled[l], batch, H, W,
+                                                                                       n->widths[l]);
+      NCK(cudaGetLastError());
+      in = n->pooled[l];
+      H /= 2;
+      W /= 2;
+    }
+  }
+  for (int l = n->L - 2; l >= 0; --l) {
+    const int C1 = n->widths[l + 1], C2 = n->widths[l];
+    const bf16 *skip = n->act[2 * l + 2];  // output of enc{l}b
+    k_upsample_concat<<<grid_for((long long)batch * 4 * H * W * (C1 + C2)), 256, 0, s>>>(in, skip, n->cat[l], batch, H,
+                                                                                         W, C1, C2);
+    NCK(cudaGetLastError());
+    H *= 2;
+    W *= 2;
+    in = n->cat[l];
+    for (int q = 0; q < 2; ++q, ++k) {
+      ConvLayer &cl = n->convs[k];
+      NCK(conv_fwd(in, cl.wf, n->p + cl.b_off, n->act[k + 1], batch, H, W, cl.cin, cl.cout, 1, s));
+      in = n->act[k + 1];
+    }
+  }
+  k_head_fwd<<<grid_for(P0 * n->cout), 256, 0, s>>>(in, n->p + n->head_w, n->p + n->head_b, n->out, P0,
+                                                     n->widths[0], n->cout);
+  NCK(cudaGetLastError());
+  return TACCHI_OK;
+}
+
+// Loss and gradients of every parameter into n->g (zeroed first).
+tacchi_status backward(tacchi_nn *n, int batch, const float *target) {
+  cudaStream_t s = n->stream;
+  const long long P0 = (long long)batch * n->H * n->W;
+  NCK(cudaMemsetAsync(n->g, 0, sizeof(float) * n->nparams, s));
+  NCK(cudaMemsetAsync(n->loss, 0, sizeof(float), s));
+  k_mse<<<grid_for(P0 * n->cout), 256, 0, s>>>(n->out, target, n->gout, P0 * n->cout, n->loss);
+  NCK(cudaGetLastError());
+  const int nk = (int)n->convs.size();
+  const int C0 = n->widths[0];
+  k_head_bwd<<<grid_for(P0 * C0), 256, (C0 * n->cout + n->cout) * sizeof(float), s>>>(
+      n->act[nk], n->gout, n->p + n->head_w, n->gact[nk], n->g + n->head_w, n->g + n->head_b, P0, C0, n->cout);
+  NCK(cudaGetLastError());
+
+  // layer k's input activation and the gradient buffer of that input
+  int H = n->H, W = n->W;
+  int k = nk - 1;
+  bf16 *gcur = n->gact[nk];  // gradient of the output of conv k
+  // decoder, level 0 first
+  for (int l = 0; l <= n->L - 2; ++l) {
+    for (int q = 0; q < 2; ++q, --k) {
+      ConvLayer &cl = n->convs[k];
+      const long long P = (long long)batch * H * W;
+      k_relu_mask<<<grid_for(P * cl.cout), 256, 0, s>>>(gcur, n->act[k + 1], P * cl.cout);
+      NCK(cudaGetLastError());
+      const bf16 *xin = q == 0 ? n->act[k] : n->cat[l];
+      bf16 *gin = q == 0 ? n->gact[k] : n->gcat[l];
+      NCK(conv_wgrad(xin, gcur, n->g + cl.w_off, batch, H, W, cl.cin, cl.cout, s));
+      NCK(bias_grad(gcur, n->g + cl.b_off, P, cl.cout, s));
+      NCK(conv_fwd(gcur, cl.wd, nullptr, gin, batch, H, W, cl.cout, cl.cin, 0, s));
+      gcur = gin;
+    }
+    // split the concatenation gradient: upsampled part and skip part
+    const int C1 = n->widths[l + 1], C2 = n->widths[l];
+    bf16 *gskip = n->gact[2 * l + 2];  // gradient of enc{l}b output (skip part first)
+    k_upsample_concat_bwd<<<grid_for((long long)batch * H * W * C2), 256, 0, s>>>(gcur, n->gup[l], gskip, batch, H / 2,
+                                                                                  W / 2, C1, C2);
+    NCK(cudaGetLastError());
+    gcur = n->gup[l];  // gradient of the level l+1 output (decoder or bottom)
+    H /= 2;
+    W /= 2;
+  }
+  // encoder, bottom level first
+  k = 2 * n->L - 1;
+  for (int l = n->L - 1; l >= 0; --l) {
+    if (l < n->L - 1) {
+      // gradient of enc{l}b output = skip gradient (already in gact) + pool^T
+      bf16 *genc = n->gact[2 * l + 2];
+      k_avgpool_bwd_add<<<grid_for((long long)batch * H * W * n->widths[l]), 256, 0, s>>>(gcur, genc, batch, H, W,
+                                                                                         n->widths[l]);
+      NCK(cudaGetLastError());
+      gcur = genc;
+    } else {
+      // bottom: gradient arrives in gup[L-2]; copy it to the bottom output's buffer
+      const long long P = (long long)batch * H * W;
+      if (gcur != n->gact[2 * l + 2])
+        NCK(cudaMemcpyAsync(n->gact[2 * l + 2], gcur, sizeof(bf16) * P * n->widths[l], cudaMemcpyDeviceToDevice, s));
+      gcur = n->gact[2 * l + 2];
+    }
+    for (int q = 0; q < 2; ++q, --k) {
+      ConvLayer &cl = n->convs[k];
+      const long long P = (long long)batch * H * W;
+      k_relu_mask<<<grid_for(P * cl.cout), 256, 0, s>>>(gcur, n->act[k + 1], P * cl.cout);
+      NCK(cudaGetLastError());
+      const bf16 *xin = (q == 1 && l > 0) ? n->pooled[l - 1] : n->act[k];
+      float *dW = (k == 0) ? n->convs[0].dwpad : n->g + cl.w_off;
+      if (k == 0) NCK(cudaMemsetAsync(dW, 0, sizeof(float) * cl.wpad_elems, s));
+      NCK(conv_wgrad(xin, gcur, dW, batch, H, W, cl.cin, cl.cout, s));
+      NCK(bias_grad(gcur, n->g + cl.b_off, P, cl.cout, s));
+      if (k == 0) {
+        k_unpad_wgrad<<<grid_for(9LL * cl.cin_real * cl.cout), 256, 0, s>>>(dW, n->g + cl.w_off, cl.cin_real, cl.cin,
+                                                                            cl.cout);
+        NCK(cudaGetLastError());
+      } else {
+        bf16 *gin = q == 0 ? n->gact[k] : n->gpooled[l - 1];
+        NCK(conv_fwd(gcur, cl.wd, nullptr, gin, batch, H, W, cl.cout, cl.cin, 0, s));
+        gcur = gin;
+      }
+    }
+    if (l > 0) {
+      H *= 2;
+      W *= 2;
+    }
+  }
+  return TACCHI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+tacchi_status tacchi_nn_create(int levels, const int *widths, int in_channels, int out_channels, int height,
+                               int width, int max_batch, uint64_t seed, void *stream, tacchi_nn_handle *out) {
+  if (!out || !widths || levels < 1 || levels > 6 || in_channels < 1 || in_channels > 32 || out_channels < 1 ||
+      out_channels > 16 || max_batch < 1 || height < 1 || width < 1)
+    return TACCHI_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (height % (1 << (levels - 1)) || width % (1 << (levels - 1))) return TACCHI_ERR_INVALID_ARG;
+  if (256 % widths[0]) return TACCHI_ERR_INVALID_ARG;  // the head kernel keeps one channel per thread
+  for (int l = 0; l < levels; ++l)
+    if (widths[l] < 32 || widths[l] % 32 || widths[l] > 1024) return TACCHI_ERR_INVALID_ARG;
+  if ((double)max_batch * height * width * widths[0] > 4.0e9) return TACCHI_ERR_INVALID_ARG;
+  tacchi_nn *n = new (std::nothrow) tacchi_nn();
+  if (!n) return TACCHI_ERR_OOM;
+  n->stream = (cudaStream_t)stream;
+  n->L = levels;
+  n->widths.assign(widths, widths + levels);
+  n->cin_real = in_channels;
+  n->cin = 32;
+  n->cout = out_channels;
+  n->H = height;
+  n->W = width;
+  n->max_batch = max_batch;
+  // parameter layout: per conv (execution order) W [3][3][cin_real][cout] then
+  // b [cout]; then head W [widths0][cout], b [cout]
+  long long off = 0;
+  auto add_conv = [&](int cin_real, int cin, int cout) {
+    ConvLayer cl;
+    cl.cin_real = cin_real;
+    cl.cin = cin;
+    cl.cout = cout;
+    cl.w_off = off;
+    off += 9LL * cin_real * cout;
+    cl.b_off = off;
+    off += cout;
+    cl.wpad_elems = 9LL * cin * cout;
+    n->convs.push_back(cl);
+  };
+  for (int l = 0; l < levels; ++l) {
+    if (l == 0) add_conv(in_channels, 32, widths[0]);
+    else add_conv(widths[l - 1], widths[l - 1], widths[l]);
+    add_conv(widths[l], widths[l], widths[l]);
+  }
+  for (int l = levels - 2; l >= 0; --l) {
+    add_conv(widths[l + 1] + widths[l], widths[l + 1] + widths[l], widths[l]);
+    add_conv(widths[l], widths[l], widths[l]);
+  }
+  n->head_w = off;
+  off += (long long)widths[0] * out_channels;
+  n->head_b = off;
+  off += out_channels;
+  n->nparams = off;
+  auto fail = [&](tacchi_status s) {
+    release_nn(n);
+    return s;
+  };
+  bool ok = nalloc(n, &n->p, off) == cudaSuccess && nalloc(n, &n->g, off) == cudaSuccess &&
+            nalloc(n, &n->m, off) == cudaSuccess && nalloc(n, &n->v, off) == cudaSuccess;
+  for (auto &cl : n->convs)
+    ok = ok && nalloc(n, &cl.wf, cl.wpad_elems) == cudaSuccess && nalloc(n, &cl.wd, cl.wpad_elems) == cudaSuccess;
+  ok = ok && nalloc(n, &n->convs[0].dwpad, n->convs[0].wpad_elems) == cudaSuccess;
+  // activations: act[0] input (32 ch), act[k+1] output of conv k
+  const long long B = max_batch;
+  int H = height, W = width;
+  std::vector<long long> sizes;
+  sizes.push_back(B * H * W * 32);
+  for (int l = 0; l < levels; ++l) {
+    sizes.push_back(B * H * W * widths[l]);
+    sizes.push_back(B * H * W * widths[l]);
+    if (l < levels - 1) {
+      H /= 2;
+      W /= 2;
+    }
+  }
+  for (int l = levels - 2; l >= 0; --l) {
+    H *= 2;
+    W *= 2;
+    sizes.push_back(B * H * W * widths[l]);
+    sizes.push_back(B * H * W * widths[l]);
+  }
+  for (long long sz : sizes) {
+    bf16 *a = nullptr, *ga = nullptr;
+    ok = ok && nalloc(n, &a, sz) == cudaSuccess && nalloc(n, &ga, sz) == cudaSuccess;
+    n->act.push_back(a);
+    n->gact.push_back(ga);
+  }
+  H = height;
+  W = width;
+  n->pooled.assign(levels, nullptr);
+  n->gpooled.assign(levels, nullptr);
+  n->cat.assign(levels, nullptr);
+  n->gcat.assign(levels, nullptr);
+  n->gup.assign(levels, nullptr);
+  for (int l = 0; l < levels - 1; ++l) {
+    const long long hw = (long long)(H >> l) * (W >> l);
+    ok = ok && nalloc(n, &n->pooled[l], B * hw / 4 * widths[l]) == cudaSuccess &&
+         nalloc(n, &n->gpooled[l], B * hw / 4 * widths[l]) == cudaSuccess &&
+         nalloc(n, &n->cat[l], B * hw * (widths[l] + widths[l + 1])) == cudaSuccess &&
+         nalloc(n, &n->gcat[l], B * hw * (widths[l] + widths[l + 1])) == cudaSuccess &&
+         nalloc(n, &n->gup[l], B * hw / 4 * widths[l + 1]) == cudaSuccess;
+  }
+  ok = ok && nalloc(n, &n->out, B * height * width * out_channels) == cudaSuccess &&
+       nalloc(n, &n->gout, B * height * width * out_channels) == cudaSuccess &&
+       nalloc(n, &n->loss, 1) == cudaSuccess && cudaMallocHost((void **)&n->h_loss, sizeof(float)) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    return fail(TACCHI_ERR_OOM);
+  }
+  // He-normal initialisation from splitmix64 + Box-Muller (host, FP64)
+  std::vector<float> hp(off, 0.f);
+  uint64_t ctr = 0;
+  auto uni = [&]() {
+    uint64_t z = seed + (++ctr) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    return ((double)(z >> 11) + 0.5) * 0x1.0p-53;
+  };
+  auto gauss = [&]() { return std::sqrt(-2.0 * std::log(uni())) * std::cos(6.283185307179586 * uni()); };
+  for (auto &cl : n->convs) {
+    const double sd = std::sqrt(2.0 / (9.0 * cl.cin_real));
+    for (long long e = 0; e < 9LL * cl.cin_real * cl.cout; ++e) hp[cl.w_off + e] = (float)(sd * gauss());
+  }
+  const double sdh = std::sqrt(1.0 / widths[0]);
+  for (long long e = 0; e < (long long)widths[0] * out_channels; ++e) hp[n->head_w + e] = (float)(sdh * gauss());
+  if (cudaMemcpy(n->p, hp.data(), sizeof(float) * off, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(n->m, 0, sizeof(float) * off) != cudaSuccess || cudaMemset(n->v, 0, sizeof(float) * off) != cudaSuccess ||
+      refresh_weights(n) != cudaSuccess || cudaStreamSynchronize(n->stream) != cudaSuccess)
+    return fail(TACCHI_ERR_CUDA);
+  *out = n;
+  return TACCHI_OK;
+}
+
+void tacchi_nn_destroy(tacchi_nn_handle n) { release_nn(n); }
+
+tacchi_status tacchi_nn_num_params(tacchi_nn_handle n, int64_t *out) {
+  if (!n || !out) return TACCHI_ERR_INVALID_ARG;
+  *out = n->nparams;
+  return TACCHI_OK;
+}
+
+tacchi_status tacchi_nn_get_params(tacchi_nn_handle n, int which, float *host) {
+  if (!n || !host || which < 0 || which > 1) return TACCHI_ERR_INVALID_ARG;
+  NCK(cudaMemcpyAsync(host, which ? n->g : n->p, sizeof(float) * n->nparams, cudaMemcpyDeviceToHost, n->stream));
+  NCK(cudaStreamSynchronize(n->stream));
+  return TACCHI_OK;
+}
+
+tacchi_status tacchi_nn_set_params(tacchi_nn_handle n, const float *host) {
+  if (!n || !host) return TACCHI_ERR_INVALID_ARG;
+  NCK(cudaMemcpyAsync(n->p, host, sizeof(float) * n->nparams, cudaMemcpyHostToDevice, n->stream));
+  NCK(cudaMemsetAsync(n->m, 0, sizeof(float) * n->nparams, n->stream));
+  NCK(cudaMemsetAsync(n->v, 0, sizeof(float) * n->nparams, n->stream));
+  n->t = 0;
+  NCK(refresh_weights(n));
+  NCK(cudaStreamSynchronize(n->stream));
+  return TACCHI_OK;
+}
+
+tacchi_status tacchi_nn_forward(tacchi_nn_handle n, int batch, const float *x_dev, float *y_dev) {
+  if (!n || !x_dev || !y_dev || batch < 1 || batch > n->max_batch) return TACCHI_ERR_INVALID_ARG;
+  tacchi_status s = forward(n, batch, x_dev);
+  if (s != TACCHI_OK) return s;
+  NCK(cudaMemcpyAsync(y_dev, n->out, sizeof(float) * batch * n->H * n->W * n->cout, cudaMemcpyDeviceToDevice,
+                      n->stream));
+  return TACCHI_OK;
+}
+
+tacchi_status tacchi_nn_gradients(tacchi_nn_handle n, int batch, const float *x_dev, const float *target_dev,
+                                  float *loss_host) {
+  if (!n || !x_dev || !target_dev || batch < 1 || batch > n->max_batch) return TACCHI_ERR_INVALID_ARG;
+  tacchi_status s = forward(n, batch, x_dev);
+  if (s == TACCHI_OK) s = backward(n, batch, target_dev);
+  if (s != TACCHI_OK) return s;
+  if (loss_host) {
+    NCK(cudaMemcpyAsync(n->h_loss, n->loss, sizeof(float), cudaMemcpyDeviceToHost, n->stream));
+    NCK(cudaStreamSynchronize(n->stream));
+    *loss_host = *n->h_loss / (float)((long long)batch * n->H * n->W * n->cout);
+  }
+  return TACCHI_OK;
+}
+
+tacchi_status tacchi_nn_train_step(tacchi_nn_handle n, int batch, const float *x_dev, const float *target_dev,
+                                   float lr, float *loss_host) {
+  if (!n || !(lr > 0) || !std::isfinite(lr)) return TACCHI_ERR_INVALID_ARG;
+  tacchi_status s = tacchi_nn_gradients(n, batch, x_dev, target_dev, nullptr);
+  if (s != TACCHI_OK) return s;
+  n->t += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = (float)(1.0 - std::pow(0.9, n->t)), c2 = (float)(1.0 - std::pow(0.999, n->t));
+  k_adam<<<grid_for(n->nparams), 256, 0, n->stream>>>(n->p, n->g, n->m, n->v, n->nparams, lr, b1, b2, 1e-8f, c1, c2);
+  NCK(cudaGetLastError());
+  NCK(refresh_weights(n));
+  if (loss_host) {
+    NCK(cudaMemcpyAsync(n->h_loss, n->loss, sizeof(float), cudaMemcpyDeviceToHost, n->stream));
+    NCK(cudaStreamSynchronize(n->stream));
+    *loss_host = *n->h_loss / (float)((long long)batch * n->H * n->W * n->cout);
+  }
+  return TACCHI_OK;
+}
+
+}  // extern "C"
