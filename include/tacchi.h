@@ -305,6 +305,24 @@ tacchi_status tacchi_batch_get_state(tacchi_handle h, int i, float *u, float *v,
 tacchi_status tacchi_batch_set_state(tacchi_handle h, int i, const float *u, const float *v,
                                      const float *C, const float *Fm);
 
+/* Top-surface displacement of instance i sampled on a w x hgt pixel grid
+ * over window_m (world frame): pixel (r, c) takes the displacement (m, x/y/z)
+ * of the top-layer particle whose rest sub-cell (the particle lattice at
+ * spacing dx/2 over the block's top face, clamped to it) contains the pixel
+ * centre.  The surrogate's training target and error reference; the paper
+ * has no counterpart.  out_dev: dev float [hgt][w][3].  Asynchronous. */
+tacchi_status tacchi_batch_displacement_map(tacchi_handle h, int i, int w, int hgt, const double window_m[4],
+                                            float *out_dev);
+
+/* Penetration of instance i's indenter into the rest top face at its current
+ * pose: per pixel centre (x, y) of window_m, max(0, z_top - z_b(x, y)) with
+ * z_b the lowest point of the indenter over (x, y) (m).  Only rotations
+ * about the vertical axis are supported.  The surrogate's input; the paper
+ * has no counterpart.  out_dev: dev float [hgt][w].  Errors: INVALID_ARG
+ * (a pose tilted out of the horizontal plane). */
+tacchi_status tacchi_batch_penetration_map(tacchi_handle h, int i, int w, int hgt, const double window_m[4],
+                                           float *out_dev);
+
 /* Sort-block shape (cells) used by the transfer kernel for every instance:
  * 4x4x4, 8x8x4, 8x8x8 or 16x8x4.  Re-sorts the particles and drops cached
  * graphs.  Errors: INVALID_ARG for other shapes. */

@@ -368,6 +368,20 @@ class TacchiBatch:
                                         fill_radius, ptr(out), ptr(out_height)), "tacchi_batch_render")
         return out
 
+    def displacement_map(self, i, w, h, window, out=None):
+        torch = self._torch
+        out = out if out is not None else torch.empty((h, w, 3), device=self.device, dtype=torch.float32)
+        check(lib().tacchi_batch_displacement_map(self._h, i, w, h, (C.c_double * 4)(*window), ptr(out)),
+              "tacchi_batch_displacement_map")
+        return out
+
+    def penetration_map(self, i, w, h, window, out=None):
+        torch = self._torch
+        out = out if out is not None else torch.empty((h, w), device=self.device, dtype=torch.float32)
+        check(lib().tacchi_batch_penetration_map(self._h, i, w, h, (C.c_double * 4)(*window), ptr(out)),
+              "tacchi_batch_penetration_map")
+        return out
+
     def get_state(self, i):
         torch = self._torch
         n = self.info[i]["N"]

@@ -168,6 +168,7 @@ struct tacchi_ctx {
   IndenterFrame *d_frames = nullptr;  // [n_inst][kMaxChunk]
   uint32_t *d_surf = nullptr;
   float *d_z0 = nullptr;
+  float *d_srest = nullptr;  // [3][Ns_tot] rest positions of the surface particles (cells)
   int *d_cov = nullptr;
   size_t cov_cap = 0;
   float *d_hbuf = nullptr;
@@ -533,7 +534,7 @@ void release(tacchi_ctx *c) {
     if (h.d_hm) cudaFree(h.d_hm);
   void *bufs[] = {c->b.u, c->b.Fm, c->b.v, c->b.C, (void *)c->b.flags, c->b.idx, c->b.key, c->b.bstart,
                   c->b.bcount, c->b.cursor, c->b.gmm, c->b.gv, c->b.err, c->b.movers, c->d_inst,
-                  c->d_node_offs, c->d_part_offs, c->d_block_inst, c->d_frames, c->d_surf, c->d_z0,
+                  c->d_node_offs, c->d_part_offs, c->d_block_inst, c->d_frames, c->d_surf, c->d_z0, c->d_srest,
                   c->d_cov, c->d_hbuf, c->d_rgb};
   for (void *p : bufs)
     if (p) cudaFree(p);
@@ -651,7 +652,8 @@ tacchi_status create_batch(int n, const tacchi_elastomer_desc *descs, void *stre
             dalloc(c, &c->d_inst, n) == cudaSuccess && dalloc(c, &c->d_node_offs, n) == cudaSuccess &&
             dalloc(c, &c->d_part_offs, n) == cudaSuccess && dalloc(c, &c->d_block_inst, blk_cap) == cudaSuccess &&
             dalloc(c, &c->d_frames, (size_t)n * kMaxChunk) == cudaSuccess &&
-            dalloc(c, &c->d_surf, surf) == cudaSuccess && dalloc(c, &c->d_z0, surf) == cudaSuccess;
+            dalloc(c, &c->d_surf, surf) == cudaSuccess && dalloc(c, &c->d_z0, surf) == cudaSuccess &&
+            dalloc(c, &c->d_srest, 3 * surf) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     return fail(TACCHI_ERR_OOM);
@@ -666,7 +668,7 @@ tacchi_status create_batch(int n, const tacchi_elastomer_desc *descs, void *stre
   std::vector<float> hu;
   std::vector<uint8_t> hf;
   std::vector<uint32_t> hs;
-  std::vector<float> hz;
+  std::vector<float> hz, hr[3];
   std::vector<long long> noffs(n), poffs(n);
   try {
     hu.resize(3 * N);
@@ -684,6 +686,7 @@ tacchi_status create_batch(int n, const tacchi_elastomer_desc *descs, void *stre
       if (hf[p] & 2) {
         hs.push_back((uint32_t)p);
         hz.push_back(hu[2 * N + p]);
+        for (int a = 0; a < 3; ++a) hr[a].push_back(hu[a * N + p]);
       }
     noffs[i] = h.node_off;
     poffs[i] = h.part_off;
@@ -702,6 +705,11 @@ tacchi_status create_batch(int n, const tacchi_elastomer_desc *descs, void *stre
             cudaMemcpy(c->d_surf, hs.data(), sizeof(uint32_t) * hs.size(), cudaMemcpyHostToDevice) ==
                 cudaSuccess &&
             cudaMemcpy(c->d_z0, hz.data(), sizeof(float) * hz.size(), cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(c->d_srest, hr[0].data(), sizeof(float) * surf, cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(c->d_srest + surf, hr[1].data(), sizeof(float) * surf, cudaMemcpyHostToDevice) ==
+                cudaSuccess &&
+            cudaMemcpy(c->d_srest + 2 * surf, hr[2].data(), sizeof(float) * surf, cudaMemcpyHostToDevice) ==
+                cudaSuccess &&
             cudaMemcpy(c->d_node_offs, noffs.data(), sizeof(long long) * n, cudaMemcpyHostToDevice) ==
                 cudaSuccess &&
             cudaMemcpy(c->d_part_offs, poffs.data(), sizeof(long long) * n, cudaMemcpyHostToDevice) ==
@@ -969,6 +977,69 @@ tacchi_status tacchi_batch_render(tacchi_handle c, int i, const tacchi_render_pa
 tacchi_status tacchi_render(tacchi_handle c, const tacchi_render_params *rp, int w, int h,
                             const double window_m[4], int fill_radius, float *out_rgb, float *out_height) {
   return tacchi_batch_render(c, 0, rp, w, h, window_m, fill_radius, out_rgb, out_height);
+}
+
+tacchi_status tacchi_batch_displacement_map(tacchi_handle c, int i, int w, int h, const double window_m[4],
+                                            float *out_dev) {
+  if (check_index(c, i) != TACCHI_OK || !out_dev) return TACCHI_ERR_INVALID_ARG;
+  tacchi_status s = validate_window(w, h, window_m, 0);
+  if (s != TACCHI_OK) return s;
+  const InstHost &I = c->in[i];
+  DispMapArgs a{};
+  a.u = c->b.u;
+  a.Ntot = c->Ntot;
+  a.surf = c->d_surf + I.surf_off;
+  a.rest = c->d_srest + I.surf_off;
+  a.rest_stride = c->Ns_tot;
+  a.nx = I.n[0];
+  a.ny = I.n[1];
+  a.X0 = (float)(window_m[0] + 0.5 * (window_m[2] - window_m[0]) / w);
+  a.Y0 = (float)(window_m[1] + 0.5 * (window_m[3] - window_m[1]) / h);
+  a.PW = (float)((window_m[2] - window_m[0]) / w);
+  a.PH = (float)((window_m[3] - window_m[1]) / h);
+  a.dx = (float)I.dx;
+  a.w = w;
+  a.h = h;
+  a.out = out_dev;
+  CK(launch_dispmap(a, c->stream));
+  return TACCHI_OK;
+}
+
+tacchi_status tacchi_batch_penetration_map(tacchi_handle c, int i, int w, int h, const double window_m[4],
+                                           float *out_dev) {
+  if (check_index(c, i) != TACCHI_OK || !out_dev) return TACCHI_ERR_INVALID_ARG;
+  tacchi_status s = validate_window(w, h, window_m, 0);
+  if (s != TACCHI_OK) return s;
+  const InstHost &I = c->in[i];
+  const double *q = I.pose + 3;
+  const double qn = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
+  if (std::fabs(q[1]) > 1e-9 * qn || std::fabs(q[2]) > 1e-9 * qn) return TACCHI_ERR_INVALID_ARG;  // yaw only
+  const double yaw = 2.0 * std::atan2(q[3], q[0]);
+  PenMapArgs a{};
+  a.kind = I.ind_kind;
+  a.p0 = (float)I.ind_params[0];
+  a.p1 = (float)I.ind_params[1];
+  a.p2 = (float)I.ind_params[2];
+  a.cx = (float)I.pose[0];
+  a.cy = (float)I.pose[1];
+  a.cz = (float)I.pose[2];
+  a.cosy = (float)std::cos(yaw);
+  a.siny = (float)std::sin(yaw);
+  a.hm = I.d_hm;
+  a.hm_w = I.hm_w;
+  a.hm_h = I.hm_h;
+  a.hm_pix = (float)I.hm_pixel;
+  a.dx = (float)I.dx;
+  a.z_top = (float)I.z_top;
+  a.X0 = (float)(window_m[0] + 0.5 * (window_m[2] - window_m[0]) / w);
+  a.Y0 = (float)(window_m[1] + 0.5 * (window_m[3] - window_m[1]) / h);
+  a.PW = (float)((window_m[2] - window_m[0]) / w);
+  a.PH = (float)((window_m[3] - window_m[1]) / h);
+  a.w = w;
+  a.h = h;
+  a.out = out_dev;
+  CK(launch_penmap(a, c->stream));
+  return TACCHI_OK;
 }
 
 tacchi_status tacchi_shade(const tacchi_render_params *rp, const float *H_dev, int w, int h, double pixel_x_m,

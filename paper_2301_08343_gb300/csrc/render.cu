@@ -130,4 +130,79 @@ cudaError_t launch_shade(const ShadeArgs &a, const float *H, float *rgb, cudaStr
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) k_dispmap(DispMapArgs a) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)a.w * a.h) return;
+  const int r = (int)(e / a.w), c = (int)(e % a.w);
+  // rest lattice of the top particle layer: spacing dx/2 from the block corner
+  const float X = a.X0 + (float)c * a.PW, Y = a.Y0 + (float)r * a.PH;
+  int i = (int)floorf(X / (0.5f * a.dx)), j = (int)floorf(Y / (0.5f * a.dx));
+  i = min(max(i, 0), 2 * a.nx - 1);
+  j = min(max(j, 0), 2 * a.ny - 1);
+  const long long s = ((long long)(j >> 1) * a.nx + (i >> 1)) * 4 + (j & 1) * 2 + (i & 1);
+  const uint32_t p = a.surf[s];
+#pragma unroll
+  for (int d = 0; d < 3; ++d)
+    a.out[3 * e + d] = a.dx * (a.u[d * a.Ntot + p] - a.rest[d * a.rest_stride + s]);
+}
+
+cudaError_t launch_dispmap(const DispMapArgs &a, cudaStream_t st) {
+  const long long P = (long long)a.w * a.h;
+  k_dispmap<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
+// Lowest point of the indenter over world (x, y); +inf where it is absent.
+__device__ float indenter_bottom(const PenMapArgs &a, float x, float y) {
+  const float dxw = x - a.cx, dyw = y - a.cy;
+  const float lx = a.cosy * dxw + a.siny * dyw;   // local frame (yaw only)
+  const float ly = -a.siny * dxw + a.cosy * dyw;
+  const float INF = __int_as_float(0x7f800000);
+  switch (a.kind) {
+    case IND_SPHERE: {  // p0 = radius, pose = centre
+      const float r2 = lx * lx + ly * ly;
+      return r2 < a.p0 * a.p0 ? a.cz - sqrtf(a.p0 * a.p0 - r2) : INF;
+    }
+    case IND_CYLINDER:  // p0 = radius, p1 = half length along local x
+      return (fabsf(lx) <= a.p1 && fabsf(ly) < a.p0) ? a.cz - sqrtf(a.p0 * a.p0 - ly * ly) : INF;
+    case IND_CONE: {    // p0 = half angle, p1 = height; apex at the pose
+      const float r = sqrtf(lx * lx + ly * ly);
+      const float t = tanf(a.p0);
+      return r <= a.p1 * t ? a.cz + r / t : INF;
+    }
+    case IND_PRISM: {   // p0 = half angle, p1 = half length (local y), p2 = height
+      const float t = tanf(a.p0);
+      return (fabsf(ly) <= a.p1 && fabsf(lx) <= a.p2 * t) ? a.cz + fabsf(lx) / t : INF;
+    }
+    case IND_HEIGHTMAP: {  // protrusions below the back plane at the pose
+      const float fx = lx / a.hm_pix + (0.5f * a.hm_w - 0.5f), fy = ly / a.hm_pix + (0.5f * a.hm_h - 0.5f);
+      if (fx < -0.5f || fx > a.hm_w - 0.5f || fy < -0.5f || fy > a.hm_h - 0.5f) return INF;
+      const float cx = fminf(fmaxf(fx, 0.f), (float)(a.hm_w - 1)), cy = fminf(fmaxf(fy, 0.f), (float)(a.hm_h - 1));
+      const int ix = min((int)floorf(cx), a.hm_w - 2), iy = min((int)floorf(cy), a.hm_h - 2);
+      const float tx = cx - ix, ty = cy - iy;
+      const float *H = a.hm;
+      const float h0 = H[iy * a.hm_w + ix] * (1.f - tx) + H[iy * a.hm_w + ix + 1] * tx;
+      const float h1 = H[(iy + 1) * a.hm_w + ix] * (1.f - tx) + H[(iy + 1) * a.hm_w + ix + 1] * tx;
+      return a.cz - a.dx * (h0 * (1.f - ty) + h1 * ty);
+    }
+    default:
+      return INF;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_penmap(PenMapArgs a) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)a.w * a.h) return;
+  const int r = (int)(e / a.w), c = (int)(e % a.w);
+  const float zb = indenter_bottom(a, a.X0 + (float)c * a.PW, a.Y0 + (float)r * a.PH);
+  a.out[e] = fmaxf(a.z_top - zb, 0.f);
+}
+
+cudaError_t launch_penmap(const PenMapArgs &a, cudaStream_t st) {
+  const long long P = (long long)a.w * a.h;
+  k_penmap<<<(unsigned)((P + 255) / 256), 256, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
 }  // namespace tacchi

@@ -165,6 +165,39 @@ struct HeightmapArgs {
 };
 cudaError_t launch_heightmap(const HeightmapArgs &a, cudaStream_t st);
 
+// Top-surface displacement sampled per pixel: the top-layer particle whose
+// rest sub-cell contains the pixel centre (lattice index (i, j) -> surface
+// index ((j/2) nx + i/2) 4 + (j%2) 2 + i%2).
+struct DispMapArgs {
+  const float *u;          // [3][Ntot] positions (cells)
+  long long Ntot;
+  const uint32_t *surf;    // [Ns] particle ids of the instance's surface list
+  const float *rest;       // [3][Ns_tot] rest positions (cells), instance slice
+  long long rest_stride;   // Ns_tot
+  int nx, ny;              // elastomer cells (the block's corner is world (0, 0))
+  float X0, Y0, PW, PH;    // pixel (r, c) centre = (X0 + c PW, Y0 + r PH), metres
+  float dx;
+  int w, h;
+  float *out;              // [h][w][3] metres
+};
+cudaError_t launch_dispmap(const DispMapArgs &a, cudaStream_t st);
+
+// Penetration of a yaw-only posed indenter into the rest top face.
+struct PenMapArgs {
+  int kind;
+  float p0, p1, p2;        // shape parameters (metres, radians)
+  float cx, cy, cz;        // pose position (metres, world)
+  float cosy, siny;        // yaw
+  const float *hm;         // heightmap in cells (device), or null
+  int hm_w, hm_h;
+  float hm_pix, dx;        // metres
+  float z_top;
+  float X0, Y0, PW, PH;
+  int w, h;
+  float *out;              // [h][w] metres
+};
+cudaError_t launch_penmap(const PenMapArgs &a, cudaStream_t st);
+
 struct ShadeArgs {
   int n_lights;
   float dir[8][3], dif[8][3], spe[8][3], amb[3];

@@ -249,3 +249,42 @@ def c2_instances(n=256, seed_base=1000):
                 math.cos(yaw / 2), 0.0, 0.0, math.sin(yaw / 2))
         out.append((blk, dict(kind=kind, params=params, pose=pose, depth=depth)))
     return out
+
+
+# --------------------------------------------------------------------------
+# Surrogate dataset (C3): presses of a C0-scale elastomer.
+C3_BLOCK = Block(24, 24, 6, 0.5e-3, pad_side=4, pad_top=4)
+C3_SUBSTEPS = 500
+C3_DT = 1.0e-5
+C3_SIZE = 64
+
+
+def c3_specs(n, seed_base=0):
+    """n random presses: an analytic indenter (sphere R U[2,4] mm, cylinder
+    R U[1,2] mm x 8 mm, cone of half angle U[25,45] deg, prism of half angle
+    U[30,60] deg x 8 mm), yaw U[0, pi), xy offset U[-1, 1] mm from the block
+    centre, depth U[0.1, 1.0] mm; from numpy's PCG64 seeded with
+    seed_base + i."""
+    out = []
+    b = C3_BLOCK
+    for i in range(n):
+        rng = np.random.default_rng(seed_base + i)
+        kind = ["sphere", "cylinder", "cone", "prism"][int(rng.integers(4))]
+        if kind == "sphere":
+            params = (float(rng.uniform(2e-3, 4e-3)),)
+            tip = params[0]
+        elif kind == "cylinder":
+            params = (float(rng.uniform(1e-3, 2e-3)), 4e-3)
+            tip = params[0]
+        elif kind == "cone":
+            params, tip = (math.radians(float(rng.uniform(25.0, 45.0))), 3e-3), 0.0
+        else:
+            params, tip = (math.radians(float(rng.uniform(30.0, 60.0))), 4e-3, 3e-3), 0.0
+        yaw = float(rng.uniform(0.0, math.pi))
+        off = rng.uniform(-1e-3, 1e-3, 2)
+        depth = float(rng.uniform(0.1e-3, 1.0e-3))
+        z_top = b.nz * b.dx
+        pose = (b.nx * b.dx / 2 + float(off[0]), b.ny * b.dx / 2 + float(off[1]), z_top + tip,
+                math.cos(yaw / 2), 0.0, 0.0, math.sin(yaw / 2))
+        out.append(dict(kind=kind, params=params, pose=pose, depth=depth, yaw=yaw, seed=seed_base + i))
+    return out
