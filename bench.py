@@ -339,6 +339,103 @@ def run_batch_bench(args, rank, world, local_rank):
     }
 
 
+def unet_flops_per_image(widths, size, cin_pad=32, cout=3):
+    """FLOPs (2 per multiply-add) of one forward pass of the surrogate U-Net."""
+    L = len(widths)
+    f = 0
+    hw = size * size
+    for l in range(L):
+        ci = cin_pad if l == 0 else widths[l - 1]
+        f += 2 * (hw >> (2 * l)) * 9 * (ci * widths[l] + widths[l] * widths[l])
+    for l in range(L - 2, -1, -1):
+        f += 2 * (hw >> (2 * l)) * 9 * ((widths[l + 1] + widths[l]) * widths[l] + widths[l] * widths[l])
+    return f + 2 * hw * widths[0] * cout
+
+
+def run_surrogate_bench(args):
+    """Surrogate of the press: MPM data, training, error against held-out MPM
+    results, inference frames/s against the MPM's frames/s."""
+    import torch
+    import paper_2301_08343_gb300 as T
+    from paper_2301_08343_gb300 import surrogate as SG
+
+    n_train, n_test = args.samples, max(256, args.samples // 10)
+    specs = W.c3_specs(n_train + n_test, seed_base=0)
+    X, Y, mpm_s = SG.generate(specs, W.C3_BLOCK, W.C3_SUBSTEPS, W.C3_DT, size=W.C3_SIZE, chunk=1024)
+    mpm_fps = len(specs) / mpm_s
+    widths = (32, 64, 128, 256)
+    net = T.SurrogateNet(widths, 2, 3, size=W.C3_SIZE, max_batch=1024, seed=0)
+    Xtr, Ytr, Xte, Yte = X[:n_train], Y[:n_train], X[n_train:], Y[n_train:]
+    # training, timed with CUDA events
+    SG.train(net, Xtr, Ytr, steps=3, batch=256)  # warm-up
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    log = SG.train(net, Xtr, Ytr, steps=args.train_steps, batch=256, lr=2e-3, log_every=max(1, args.train_steps // 10))
+    e1.record()
+    torch.cuda.synchronize()
+    train_ms = e0.elapsed_time(e1)
+    err = SG.errors_um(SG.predict(net, Xte), Yte)
+    err_train = SG.errors_um(SG.predict(net, Xtr[:n_test]), Ytr[:n_test])
+    zero = SG.errors_um(torch.zeros_like(Yte), Yte)
+    fps = {b: SG.inference_rate(net, Xte.repeat(max(1, 1024 // n_test + 1), 1, 1, 1), b) for b in (1, 256, 1024)}
+    step_flops = 3 * 256 * unet_flops_per_image(widths, W.C3_SIZE)
+    tflops = step_flops * args.train_steps / (train_ms * 1e-3) / 1e12
+    peaks, src = measured_peaks()
+    return {
+        "metric": "surrogate frames/s at batch 1024 vs MPM (error vs MPM in um)", "value": fps[1024],
+        "unit": "frames/s", "n_gpus": 1, "steps": args.train_steps, "warmup": 3,
+        "ms_per_step": train_ms / args.train_steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16 (fp32 accumulate)", "data": "synthetic",
+        "config": {"workload": f"c3: {n_train} training / {n_test} held-out MPM presses of a 12x12x3 mm "
+                               f"elastomer (dx 0.5 mm, 500 substeps), 64x64 maps, U-Net widths {widths}, "
+                               f"{net.num_params} parameters, batch 256, Adam",
+                   "samples": n_train, "held_out": n_test, "params": net.num_params},
+        "error_vs_mpm_heldout": err, "error_vs_mpm_train": err_train, "zero_predictor": zero,
+        "gate_5um_rms_uz": err["rms_uz_um_mean"] <= 5.0,
+        "inference_fps": fps, "mpm_fps_batched": mpm_fps, "speedup_vs_mpm": fps[1024] / mpm_fps,
+        "train_samples_per_s": 256 * args.train_steps / (train_ms * 1e-3),
+        "loss_log": log,
+        "roofline": {"kernel": "training step (3x3 conv fwd/dgrad/wgrad dominate)", "bound": "tensor",
+                     "achieved": round(tflops, 2), "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                     "frac": round(tflops / peaks["bf16_tflops"], 4),
+                     "peak_source": f"{src} (MEASURED_PEAKS bf16_tflops)", "traffic": None},
+    }
+
+
+def run_serving_bench(args):
+    """Poisson press-query stream served by surrogate + MPM fallback, against
+    the same stream served by the batched MPM alone."""
+    import paper_2301_08343_gb300 as T
+    from paper_2301_08343_gb300 import serving as SV
+    from paper_2301_08343_gb300 import surrogate as SG
+
+    specs = W.c3_specs(args.samples, seed_base=0)
+    X, Y, _ = SG.generate(specs, W.C3_BLOCK, W.C3_SUBSTEPS, W.C3_DT, size=W.C3_SIZE, chunk=1024)
+    net = T.SurrogateNet((32, 64, 128, 256), 2, 3, size=W.C3_SIZE, max_batch=1024, seed=0)
+    SG.train(net, X, Y, steps=args.train_steps, batch=256, lr=2e-3)
+    del X, Y
+    q = W.c4_queries(rate_hz=4096.0, duration_s=args.stream_s, seed=4)
+    srv = SV.PressServer(net, W.C3_BLOCK, W.C3_SUBSTEPS, W.C3_DT, size=W.C3_SIZE)
+    srv.serve(q[:64])  # warm-up: pooled MPM handles and their step graphs
+    mixed = srv.serve(q)
+    base = SV.PressServer(net, W.C3_BLOCK, W.C3_SUBSTEPS, W.C3_DT, size=W.C3_SIZE, use_surrogate=False,
+                          mpm_batch=1024)
+    base.serve(q[:64])
+    plain = base.serve(q)
+    return {
+        "metric": "served press frames/s (surrogate + MPM fallback) vs plain batched MPM", "value":
+        mixed["frames_per_s"], "unit": "frames/s", "n_gpus": 1, "steps": 1, "warmup": 0,
+        "ms_per_step": mixed["makespan_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16 + f32", "data": "synthetic",
+        "config": {"workload": f"c4: Poisson stream of {len(q)} press queries at 4096/s over {args.stream_s} s, "
+                               "10% out of the training range, windows of 20 ms, surrogate batch <= 1024, "
+                               "every 64th in-range query checked against the MPM (5 um RMS gate)",
+                   "train_samples": args.samples, "train_steps": args.train_steps},
+        "mixed": mixed, "plain_mpm": plain, "speedup": mixed["frames_per_s"] / plain["frames_per_s"],
+    }
+
+
 def load_traffic(workload):
     """DRAM bytes per fused launch from the committed ncu summary; null when
     the kernel source changed since the counters were taken."""
@@ -417,7 +514,10 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["c2"], default="c1")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["c2", "surrogate", "serving"], default="c1")
+    ap.add_argument("--stream-s", type=float, default=0.5, help="seconds of the served query stream")
+    ap.add_argument("--samples", type=int, default=4096, help="surrogate training presses")
+    ap.add_argument("--train-steps", type=int, default=1500)
     ap.add_argument("--substeps", type=int, default=0, help="override substeps per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
@@ -440,6 +540,14 @@ def main():
     if world > 1:
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
+    if args.workload == "serving":
+        if rank == 0:
+            print(json.dumps(run_serving_bench(args)))
+        return
+    if args.workload == "surrogate":
+        if rank == 0:
+            print(json.dumps(run_surrogate_bench(args)))
+        return
     if args.workload == "c2":
         result = run_batch_bench(args, rank, world, local_rank)
         if rank == 0:

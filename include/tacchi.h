@@ -323,6 +323,12 @@ tacchi_status tacchi_batch_displacement_map(tacchi_handle h, int i, int w, int h
 tacchi_status tacchi_batch_penetration_map(tacchi_handle h, int i, int w, int hgt, const double window_m[4],
                                            float *out_dev);
 
+/* Put every instance back to its initial particle lattice (v = 0, C = 0,
+ * F = I), clear the device error and re-sort; indenters are kept.  Lets a
+ * caller reuse one handle (and its cached step graphs) for new presses.
+ * Asynchronous.  Errors: INVALID_ARG, CUDA. */
+tacchi_status tacchi_batch_reset(tacchi_handle h);
+
 /* Sort-block shape (cells) used by the transfer kernel for every instance:
  * 4x4x4, 8x8x4, 8x8x8 or 16x8x4.  Re-sorts the particles and drops cached
  * graphs.  Errors: INVALID_ARG for other shapes. */

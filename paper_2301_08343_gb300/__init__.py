@@ -344,6 +344,10 @@ class TacchiBatch:
         check(lib().tacchi_get_profile(self._h, C.byref(p), int(bool(reset))), "tacchi_get_profile")
         return {f: getattr(p, f) for f, _ in p._fields_}
 
+    def reset(self):
+        """Every instance back to its initial lattice (indenters kept)."""
+        check(lib().tacchi_batch_reset(self._h), "tacchi_batch_reset")
+
     def set_block(self, shape):
         check(lib().tacchi_set_block(self._h, *shape), "tacchi_set_block")
 

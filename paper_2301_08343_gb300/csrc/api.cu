@@ -169,6 +169,7 @@ struct tacchi_ctx {
   uint32_t *d_surf = nullptr;
   float *d_z0 = nullptr;
   float *d_srest = nullptr;  // [3][Ns_tot] rest positions of the surface particles (cells)
+  float *d_u0 = nullptr;     // [3][Ntot] initial positions (for tacchi_batch_reset)
   int *d_cov = nullptr;
   size_t cov_cap = 0;
   float *d_hbuf = nullptr;
@@ -535,6 +536,7 @@ void release(tacchi_ctx *c) {
   void *bufs[] = {c->b.u, c->b.Fm, c->b.v, c->b.C, (void *)c->b.flags, c->b.idx, c->b.key, c->b.bstart,
                   c->b.bcount, c->b.cursor, c->b.gmm, c->b.gv, c->b.err, c->b.movers, c->d_inst,
                   c->d_node_offs, c->d_part_offs, c->d_block_inst, c->d_frames, c->d_surf, c->d_z0, c->d_srest,
+                  c->d_u0,
                   c->d_cov, c->d_hbuf, c->d_rgb};
   for (void *p : bufs)
     if (p) cudaFree(p);
@@ -637,8 +639,8 @@ tacchi_status create_batch(int n, const tacchi_elastomer_desc *descs, void *stre
   c->Nnodes = node;
   c->Ns_tot = surf;
   c->Nblk_cap = blk_cap;
-  SortBlock blk = user_block ? SortBlock{d0.block[0], d0.block[1], d0.block[2]}
-                             : (part / n < 2000000 ? SortBlock{4, 4, 4} : SortBlock{8, 8, 4});
+  // one thread per home cell: 8x8x4 blocks keep the 128 threads of a CTA busy
+  SortBlock blk = user_block ? SortBlock{d0.block[0], d0.block[1], d0.block[2]} : SortBlock{8, 8, 4};
   for (int i = 0; i < n; ++i) c->in[i].dev.frames = nullptr;
 
   const long long N = c->Ntot, Nn = c->Nnodes;
@@ -653,7 +655,7 @@ tacchi_status create_batch(int n, const tacchi_elastomer_desc *descs, void *stre
             dalloc(c, &c->d_part_offs, n) == cudaSuccess && dalloc(c, &c->d_block_inst, blk_cap) == cudaSuccess &&
             dalloc(c, &c->d_frames, (size_t)n * kMaxChunk) == cudaSuccess &&
             dalloc(c, &c->d_surf, surf) == cudaSuccess && dalloc(c, &c->d_z0, surf) == cudaSuccess &&
-            dalloc(c, &c->d_srest, 3 * surf) == cudaSuccess;
+            dalloc(c, &c->d_srest, 3 * surf) == cudaSuccess && dalloc(c, &c->d_u0, 3 * N) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     return fail(TACCHI_ERR_OOM);
@@ -701,6 +703,7 @@ tacchi_status create_batch(int n, const tacchi_elastomer_desc *descs, void *stre
 
   cudaStream_t st = c->stream;
   bool up = cudaMemcpy(c->b.u, hu.data(), sizeof(float) * 3 * N, cudaMemcpyHostToDevice) == cudaSuccess &&
+            cudaMemcpy(c->d_u0, hu.data(), sizeof(float) * 3 * N, cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy((void *)c->b.flags, hf.data(), N, cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(c->d_surf, hs.data(), sizeof(uint32_t) * hs.size(), cudaMemcpyHostToDevice) ==
                 cudaSuccess &&
@@ -1101,6 +1104,21 @@ tacchi_status tacchi_batch_set_state(tacchi_handle c, int i, const float *u, con
 
 tacchi_status tacchi_set_state(tacchi_handle c, const float *u, const float *v, const float *C, const float *Fm) {
   return tacchi_batch_set_state(c, 0, u, v, C, Fm);
+}
+
+tacchi_status tacchi_batch_reset(tacchi_handle c) {
+  if (!c) return TACCHI_ERR_INVALID_ARG;
+  const long long T = c->Ntot;
+  cudaStream_t st = c->stream;
+  CK(cudaMemcpyAsync(c->b.u, c->d_u0, sizeof(float) * 3 * T, cudaMemcpyDeviceToDevice, st));
+  CK(cudaMemsetAsync(c->b.v, 0, sizeof(float) * 3 * T, st));
+  CK(cudaMemsetAsync(c->b.C, 0, sizeof(float) * 9 * T, st));
+  CK(cudaMemsetAsync(c->b.Fm, 0, sizeof(float) * 9 * T, st));
+  CK(cudaMemsetAsync(c->b.err, 0, sizeof(int), st));
+  CK(launch_sort(c->b, c->blk, 1, st));
+  CK(cudaMemsetAsync(c->b.movers, 0, sizeof(int), st));
+  c->stepped = false;
+  return TACCHI_OK;
 }
 
 tacchi_status tacchi_get_grid(tacchi_handle c, float *out) {

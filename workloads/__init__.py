@@ -288,3 +288,32 @@ def c3_specs(n, seed_base=0):
                 math.cos(yaw / 2), 0.0, 0.0, math.sin(yaw / 2))
         out.append(dict(kind=kind, params=params, pose=pose, depth=depth, yaw=yaw, seed=seed_base + i))
     return out
+
+
+# --------------------------------------------------------------------------
+# Serving mix (C4): a Poisson stream of press queries on the C3 sensor.
+def c4_queries(rate_hz=4096.0, duration_s=1.0, seed=4, out_of_range=0.10):
+    """Arrival times (exponential gaps at rate_hz) and press specs: mostly
+    presses like the training set; a fraction out of its range (depth 1.0-1.5
+    mm, or a height-map dot-grid indenter the network never saw)."""
+    rng = np.random.default_rng(seed)
+    t, out = 0.0, []
+    i = 0
+    while True:
+        t += float(rng.exponential(1.0 / rate_hz))
+        if t > duration_s:
+            break
+        spec = c3_specs(1, seed_base=10_000_000 + 97 * seed + i)[0]
+        if rng.uniform() < out_of_range:
+            if rng.uniform() < 0.5:
+                spec["depth"] = float(rng.uniform(1.0e-3, 1.5e-3))
+            else:
+                b = C3_BLOCK
+                hm = hm_dots(n=64, pix=0.1e-3, pitch=1.2e-3, count=4, height=0.8e-3)
+                spec.update(kind="heightmap", params=(2e-3,), hm=hm,
+                            pose=(b.nx * b.dx / 2, b.ny * b.dx / 2, b.nz * b.dx + float(hm.max()), 1.0, 0.0, 0.0, 0.0))
+        spec["arrival"] = t
+        spec["id"] = i
+        out.append(spec)
+        i += 1
+    return out
