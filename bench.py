@@ -118,6 +118,24 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
+def reduce_over_ranks(times, units, world, device):
+    """Whole-job timing across ranks: each entry of times becomes its maximum
+    over the ranks (the slowest rank ends the job) and units the sum of every
+    rank's work.  Returns (times, units)."""
+    import torch
+    t = torch.tensor([float(x) for x in times], dtype=torch.float64, device=device)
+    u = torch.tensor([float(units)], dtype=torch.float64, device=device)
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        torch.distributed.all_reduce(u, op=torch.distributed.ReduceOp.SUM)
+    return [float(x) for x in t.tolist()], float(u[0])
+
+
+def whole_job_rate(units, seconds):
+    """Units all ranks processed per second of the slowest rank."""
+    return units / seconds
+
+
 def indenter_for_step(block, s, substeps, dt):
     """Indenter s (cycled over the nine shapes and four depths): its tip
     starts at the rest top face over the block centre and moves straight
@@ -214,13 +232,10 @@ def run_ours(args, rank, world, local_rank):
     h2d = int(hm_bytes + frame_bytes + 13 * 8)
     d2h = int(host_img.numel() * 4 + host_h.numel() * 4)
 
-    totals = torch.tensor([ms, e2e_s], dtype=torch.float64, device=dev)
-    if world > 1:
-        torch.distributed.all_reduce(totals, op=torch.distributed.ReduceOp.MAX)
-    ms, e2e_s = float(totals[0]), float(totals[1])
     units_per_step = sim.N * substeps
-    value = units_per_step * args.steps * world / (ms * 1e-3)
-    e2e_value = units_per_step * e_steps * world / e2e_s
+    (ms, e2e_s), units_all = reduce_over_ranks([ms, e2e_s], units_per_step, world, dev)
+    value = whole_job_rate(units_all * args.steps, ms * 1e-3)
+    e2e_value = whole_job_rate(units_all * e_steps, e2e_s)
 
     peaks, src = measured_peaks()
     fused_avg_ms = prof["fused_ms"] / max(prof["fused_launches"], 1)
@@ -304,21 +319,27 @@ def run_batch_bench(args, rank, world, local_rank):
     bt.set_profiling(True)  # profiled step graphs are built during warm-up
     for s in range(args.warmup):
         one_step(s)
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
     clocks = ClockSampler(local_rank)
     bt.profile(reset=True)
-    torch.cuda.synchronize(dev)
+    barrier()
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for s in range(args.steps):
         one_step(args.warmup + s)
     e1.record(stream)
-    torch.cuda.synchronize(dev)
+    barrier()
     clk = clocks.stop()
     bt.set_profiling(False)
     ms = e0.elapsed_time(e1)
     prof = bt.profile(reset=True)
-    value = bt.N_total * substeps * args.steps * world / (ms * 1e-3)
+    (ms,), units_all = reduce_over_ranks([ms], bt.N_total * substeps, world, dev)
+    value = whole_job_rate(units_all * args.steps, ms * 1e-3)
     sizes = [b.n_particles for b, _ in specs]
     fused_avg = prof["fused_ms"] / max(prof["fused_launches"], 1)
     return {
@@ -329,7 +350,8 @@ def run_batch_bench(args, rank, world, local_rank):
         "config": {"workload": f"c2: {len(specs)} sensors, sides U[8,16] mm x thickness U[2,4] mm, "
                                f"dx=0.25 mm, {bt.N_total} particles ({min(sizes)}-{max(sizes)} each), "
                                f"{substeps} substeps dt={dt:g} s + 64x64 map per sensor per step",
-                   "instances": len(specs), "particles": bt.N_total, "autotune": tuned,
+                   "instances": len(specs), "particles": bt.N_total,
+                   "particles_all_ranks": int(units_all // substeps), "autotune": tuned,
                    "parallelism": f"replicas x{world}", "l2": "inputs larger than L2"},
         "kernel_share_of_step": {k: round(prof[k + "_ms"] / max(ms, 1e-9), 4)
                                  for k in ("grid", "fused", "edge", "sort")},
@@ -429,7 +451,8 @@ def run_serving_bench(args):
         "ms_per_step": mixed["makespan_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16 + f32", "data": "synthetic",
         "config": {"workload": f"c4: Poisson stream of {len(q)} press queries at 4096/s over {args.stream_s} s, "
-                               "10% out of the training range, windows of 20 ms, surrogate batch <= 1024, "
+                               "10% out of the training range, surrogate batch <= 1024, MPM lane in 50-substep "
+                               "slices (batch 256 or 0.25 s wait), "
                                "every 64th in-range query checked against the MPM (5 um RMS gate)",
                    "train_samples": args.samples, "train_steps": args.train_steps},
         "mixed": mixed, "plain_mpm": plain, "speedup": mixed["frames_per_s"] / plain["frames_per_s"],
