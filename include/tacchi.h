@@ -246,6 +246,8 @@ typedef struct {
   double edge_ms;        /* P2G-only and G2P-only transfers opening/closing a step */
   double sort_ms;        /* particle sort (three kernels, timed together) */
   int64_t grid_launches, fused_launches, edge_launches, sort_launches;
+  int64_t sort_runs;     /* sorts that did work: some particle had left its block
+                            (the others only checked the flag) */
 } tacchi_profile_t;
 
 /* Turn kernel timing on (1) or off (0).  While on, every step graph carries
@@ -254,7 +256,8 @@ typedef struct {
 tacchi_status tacchi_set_profiling(tacchi_handle h, int on);
 
 /* Accumulated kernel times since profiling was turned on or last reset;
- * reset != 0 zeroes them after reading.  out: host. */
+ * reset != 0 zeroes them after reading.  Synchronises the stream (to read the
+ * device count of sorts).  out: host.  Errors: INVALID_ARG, CUDA. */
 tacchi_status tacchi_get_profile(tacchi_handle h, tacchi_profile_t *out, int reset);
 
 /* Wait for the context's queued work and report the sticky device error. */

@@ -52,7 +52,7 @@ class Profile(C.Structure):
     _fields_ = [("grid_ms", C.c_double), ("fused_ms", C.c_double), ("edge_ms", C.c_double),
                 ("sort_ms", C.c_double), ("grid_launches", C.c_int64),
                 ("fused_launches", C.c_int64), ("edge_launches", C.c_int64),
-                ("sort_launches", C.c_int64)]
+                ("sort_launches", C.c_int64), ("sort_runs", C.c_int64)]
 
 
 _lock = threading.Lock()

@@ -186,6 +186,7 @@ struct tacchi_ctx {
   bool profiling = false;
   double prof_ms[4] = {0, 0, 0, 0};
   int64_t prof_n[4] = {0, 0, 0, 0};
+  int sort_base = 0;  // device count of sorts that did work, at the last profile reset
   bool stepped = false;
   size_t device_bytes = 0;
 
@@ -442,7 +443,7 @@ tacchi_status run_heightmap(tacchi_ctx *c, int i, int w, int h, const double *wi
   const InstHost &I = c->in[i];
   CK(ensure(c, &c->d_cov, &c->cov_cap, (size_t)w * h));
   HeightmapArgs a{};
-  a.u = c->b.u;
+  a.ps = c->b.ps;
   a.Ntot = c->Ntot;
   a.surf = c->d_surf + I.surf_off;
   a.z0 = c->d_z0 + I.surf_off;
@@ -533,7 +534,7 @@ void release(tacchi_ctx *c) {
   drop_graphs(c);
   for (auto &h : c->in)
     if (h.d_hm) cudaFree(h.d_hm);
-  void *bufs[] = {c->b.u, c->b.Fm, c->b.v, c->b.C, (void *)c->b.flags, c->b.idx, c->b.key, c->b.bstart,
+  void *bufs[] = {c->b.ps, c->b.v, c->b.C, (void *)c->b.flags, c->b.idx, c->b.key, c->b.bstart,
                   c->b.bcount, c->b.cursor, c->b.gmm, c->b.gv, c->b.err, c->b.movers, c->d_inst,
                   c->d_node_offs, c->d_part_offs, c->d_block_inst, c->d_frames, c->d_surf, c->d_z0, c->d_srest,
                   c->d_u0,
@@ -644,13 +645,13 @@ tacchi_status create_batch(int n, const tacchi_elastomer_desc *descs, void *stre
   for (int i = 0; i < n; ++i) c->in[i].dev.frames = nullptr;
 
   const long long N = c->Ntot, Nn = c->Nnodes;
-  bool ok = dalloc(c, &c->b.u, 3 * N) == cudaSuccess && dalloc(c, &c->b.Fm, 9 * N) == cudaSuccess &&
+  bool ok = dalloc(c, &c->b.ps, 3 * N) == cudaSuccess &&
             dalloc(c, &c->b.v, 3 * N) == cudaSuccess && dalloc(c, &c->b.C, 9 * N) == cudaSuccess &&
             dalloc(c, (uint8_t **)&c->b.flags, N) == cudaSuccess && dalloc(c, &c->b.idx, N) == cudaSuccess &&
             dalloc(c, &c->b.key, N) == cudaSuccess && dalloc(c, &c->b.bstart, blk_cap + 1) == cudaSuccess &&
             dalloc(c, &c->b.bcount, blk_cap) == cudaSuccess && dalloc(c, &c->b.cursor, blk_cap) == cudaSuccess &&
             dalloc(c, &c->b.gmm, Nn) == cudaSuccess && dalloc(c, &c->b.gv, Nn) == cudaSuccess &&
-            dalloc(c, &c->b.err, 1) == cudaSuccess && dalloc(c, &c->b.movers, 1) == cudaSuccess &&
+            dalloc(c, &c->b.err, 1) == cudaSuccess && dalloc(c, &c->b.movers, 2) == cudaSuccess &&
             dalloc(c, &c->d_inst, n) == cudaSuccess && dalloc(c, &c->d_node_offs, n) == cudaSuccess &&
             dalloc(c, &c->d_part_offs, n) == cudaSuccess && dalloc(c, &c->d_block_inst, blk_cap) == cudaSuccess &&
             dalloc(c, &c->d_frames, (size_t)n * kMaxChunk) == cudaSuccess &&
@@ -660,6 +661,7 @@ tacchi_status create_batch(int n, const tacchi_elastomer_desc *descs, void *stre
     cudaGetLastError();
     return fail(TACCHI_ERR_OOM);
   }
+  if (cudaMemset(c->b.movers, 0, 2 * sizeof(int)) != cudaSuccess) return fail(TACCHI_ERR_CUDA);
   if (cudaMallocHost((void **)&c->h_stage, stage_bytes(n)) != cudaSuccess ||
       cudaMallocHost((void **)&c->h_err, sizeof(int)) != cudaSuccess)
     return fail(TACCHI_ERR_OOM);
@@ -702,8 +704,8 @@ tacchi_status create_batch(int n, const tacchi_elastomer_desc *descs, void *stre
   c->b.Nnodes = Nn;
 
   cudaStream_t st = c->stream;
-  bool up = cudaMemcpy(c->b.u, hu.data(), sizeof(float) * 3 * N, cudaMemcpyHostToDevice) == cudaSuccess &&
-            cudaMemcpy(c->d_u0, hu.data(), sizeof(float) * 3 * N, cudaMemcpyHostToDevice) == cudaSuccess &&
+  bool up = cudaMemcpy(c->d_u0, hu.data(), sizeof(float) * 3 * N, cudaMemcpyHostToDevice) == cudaSuccess &&
+            launch_pack_state(c->b.ps, 0, N, c->d_u0, nullptr, st) == cudaSuccess &&
             cudaMemcpy((void *)c->b.flags, hf.data(), N, cudaMemcpyHostToDevice) == cudaSuccess &&
             cudaMemcpy(c->d_surf, hs.data(), sizeof(uint32_t) * hs.size(), cudaMemcpyHostToDevice) ==
                 cudaSuccess &&
@@ -717,7 +719,6 @@ tacchi_status create_batch(int n, const tacchi_elastomer_desc *descs, void *stre
                 cudaSuccess &&
             cudaMemcpy(c->d_part_offs, poffs.data(), sizeof(long long) * n, cudaMemcpyHostToDevice) ==
                 cudaSuccess &&
-            cudaMemsetAsync(c->b.Fm, 0, sizeof(float) * 9 * N, st) == cudaSuccess &&
             cudaMemsetAsync(c->b.v, 0, sizeof(float) * 3 * N, st) == cudaSuccess &&
             cudaMemsetAsync(c->b.C, 0, sizeof(float) * 9 * N, st) == cudaSuccess &&
             cudaMemsetAsync(c->b.gmm, 0, sizeof(float4) * Nn, st) == cudaSuccess &&
@@ -989,7 +990,7 @@ tacchi_status tacchi_batch_displacement_map(tacchi_handle c, int i, int w, int h
   if (s != TACCHI_OK) return s;
   const InstHost &I = c->in[i];
   DispMapArgs a{};
-  a.u = c->b.u;
+  a.ps = c->b.ps;
   a.Ntot = c->Ntot;
   a.surf = c->d_surf + I.surf_off;
   a.rest = c->d_srest + I.surf_off;
@@ -1061,14 +1062,11 @@ tacchi_status tacchi_batch_get_state(tacchi_handle c, int i, float *u, float *v,
   const InstHost &h = c->in[i];
   const long long N = h.N, T = c->Ntot, o = h.part_off;
   const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
-  for (int a = 0; a < 3; ++a) {
-    if (u) CK(cudaMemcpyAsync(u + a * N, c->b.u + a * T + o, sizeof(float) * N, k, c->stream));
+  if (u || Fm) CK(launch_unpack_state(c->b.ps, o, N, u, Fm, c->stream));
+  for (int a = 0; a < 3; ++a)
     if (v) CK(cudaMemcpyAsync(v + a * N, c->b.v + a * T + o, sizeof(float) * N, k, c->stream));
-  }
-  for (int e = 0; e < 9; ++e) {
+  for (int e = 0; e < 9; ++e)
     if (C) CK(cudaMemcpyAsync(C + e * N, c->b.C + e * T + o, sizeof(float) * N, k, c->stream));
-    if (Fm) CK(cudaMemcpyAsync(Fm + e * N, c->b.Fm + e * T + o, sizeof(float) * N, k, c->stream));
-  }
   if (flags) CK(cudaMemcpyAsync(flags, c->b.flags + o, N, k, c->stream));
   return sync_and_check(c);
 }
@@ -1084,16 +1082,14 @@ tacchi_status tacchi_batch_set_state(tacchi_handle c, int i, const float *u, con
   const long long N = h.N, T = c->Ntot, o = h.part_off;
   const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
   cudaStream_t st = c->stream;
+  CK(launch_pack_state(c->b.ps, o, N, u, Fm, st));
   for (int a = 0; a < 3; ++a) {
-    CK(cudaMemcpyAsync(c->b.u + a * T + o, u + a * N, sizeof(float) * N, k, st));
     if (v) CK(cudaMemcpyAsync(c->b.v + a * T + o, v + a * N, sizeof(float) * N, k, st));
     else CK(cudaMemsetAsync(c->b.v + a * T + o, 0, sizeof(float) * N, st));
   }
   for (int e = 0; e < 9; ++e) {
     if (C) CK(cudaMemcpyAsync(c->b.C + e * T + o, C + e * N, sizeof(float) * N, k, st));
     else CK(cudaMemsetAsync(c->b.C + e * T + o, 0, sizeof(float) * N, st));
-    if (Fm) CK(cudaMemcpyAsync(c->b.Fm + e * T + o, Fm + e * N, sizeof(float) * N, k, st));
-    else CK(cudaMemsetAsync(c->b.Fm + e * T + o, 0, sizeof(float) * N, st));
   }
   CK(cudaMemsetAsync(c->b.err, 0, sizeof(int), st));
   CK(launch_sort(c->b, c->blk, 1, st));
@@ -1110,10 +1106,9 @@ tacchi_status tacchi_batch_reset(tacchi_handle c) {
   if (!c) return TACCHI_ERR_INVALID_ARG;
   const long long T = c->Ntot;
   cudaStream_t st = c->stream;
-  CK(cudaMemcpyAsync(c->b.u, c->d_u0, sizeof(float) * 3 * T, cudaMemcpyDeviceToDevice, st));
+  CK(launch_pack_state(c->b.ps, 0, T, c->d_u0, nullptr, st));
   CK(cudaMemsetAsync(c->b.v, 0, sizeof(float) * 3 * T, st));
   CK(cudaMemsetAsync(c->b.C, 0, sizeof(float) * 9 * T, st));
-  CK(cudaMemsetAsync(c->b.Fm, 0, sizeof(float) * 9 * T, st));
   CK(cudaMemsetAsync(c->b.err, 0, sizeof(int), st));
   CK(launch_sort(c->b, c->blk, 1, st));
   CK(cudaMemsetAsync(c->b.movers, 0, sizeof(int), st));
@@ -1142,22 +1137,19 @@ tacchi_status tacchi_autotune(tacchi_handle c, int n_substeps, double dt, int be
   float *save = nullptr;
   CK(cudaMalloc((void **)&save, sizeof(float) * 24 * T));
   auto restore = [&]() -> tacchi_status {
-    CK(cudaMemcpyAsync(c->b.u, save, sizeof(float) * 3 * T, cudaMemcpyDeviceToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->b.v, save + 3 * T, sizeof(float) * 3 * T, cudaMemcpyDeviceToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->b.C, save + 6 * T, sizeof(float) * 9 * T, cudaMemcpyDeviceToDevice, c->stream));
-    CK(cudaMemcpyAsync(c->b.Fm, save + 15 * T, sizeof(float) * 9 * T, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->b.ps, save, sizeof(float) * 12 * T, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->b.v, save + 12 * T, sizeof(float) * 3 * T, cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(c->b.C, save + 15 * T, sizeof(float) * 9 * T, cudaMemcpyDeviceToDevice, c->stream));
     CK(launch_sort(c->b, c->blk, 1, c->stream));  // the sort must match the restored positions
     CK(cudaMemsetAsync(c->b.movers, 0, sizeof(int), c->stream));
     CK(cudaMemsetAsync(c->b.err, 0, sizeof(int), c->stream));
     return TACCHI_OK;
   };
   tacchi_status st = TACCHI_OK;
-  if (cudaMemcpyAsync(save, c->b.u, sizeof(float) * 3 * T, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess ||
-      cudaMemcpyAsync(save + 3 * T, c->b.v, sizeof(float) * 3 * T, cudaMemcpyDeviceToDevice, c->stream) !=
+  if (cudaMemcpyAsync(save, c->b.ps, sizeof(float) * 12 * T, cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(save + 12 * T, c->b.v, sizeof(float) * 3 * T, cudaMemcpyDeviceToDevice, c->stream) !=
           cudaSuccess ||
-      cudaMemcpyAsync(save + 6 * T, c->b.C, sizeof(float) * 9 * T, cudaMemcpyDeviceToDevice, c->stream) !=
-          cudaSuccess ||
-      cudaMemcpyAsync(save + 15 * T, c->b.Fm, sizeof(float) * 9 * T, cudaMemcpyDeviceToDevice, c->stream) !=
+      cudaMemcpyAsync(save + 15 * T, c->b.C, sizeof(float) * 9 * T, cudaMemcpyDeviceToDevice, c->stream) !=
           cudaSuccess)
     st = TACCHI_ERR_CUDA;
   std::vector<std::vector<double>> poses(c->n_inst());
@@ -1201,8 +1193,20 @@ tacchi_status tacchi_autotune(tacchi_handle c, int n_substeps, double dt, int be
   return st;
 }
 
+namespace {
+tacchi_status sort_count(tacchi_ctx *c, int *out) {
+  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpy(out, c->b.movers + 1, sizeof(int), cudaMemcpyDeviceToHost));
+  return TACCHI_OK;
+}
+}  // namespace
+
 tacchi_status tacchi_set_profiling(tacchi_handle c, int on) {
   if (!c) return TACCHI_ERR_INVALID_ARG;
+  if (on && !c->profiling) {
+    const tacchi_status st = sort_count(c, &c->sort_base);
+    if (st != TACCHI_OK) return st;
+  }
   c->profiling = on != 0;
   return TACCHI_OK;
 }
@@ -1217,11 +1221,17 @@ tacchi_status tacchi_get_profile(tacchi_handle c, tacchi_profile_t *o, int reset
   o->fused_launches = c->prof_n[1];
   o->edge_launches = c->prof_n[2];
   o->sort_launches = c->prof_n[3];
-  if (reset)
+  int runs = 0;
+  const tacchi_status st = sort_count(c, &runs);
+  if (st != TACCHI_OK) return st;
+  o->sort_runs = runs - c->sort_base;
+  if (reset) {
     for (int k = 0; k < 4; ++k) {
       c->prof_ms[k] = 0;
       c->prof_n[k] = 0;
     }
+    c->sort_base = runs;
+  }
   return TACCHI_OK;
 }
 

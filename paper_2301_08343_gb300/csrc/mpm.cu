@@ -288,10 +288,16 @@ __global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer(Batch 
   const int B0x = (int)(lb % nb0) * BX, B0y = (int)((lb / nb0) % nb1) * BY,
             B0z = (int)(lb / ((long long)nb0 * nb1)) * BZ;
   const long long Ntot = b.Ntot;
-  const float inv_dx = I.inv_dx, dx = I.dx, m = I.m;
+  // the instance record is read once: stores to the particle arrays below
+  // could otherwise alias it and force reloads inside the particle loop
+  const float inv_dx = I.inv_dx, dx = I.dx, m = I.m, mu = I.mu, la = I.la;
+  const bool fix_base = I.fix_base != 0;
+  const long long node_off = I.node_off;
   const float c4 = 4.0f * dt * inv_dx;
   const float ks = 4.0f * dt * I.V0 * inv_dx;
   const int tid = threadIdx.x;
+  float4 *__restrict__ gps = b.ps;
+  const uint8_t *__restrict__ gfl = b.flags;
 
   // ---- group the block's particles by home cell
   for (int c = tid; c < P::NE; c += P::THREADS) s_cnt[c] = 0;
@@ -301,19 +307,38 @@ __global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer(Batch 
   }
   __syncthreads();
   if (n <= (uint32_t)P::MAXP) {
-    for (uint32_t l = tid; l < n; l += P::THREADS) {
-      const uint32_t p = b.idx[start + l];
-      const int ex = (int)floorf(b.u[p] - 0.5f) - (B0x - 1);
-      const int ey = (int)floorf(b.u[Ntot + p] - 0.5f) - (B0y - 1);
-      const int ez = (int)floorf(b.u[2 * Ntot + p] - 0.5f) - (B0z - 1);
-      uint32_t key = 0xFFFFFFFFu;
-      if (ex >= 0 && ey >= 0 && ez >= 0 && ex < P::EX && ey < P::EY && ez < P::EZ) {
-        const uint32_t c = (uint32_t)((ez * P::EY + ey) * P::EX + ex);
-        key = (atomicAdd(s_cnt + c, 1u) << 12) | c;  // rank, cell (< 4096)
-      } else {
-        s_overflow = 1;  // not at home: the sort invariant is broken
+    // GB particles per thread per round, so that their id and position loads
+    // are all in flight together
+    constexpr int GB = 8;
+    for (uint32_t l0 = 0; l0 < n; l0 += GB * P::THREADS) {
+      uint32_t pp[GB];
+      float4 px[GB];
+#pragma unroll
+      for (int g = 0; g < GB; ++g) {
+        const uint32_t l = l0 + g * P::THREADS + tid;
+        pp[g] = l < n ? b.idx[start + l] : 0u;
       }
-      s_key[l] = key;
+#pragma unroll
+      for (int g = 0; g < GB; ++g) {
+        const uint32_t l = l0 + g * P::THREADS + tid;
+        px[g] = l < n ? load_position(gps, pp[g]) : make_float4(0.f, 0.f, 0.f, 0.f);
+      }
+#pragma unroll
+      for (int g = 0; g < GB; ++g) {
+        const uint32_t l = l0 + g * P::THREADS + tid;
+        if (l >= n) continue;
+        const int ex = (int)floorf(px[g].x - 0.5f) - (B0x - 1);
+        const int ey = (int)floorf(px[g].y - 0.5f) - (B0y - 1);
+        const int ez = (int)floorf(px[g].z - 0.5f) - (B0z - 1);
+        uint32_t key = 0xFFFFFFFFu;
+        if (ex >= 0 && ey >= 0 && ez >= 0 && ex < P::EX && ey < P::EY && ez < P::EZ) {
+          const uint32_t c = (uint32_t)((ez * P::EY + ey) * P::EX + ex);
+          key = (atomicAdd(s_cnt + c, 1u) << 12) | c;  // rank, cell (< 4096)
+        } else {
+          s_overflow = 1;  // not at home: the sort invariant is broken
+        }
+        s_key[l] = key;
+      }
     }
   }
   __syncthreads();
@@ -327,10 +352,13 @@ __global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer(Batch 
     }
   }
   __syncthreads();
-  if (DO_P2G)
-    for (int t = tid; t < 4 * TN; t += P::THREADS) tile[t] = 0.f;
+  if (DO_P2G) {
+    float4 *tile4 = reinterpret_cast<float4 *>(tile);
+    for (int t = tid; t < TN; t += P::THREADS) tile4[t] = make_float4(0.f, 0.f, 0.f, 0.f);
+  }
   if (DO_G2P) {  // grid velocities of nodes [B0-1, B0+B+3) into the V tile
-    const float4 *gv = b.gv + I.node_off;
+    const float4 *gv = b.gv + node_off;
+#pragma unroll 4
     for (int t = tid; t < P::VN; t += P::THREADS) {
       const int x = B0x - 1 + t % VX, y = B0y - 1 + (t / VX) % VY, z = B0z - 1 + t / (VX * VY);
       float4 V = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -360,29 +388,27 @@ __global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer(Batch 
     }
     // accumulators of the cell's 27 nodes: sum of w (mass / m) and of
     // w (m v + A (X_i - x)) per axis
-    float accw[27], acc0[27], acc1[27], acc2[27];
+    float2 acc01[27], acc2w[27];  // (MG x, MG y), (MG z, sum of w)
     if (DO_P2G && grouped) {
 #pragma unroll
-      for (int e = 0; e < 27; ++e) accw[e] = acc0[e] = acc1[e] = acc2[e] = 0.f;
+      for (int e = 0; e < 27; ++e) acc01[e] = acc2w[e] = make_float2(0.f, 0.f);
     }
     // the state of particle q+1 is loaded while particle q computes
     uint32_t pn = grouped ? s_list[q0] : b.idx[start + q0];
-    float un[3] = {b.u[pn], b.u[Ntot + pn], b.u[2 * Ntot + pn]};
-    float Hnx[9];
-#pragma unroll
-    for (int e = 0; e < 9; ++e) Hnx[e] = b.Fm[e * Ntot + pn];
+    float un[3], Hnx[9];
+    load_particle(gps, pn, un, Hnx);
+    uint32_t fln = DO_G2P ? gfl[pn] : 0u;
     for (uint32_t q = q0; q < q1; ++q) {
       const uint32_t p = pn;
+      const uint32_t fl = fln;
       float u[3] = {un[0], un[1], un[2]};
       float H[9];
 #pragma unroll
       for (int e = 0; e < 9; ++e) H[e] = Hnx[e];
       if (q + 1 < q1) {
         pn = grouped ? s_list[q + 1] : b.idx[start + q + 1];
-#pragma unroll
-        for (int a = 0; a < 3; ++a) un[a] = b.u[a * Ntot + pn];
-#pragma unroll
-        for (int e = 0; e < 9; ++e) Hnx[e] = b.Fm[e * Ntot + pn];
+        load_particle(gps, pn, un, Hnx);
+        if (DO_G2P) fln = gfl[pn];
       }
       int bs[3];
 #pragma unroll
@@ -397,36 +423,51 @@ __global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer(Batch 
         bspline3(f[0], wx, dpx);
         bspline3(f[1], wy, dpy);
         bspline3(f[2], wz, dpz);
-        float wdx[3];
+        // x and y velocity components in packed FP32 pairs (two lanes per
+        // instruction), z in scalars
+        float2 wxd[3], wdxd[3];
 #pragma unroll
-        for (int i = 0; i < 3; ++i) wdx[i] = wx[i] * dpx[i];
-#pragma unroll
-        for (int e = 0; e < 9; ++e) Bm[e] = 0.f;
-        v[0] = v[1] = v[2] = 0.f;
+        for (int i = 0; i < 3; ++i) {
+          wxd[i] = make_float2(wx[i], wx[i]);
+          wdxd[i] = make_float2(wx[i] * dpx[i], wx[i] * dpx[i]);
+        }
+        const float2 z2 = make_float2(0.f, 0.f);
+        float2 vxy = z2, b0xy = z2, b1xy = z2, b2xy = z2;  // v (Eq. 7), Bm columns (Eq. 8), rows x, y
+        float vz = 0.f, b0z = 0.f, b1z = 0.f, b2z = 0.f;    // row z
         // home cells lie inside the V tile; clamp only as a guard
         const int vx = clampi(bs[0] - (B0x - 1), 0, VX - 3), vy = clampi(bs[1] - (B0y - 1), 0, VY - 3),
-                  vz = clampi(bs[2] - (B0z - 1), 0, P::VZ - 3);
-        if (vx != bs[0] - (B0x - 1) || vy != bs[1] - (B0y - 1) || vz != bs[2] - (B0z - 1)) err |= ERRBIT_CFL;
+                  vz0 = clampi(bs[2] - (B0z - 1), 0, P::VZ - 3);
+        if (vx != bs[0] - (B0x - 1) || vy != bs[1] - (B0y - 1) || vz0 != bs[2] - (B0z - 1)) err |= ERRBIT_CFL;
 #pragma unroll
         for (int k = 0; k < 3; ++k)
 #pragma unroll
           for (int j = 0; j < 3; ++j) {
-            const float4 *row = vt + ((vz + k) * VY + (vy + j)) * VX + vx;
+            const float4 *row = vt + ((vz0 + k) * VY + (vy + j)) * VX + vx;
             const float4 V0 = row[0], V1 = row[1], V2 = row[2];
             // row sums over i: s = sum w_i V_i, t = sum w_i (i - f_x) V_i
-            const float s0 = wx[0] * V0.x + wx[1] * V1.x + wx[2] * V2.x;
-            const float s1 = wx[0] * V0.y + wx[1] * V1.y + wx[2] * V2.y;
-            const float s2 = wx[0] * V0.z + wx[1] * V1.z + wx[2] * V2.z;
-            const float t0 = wdx[0] * V0.x + wdx[1] * V1.x + wdx[2] * V2.x;
-            const float t1 = wdx[0] * V0.y + wdx[1] * V1.y + wdx[2] * V2.y;
-            const float t2 = wdx[0] * V0.z + wdx[1] * V1.z + wdx[2] * V2.z;
+            float2 sxy = __fmul2_rn(wxd[0], make_float2(V0.x, V0.y));
+            float2 txy = __fmul2_rn(wdxd[0], make_float2(V0.x, V0.y));
+            sxy = __ffma2_rn(wxd[1], make_float2(V1.x, V1.y), sxy);
+            txy = __ffma2_rn(wdxd[1], make_float2(V1.x, V1.y), txy);
+            sxy = __ffma2_rn(wxd[2], make_float2(V2.x, V2.y), sxy);
+            txy = __ffma2_rn(wdxd[2], make_float2(V2.x, V2.y), txy);
+            const float sz = wx[0] * V0.z + wx[1] * V1.z + wx[2] * V2.z;
+            const float tz = wdxd[0].x * V0.z + wdxd[1].x * V1.z + wdxd[2].x * V2.z;
             const float wjk = wy[j] * wz[k];
             const float wjy = wjk * dpy[j], wjz = wjk * dpz[k];
-            v[0] += wjk * s0; v[1] += wjk * s1; v[2] += wjk * s2;               // Eq. 7
-            Bm[0] += wjk * t0; Bm[3] += wjk * t1; Bm[6] += wjk * t2;            // Eq. 8
-            Bm[1] += wjy * s0; Bm[4] += wjy * s1; Bm[7] += wjy * s2;
-            Bm[2] += wjz * s0; Bm[5] += wjz * s1; Bm[8] += wjz * s2;
+            vxy = __ffma2_rn(make_float2(wjk, wjk), sxy, vxy);      // Eq. 7
+            b0xy = __ffma2_rn(make_float2(wjk, wjk), txy, b0xy);    // Eq. 8
+            b1xy = __ffma2_rn(make_float2(wjy, wjy), sxy, b1xy);
+            b2xy = __ffma2_rn(make_float2(wjz, wjz), sxy, b2xy);
+            vz += wjk * sz;
+            b0z += wjk * tz;
+            b1z += wjy * sz;
+            b2z += wjz * sz;
           }
+        v[0] = vxy.x; v[1] = vxy.y; v[2] = vz;
+        Bm[0] = b0xy.x; Bm[1] = b1xy.x; Bm[2] = b2xy.x;
+        Bm[3] = b0xy.y; Bm[4] = b1xy.y; Bm[5] = b2xy.y;
+        Bm[6] = b0z; Bm[7] = b1z; Bm[8] = b2z;
         // Eq. 9: F <- (I + dt C) F, i.e. H <- H + dt C (I + H), C = 4/dx Bm
         float Hn[9];
 #pragma unroll
@@ -440,15 +481,11 @@ __global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer(Batch 
           }
 #pragma unroll
         for (int e = 0; e < 9; ++e) H[e] = Hn[e];
-        if (I.fix_base && (b.flags[p] & 1)) v[0] = v[1] = v[2] = 0.f;  // Eq. 10
+        if (fix_base && (fl & 1u)) v[0] = v[1] = v[2] = 0.f;  // Eq. 10
 #pragma unroll
         for (int a = 0; a < 3; ++a) u[a] = u[a] + dt * inv_dx * v[a];  // Eq. 11
         if (!(isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]))) err |= ERRBIT_NUMERICAL;
-        b.u[p] = u[0];
-        b.u[Ntot + p] = u[1];
-        b.u[2 * Ntot + p] = u[2];
-#pragma unroll
-        for (int e = 0; e < 9; ++e) b.Fm[e * Ntot + p] = H[e];
+        store_particle(gps, p, u, H);
         if (!DO_P2G) {
 #pragma unroll
           for (int a = 0; a < 3; ++a) b.v[a * Ntot + p] = v[a];
@@ -477,7 +514,7 @@ __global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer(Batch 
         // MG_i += w (m v + A (X_i - x)),  A (X_i - x) = Abar (i - f),
         // Abar = dx (m C - dt V0 (4/dx^2) tau) = 4 m Bm - (4 dt V0 / dx) tau.
         float tau[9];
-        const float Jm1 = kirchhoff_stress(H, I.mu, I.la, tau);
+        const float Jm1 = kirchhoff_stress(H, mu, la, tau);
         if (!(1.0f + Jm1 > 0.f)) err |= ERRBIT_NUMERICAL;
         float A[9];
 #pragma unroll
@@ -495,31 +532,36 @@ __global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer(Batch 
           bspline3(f[0], wx, dpx);
           bspline3(f[1], wy, dpy);
           bspline3(f[2], wz, dpz);
-          float ax[3][3], ay[3][3], az[3][3];
+          // packed pairs: (x, y) momentum components, and (z, mass weight)
+          // with 1 in the second lane, so one FFMA2 adds w to the mass sum
+          const float2 Axy0 = make_float2(A[0], A[3]), Axy1 = make_float2(A[1], A[4]),
+                       Axy2 = make_float2(A[2], A[5]);
+          float2 axy[3], ayxy[3], azxy[3];
+          float axz[3], ayz[3], azz[3];
 #pragma unroll
-          for (int i = 0; i < 3; ++i)
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-              ax[i][a] = A[a * 3 + 0] * dpx[i];
-              ay[i][a] = A[a * 3 + 1] * dpy[i];
-              az[i][a] = A[a * 3 + 2] * dpz[i];
-            }
+          for (int i = 0; i < 3; ++i) {
+            axy[i] = __fmul2_rn(Axy0, make_float2(dpx[i], dpx[i]));
+            ayxy[i] = __fmul2_rn(Axy1, make_float2(dpy[i], dpy[i]));
+            azxy[i] = __fmul2_rn(Axy2, make_float2(dpz[i], dpz[i]));
+            axz[i] = A[6] * dpx[i];
+            ayz[i] = A[7] * dpy[i];
+            azz[i] = A[8] * dpz[i];
+          }
+          const float2 mvxy = make_float2(mv[0], mv[1]);
 #pragma unroll
           for (int k = 0; k < 3; ++k)
 #pragma unroll
             for (int j = 0; j < 3; ++j) {
               const float wjk = wy[j] * wz[k];
-              const float r0 = mv[0] + ay[j][0] + az[k][0];
-              const float r1 = mv[1] + ay[j][1] + az[k][1];
-              const float r2 = mv[2] + ay[j][2] + az[k][2];
+              const float2 wjk2 = make_float2(wjk, wjk);
+              const float2 rxy = __fadd2_rn(__fadd2_rn(mvxy, ayxy[j]), azxy[k]);
+              const float rz = mv[2] + ayz[j] + azz[k];
 #pragma unroll
               for (int i = 0; i < 3; ++i) {
                 const int e = (k * 3 + j) * 3 + i;
-                const float w = wx[i] * wjk;
-                accw[e] += w;                        // Eq. 2 (/ m)
-                acc0[e] += w * (r0 + ax[i][0]);      // Eqs. 3-5
-                acc1[e] += w * (r1 + ax[i][1]);
-                acc2[e] += w * (r2 + ax[i][2]);
+                const float2 w2 = __fmul2_rn(make_float2(wx[i], wx[i]), wjk2);
+                acc01[e] = __ffma2_rn(w2, __fadd2_rn(rxy, axy[i]), acc01[e]);          // Eqs. 3-5
+                acc2w[e] = __ffma2_rn(w2, make_float2(rz + axz[i], 1.0f), acc2w[e]);  // and Eq. 2 (/ m)
               }
             }
         } else {
@@ -546,17 +588,17 @@ __global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer(Batch 
           for (int i = 0; i < 3; ++i) {
             const int e = (k * 3 + j) * 3 + i;
             float *tt = t + (k * TY + j) * TX + i;
-            atomicAdd(tt, accw[e]);
-            atomicAdd(tt + TN, acc0[e]);
-            atomicAdd(tt + 2 * TN, acc1[e]);
-            atomicAdd(tt + 3 * TN, acc2[e]);
+            atomicAdd(tt, acc2w[e].y);
+            atomicAdd(tt + TN, acc01[e].x);
+            atomicAdd(tt + 2 * TN, acc01[e].y);
+            atomicAdd(tt + 3 * TN, acc2w[e].x);
           }
     }
   }
   __syncthreads();
   if (DO_G2P && tid == 0 && s_moved) *b.movers = 1;
   if (DO_P2G) {
-    float4 *gmm = b.gmm + I.node_off;
+    float4 *gmm = b.gmm + node_off;
     for (int t = tid; t < TN; t += P::THREADS) {
       const float wsum = tile[t];
       if (wsum == 0.f) continue;
@@ -574,26 +616,33 @@ __global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer(Batch 
 // block size, clamped into the instance's block grid.
 __device__ __forceinline__ uint32_t particle_block(const Batch &b, const Instance &I, SortBlock blk,
                                                    long long p) {
-  const int bx = clampi((int)floorf(b.u[p] - 0.5f), 0, I.G[0] - 1) / blk.x;
-  const int by = clampi((int)floorf(b.u[b.Ntot + p] - 0.5f), 0, I.G[1] - 1) / blk.y;
-  const int bz = clampi((int)floorf(b.u[2 * b.Ntot + p] - 0.5f), 0, I.G[2] - 1) / blk.z;
+  const float4 u = load_position(b.ps, p);
+  const int bx = clampi((int)floorf(u.x - 0.5f), 0, I.G[0] - 1) / blk.x;
+  const int by = clampi((int)floorf(u.y - 0.5f), 0, I.G[1] - 1) / blk.y;
+  const int bz = clampi((int)floorf(u.z - 0.5f), 0, I.G[2] - 1) / blk.z;
   const int cx = clampi(bx, 0, I.nb[0] - 1), cy = clampi(by, 0, I.nb[1] - 1), cz = clampi(bz, 0, I.nb[2] - 1);
   return (uint32_t)(I.block_off + ((long long)cz * I.nb[1] + cy) * I.nb[0] + cx);
 }
 
+// The sort kernels run on a small grid-stride grid: most substeps no particle
+// has left its block and they only read the flag and return, which must cost
+// a few microseconds, not a launch of one CTA per 256 particles.
 __global__ void __launch_bounds__(256) k_sort_keys(Batch b, SortBlock blk, int force) {
   if (!force && *(volatile int *)b.movers == 0) return;
-  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool valid = p < b.Ntot;
-  uint32_t key = 0xFFFFFFFFu;
-  if (valid) {
-    const int ii = find_instance(b.part_offs, b.n_inst, p);
-    key = particle_block(b, b.inst[ii], blk, p);
-    b.key[p] = key;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < b.Ntot; base += stride) {
+    const long long p = base + threadIdx.x;  // base is warp-uniform
+    const bool valid = p < b.Ntot;
+    uint32_t key = 0xFFFFFFFFu;
+    if (valid) {
+      const int ii = find_instance(b.part_offs, b.n_inst, p);
+      key = particle_block(b, b.inst[ii], blk, p);
+      b.key[p] = key;
+    }
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
+    const int leader = __ffs(peers) - 1;
+    if (valid && (int)(threadIdx.x & 31) == leader) atomicAdd(b.bcount + key, (uint32_t)__popc(peers));
   }
-  const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
-  const int leader = __ffs(peers) - 1;
-  if (valid && (int)(threadIdx.x & 31) == leader) atomicAdd(b.bcount + key, (uint32_t)__popc(peers));
 }
 
 // Exclusive scan of the block counts by one CTA of 1024 threads; also sets
@@ -636,21 +685,70 @@ __global__ void __launch_bounds__(1024) k_sort_scan(Batch b, int force) {
     b.bcount[i] = 0u;
     run += c;
   }
-  if (threadIdx.x == T - 1) b.bstart[n] = run;
+  if (threadIdx.x == T - 1) {
+    b.bstart[n] = run;
+    b.movers[1] += 1;  // sorts that did work, read by the profile
+  }
 }
 
 __global__ void __launch_bounds__(256) k_sort_scatter(Batch b, int force) {
   if (!force && *(volatile int *)b.movers == 0) return;
-  const long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const bool valid = p < b.Ntot;
-  const uint32_t key = valid ? b.key[p] : 0xFFFFFFFFu;
-  const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
+  const long long stride = (long long)gridDim.x * blockDim.x;
   const int lane = threadIdx.x & 31;
-  const int leader = __ffs(peers) - 1;
-  uint32_t base = 0;
-  if (valid && lane == leader) base = atomicAdd(b.cursor + key, (uint32_t)__popc(peers));
-  base = __shfl_sync(0xFFFFFFFFu, base, leader);
-  if (valid) b.idx[base + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)p;
+  for (long long base = (long long)blockIdx.x * blockDim.x; base < b.Ntot; base += stride) {
+    const long long p = base + threadIdx.x;
+    const bool valid = p < b.Ntot;
+    const uint32_t key = valid ? b.key[p] : 0xFFFFFFFFu;
+    const unsigned peers = __match_any_sync(0xFFFFFFFFu, key);
+    const int leader = __ffs(peers) - 1;
+    uint32_t base_slot = 0;
+    if (valid && lane == leader) base_slot = atomicAdd(b.cursor + key, (uint32_t)__popc(peers));
+    base_slot = __shfl_sync(0xFFFFFFFFu, base_slot, leader);
+    if (valid) b.idx[base_slot + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)p;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Conversion between the particle records and the structure-of-arrays layout
+// of the C ABI.
+__global__ void __launch_bounds__(256) k_pack_state(float4 *ps, long long o, long long n, const float *u,
+                                                   const float *Fm) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  float x[3], H[9];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) x[a] = u[a * n + q];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) H[e] = Fm ? Fm[e * n + q] : 0.f;
+  store_particle(ps, o + q, x, H);
+}
+
+__global__ void __launch_bounds__(256) k_unpack_state(const float4 *ps, long long o, long long n, float *u,
+                                                     float *Fm) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  float x[3], H[9];
+  load_particle(ps, o + q, x, H);
+  if (u)
+#pragma unroll
+    for (int a = 0; a < 3; ++a) u[a * n + q] = x[a];
+  if (Fm)
+#pragma unroll
+    for (int e = 0; e < 9; ++e) Fm[e * n + q] = H[e];
+}
+
+cudaError_t launch_pack_state(float4 *ps, long long o, long long n, const float *u, const float *Fm,
+                              cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_pack_state<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ps, o, n, u, Fm);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_unpack_state(const float4 *ps, long long o, long long n, float *u, float *Fm,
+                                cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_unpack_state<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(ps, o, n, u, Fm);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------
@@ -714,7 +812,15 @@ cudaError_t launch_transfer(const Batch &b, SortBlock blk, int mode, float dt, c
 
 cudaError_t launch_sort(const Batch &b, SortBlock blk, int force, cudaStream_t st) {
   if (b.Ntot == 0) return cudaSuccess;
-  const unsigned gp = (unsigned)((b.Ntot + 255) / 256);
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) !=
+                                                   cudaSuccess || sms <= 0)
+      sms = 152;
+  }
+  const long long full = (b.Ntot + 255) / 256;
+  const unsigned gp = (unsigned)(full < 8LL * sms ? full : 8LL * sms);  // 8 CTAs of 256 fill an SM
   k_sort_keys<<<gp, 256, 0, st>>>(b, blk, force);
   k_sort_scan<<<1, 1024, 0, st>>>(b, force);
   k_sort_scatter<<<gp, 256, 0, st>>>(b, force);

@@ -30,7 +30,13 @@ __global__ void __launch_bounds__(256) k_hm_splat(HeightmapArgs a) {
   const int s = blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= a.Ns) return;
   const uint32_t p = a.surf[s];
-  const float ux = a.u[p], uy = a.u[a.Ntot + p], uz = a.u[2 * a.Ntot + p];
+  float ux, uy, uz;
+  if (a.ps) {
+    const float4 q = load_position(a.ps, p);
+    ux = q.x; uy = q.y; uz = q.z;
+  } else {
+    ux = a.u[p]; uy = a.u[a.Ntot + p]; uz = a.u[2 * a.Ntot + p];
+  }
   // rest top plane plus the particle's vertical displacement (metres)
   const float h = a.z_top + a.dx * (uz - a.z0[s]);
   if (!(isfinite(ux) && isfinite(uy) && isfinite(h))) return;
@@ -142,9 +148,10 @@ __global__ void __launch_bounds__(256) k_dispmap(DispMapArgs a) {
   j = min(max(j, 0), 2 * a.ny - 1);
   const long long s = ((long long)(j >> 1) * a.nx + (i >> 1)) * 4 + (j & 1) * 2 + (i & 1);
   const uint32_t p = a.surf[s];
-#pragma unroll
-  for (int d = 0; d < 3; ++d)
-    a.out[3 * e + d] = a.dx * (a.u[d * a.Ntot + p] - a.rest[d * a.rest_stride + s]);
+  const float4 q = load_position(a.ps, p);
+  a.out[3 * e + 0] = a.dx * (q.x - a.rest[s]);
+  a.out[3 * e + 1] = a.dx * (q.y - a.rest[a.rest_stride + s]);
+  a.out[3 * e + 2] = a.dx * (q.z - a.rest[2 * a.rest_stride + s]);
 }
 
 cudaError_t launch_dispmap(const DispMapArgs &a, cudaStream_t st) {

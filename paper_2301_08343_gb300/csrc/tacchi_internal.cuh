@@ -2,11 +2,15 @@
 // the GB300 Tacchi library.  Included only by the library's own .cu files.
 //
 // Layout in HBM (all instances of a batch concatenated):
-//   particles (global index p, total Ntot), structure of arrays:
-//     u  [3][Ntot]  position in grid-cell units from the instance's node 0
-//     Fm [9][Ntot]  F - I, row-major
-//     v  [3][Ntot], C [9][Ntot]  only written at the end of a step call and
-//                                read by the first transfer of the next call
+//   particles (global index p, total Ntot):
+//     ps [Ntot][3] float4  the per-substep state as one 48-byte record:
+//                  (u0, u1, u2, H0) (H1, H2, H3, H4) (H5, H6, H7, H8), with
+//                  u the position in grid-cell units from the instance's
+//                  node 0 and H = F - I row-major; one thread loads or stores
+//                  a particle with three 16-byte accesses
+//     v  [3][Ntot], C [9][Ntot]  structure of arrays, only written at the
+//                  end of a step call and read by the first transfer of the
+//                  next call
 //     flags [Ntot]  bit0 base set (Eq. 10), bit1 top-layer surface particle
 //   sort: idx [Ntot] particle ids grouped by grid block, bstart [Nblk+1],
 //     key [Ntot], bcount/cursor [Nblk]
@@ -73,12 +77,32 @@ struct Batch {
   const uint32_t *block_inst; // [Nblk] instance of each global block
   int n_inst;
   long long Ntot, Nnodes, Nblk;
-  float *u, *Fm, *v, *C;
+  float4 *ps;
+  float *v, *C;
   const uint8_t *flags;
   uint32_t *idx, *key, *bstart, *bcount, *cursor;
   float4 *gmm, *gv;
-  int *err, *movers;
+  int *err;
+  int *movers;  // [0] a particle left its block in the last transfer; [1] sorts that did work
 };
+
+// Particle records (see the layout above).
+__device__ __forceinline__ void load_particle(const float4 *ps, long long p, float u[3], float H[9]) {
+  const float4 *r = ps + 3 * p;
+  const float4 a = r[0], b = r[1], c = r[2];
+  u[0] = a.x; u[1] = a.y; u[2] = a.z;
+  H[0] = a.w; H[1] = b.x; H[2] = b.y; H[3] = b.z; H[4] = b.w;
+  H[5] = c.x; H[6] = c.y; H[7] = c.z; H[8] = c.w;
+}
+
+__device__ __forceinline__ void store_particle(float4 *ps, long long p, const float u[3], const float H[9]) {
+  float4 *r = ps + 3 * p;
+  r[0] = make_float4(u[0], u[1], u[2], H[0]);
+  r[1] = make_float4(H[1], H[2], H[3], H[4]);
+  r[2] = make_float4(H[5], H[6], H[7], H[8]);
+}
+
+__device__ __forceinline__ float4 load_position(const float4 *ps, long long p) { return ps[3 * p]; }
 
 // Largest i with offs[i] <= x (offs ascending, offs[0] = 0).
 __device__ __forceinline__ int find_instance(const long long *offs, int n, long long x) {
@@ -148,11 +172,17 @@ cudaError_t launch_grid_update(const Batch &b, int substep, float dt, int clear,
 cudaError_t launch_transfer(const Batch &b, SortBlock blk, int mode, float dt, cudaStream_t st);
 cudaError_t launch_sort(const Batch &b, SortBlock blk, int force, cudaStream_t st);
 cudaError_t prepare_transfer(SortBlock blk);
+// Particles [o, o + n) of the records from / to structure-of-arrays u [3][n]
+// and Fm [9][n] (F - I); a null Fm packs F = I, a null output is skipped.
+cudaError_t launch_pack_state(float4 *ps, long long o, long long n, const float *u, const float *Fm,
+                              cudaStream_t st);
+cudaError_t launch_unpack_state(const float4 *ps, long long o, long long n, float *u, float *Fm, cudaStream_t st);
 
 enum : int { XFER_P2G = 1, XFER_G2P = 2, XFER_FUSED = 3 };
 
 struct HeightmapArgs {
-  const float *u;         // particle positions [3][Ntot]
+  const float4 *ps;       // particle records [Ntot][3], or null: then
+  const float *u;         // particle positions [3][Ntot] (caller's arrays)
   long long Ntot;
   const uint32_t *surf;   // [Ns] global particle ids of top-layer particles
   const float *z0;        // [Ns] rest z (cells)
@@ -169,7 +199,7 @@ cudaError_t launch_heightmap(const HeightmapArgs &a, cudaStream_t st);
 // rest sub-cell contains the pixel centre (lattice index (i, j) -> surface
 // index ((j/2) nx + i/2) 4 + (j%2) 2 + i%2).
 struct DispMapArgs {
-  const float *u;          // [3][Ntot] positions (cells)
+  const float4 *ps;        // particle records [Ntot][3] (positions in cells)
   long long Ntot;
   const uint32_t *surf;    // [Ns] particle ids of the instance's surface list
   const float *rest;       // [3][Ns_tot] rest positions (cells), instance slice

@@ -335,3 +335,26 @@ def test_profiling_counts_every_kernel_of_a_step():
     assert all(p[k] > 0 for k in ("fused_ms", "grid_ms", "edge_ms", "sort_ms"))
     g.step(5, 1e-5)
     assert g.profile()["fused_launches"] == 0
+
+
+def test_sort_runs_only_when_a_particle_leaves_its_block():
+    import paper_2301_08343_gb300 as T
+    b = W.Block(6, 6, 2, 0.5e-3, seed=5)
+    g = T.Tacchi(b.extent_m, b.dx, b.E, b.nu, b.rho, seed=b.seed, pad_side=8, fix_base=False)
+    u0 = g.get_state()["u"].clone()
+    g.set_profiling(True)
+    g.step(20, 1e-5)  # at rest: nobody moves, every sort only checks the flag
+    p = g.profile(reset=True)
+    assert p["sort_launches"] == 20 and p["sort_runs"] == 0
+    # uniform drift of 0.3 cells per substep along x: exact under APIC; within
+    # 10 substeps the particles near each block's upper x face leave its slack
+    v = torch.zeros_like(u0)
+    v[0] = 0.3 * b.dx / 1e-5
+    g.set_state(u0, v)
+    g.step(10, 1e-5)
+    p = g.profile(reset=True)
+    assert g.status() == 0
+    assert 1 <= p["sort_runs"] <= 10
+    u = g.get_state()["u"]
+    assert torch.allclose(u[0] - u0[0], torch.full_like(u0[0], 3.0), atol=1e-4)
+    g.set_profiling(False)
