@@ -12,10 +12,12 @@
 //   1x1 convolution to the output channels (FP32).  Loss: mean squared error.
 //
 // Kernels:
-//   k_conv3x3      implicit-GEMM 3x3 convolution, rows = pixels, columns =
-//                  output channels, K = 9 x C_in; mma.sync m16n8k16 BF16 with
-//                  FP32 accumulators, cp.async double buffering, bias+ReLU
-//                  epilogue.  The data gradient runs the same kernel on the
+//   k_conv3x3_tc   implicit-GEMM 3x3 convolution on the 5th-generation tensor
+//                  cores: rows = pixels, columns = output channels, K = 9 x
+//                  C_in; tcgen05.mma BF16 x BF16 -> FP32 in tensor memory,
+//                  operands staged by cp.async in a 4-stage ring released by
+//                  MMA-completion mbarriers, bias+ReLU+BF16 epilogue from
+//                  tcgen05.ld.  The data gradient runs the same kernel on the
 //                  output gradient with the weights flipped and transposed.
 //   k_conv3x3_wgrad  weight gradient: rows = (tap, C_in), columns = C_out,
 //                  K = pixels, split over pixel chunks with FP32 atomics.
@@ -50,11 +52,6 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
-__device__ __forceinline__ void ldsm_x4(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3, const void *p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-               : "r"(smem_addr(p)));
-}
 __device__ __forceinline__ void ldsm_x4_t(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3, const void *p) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
                : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
@@ -70,104 +67,215 @@ __device__ __forceinline__ void mma_bf16(float d[4], const uint32_t a[4], uint32
 }
 
 // ---------------------------------------------------------------------------
-// Y[m][co] = act(b[co] + sum_k A[m][k] Wt[k][co]); A[m][k] = X at pixel m
-// shifted by tap(k), channel ci(k); k = tap * Cin + ci, tap = 3 dy + dx.
-// Requires Cin % 32 == 0 and Cout % BN == 0.
-template <int BN>
-__global__ void __launch_bounds__((BN / 32) * 4 * 32) k_conv3x3(const bf16 *__restrict__ X, const bf16 *__restrict__ Wt,
-                                                              const float *__restrict__ bias, bf16 *__restrict__ Y,
-                                                              int nimg, int H, int W, int Cin, int Cout, int relu) {
-  constexpr int BM = 128, BK = 32, WARPS_M = 4, THREADS = (BN / 32) * WARPS_M * 32;
-  constexpr int AS = BK + 8, BS = BN + 8;
-  __shared__ __align__(16) bf16 sA[2][BM * AS];
-  __shared__ __align__(16) bf16 sB[2][BK * BS];
-  const int M = nimg * H * W;
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-  const int nk = 9 * Cin / BK;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = warp % WARPS_M, wn = warp / WARPS_M;
+// 5th-generation tensor cores (tcgen05): operands in shared memory described
+// by matrix descriptors, the FP32 accumulator in tensor memory (TMEM).
+//
+// Shared-memory operand layout (K-major, no swizzle): the tile is a grid of
+// "core matrices" of 8 rows x 16 bytes (8 BF16 along K), each stored as 128
+// contiguous bytes (row r at +16 r).  With K_CH = BK / 8 core matrices per
+// 8-row group along K, core matrix (row group g, K chunk j) sits at byte
+// (g * K_CH + j) * 128: the descriptor's leading-dimension offset (between K
+// neighbours) is 128 B and its stride-dimension offset (between 8-row groups)
+// K_CH * 128 B.
+namespace tc {
 
-  auto load_stage = [&](int kk, int buf) {
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
+  d |= (uint64_t)1 << 46;  // descriptor version; base offset 0, no swizzle
+  return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), A and
+// B BF16 (bits 7-9 and 10-12 = 1), both K-major, N / 8 at bit 17, M / 16 at
+// bit 24.
+template <int M, int N>
+__device__ __forceinline__ constexpr uint32_t instr_desc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count));
+}
+// Bounded wait for the phase with the given parity; false when it gave up.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+  for (int it = 0; it < (1 << 22); ++it) {
+    uint32_t done;
+    asm volatile(
+        "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
+
+// D (TMEM) (+)= A (smem) * B (smem)^T, issued by one thread.
+__device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// Arrive on the mbarrier once every MMA this thread issued so far is done.
+__device__ __forceinline__ void commit(uint64_t *bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+                   smem_addr(bar))
+               : "memory");
+}
+// 16 consecutive FP32 columns of this thread's TMEM lane.
+__device__ __forceinline__ void ld16(uint32_t taddr, float v[16]) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+  for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+}  // namespace tc
+
+// ---------------------------------------------------------------------------
+// Y[m][co] = act(b[co] + sum_k A[m][k] Wk[co][k]) for one 3x3 'same'
+// convolution as an implicit GEMM: row m = pixel (n, y, x), K = 9 taps x Cin,
+// A[m][k] = X at pixel m shifted by tap(k) = 3 dy + dx in channel ci(k)
+// (zero outside the image), k = tap * Cin + ci; Wk is K-major [Cout][9 Cin].
+// One CTA of 128 threads computes 128 pixels x N output channels: each stage
+// copies a 32-channel slice of one tap (A: 128 x 64 B, B: N x 64 B) with
+// cp.async, one thread issues two 128 x N x 16 MMAs into TMEM and commits
+// them to the stage's mbarrier, which frees the stage for a later copy.  The
+// epilogue reads TMEM lane = pixel, adds the bias, applies ReLU and stores
+// BF16.  Requires Cin % 32 == 0, Cout % N == 0.  A wait that gives up sets
+// *err, abandons the tile and frees TMEM.
+template <int N, int STAGES>
+__global__ void __launch_bounds__(128) k_conv3x3_tc(const bf16 *__restrict__ X, const bf16 *__restrict__ Wk,
+                                                    const float *__restrict__ bias, bf16 *__restrict__ Y, int nimg,
+                                                    int H, int W, int Cin, int Cout, int relu, int *err) {
+  constexpr int BM = 128, BK = 32, KCH = BK / 8;
+  constexpr int A_BYTES = BM * BK * 2, B_BYTES = N * BK * 2, STAGE = A_BYTES + B_BYTES;
+  constexpr int TCOLS = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
+  static_assert(N % 16 == 0 && N >= 32 && N <= 256, "UMMA N for M = 128");
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ __align__(8) uint64_t bar[STAGES];
+  __shared__ uint32_t tmem_base;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int M = nimg * H * W;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * N;
+  const int nk = 9 * Cin / BK;
+  const long long ldw = 9LL * Cin;
+
+  // this thread copies the A row of pixel m0 + tid
+  const int m = m0 + tid;
+  const bool mvalid = m < M;
+  const int px = mvalid ? m % W : 0, py = mvalid ? (m / W) % H : 0, pimg = mvalid ? m / (W * H) : 0;
+  auto load = [&](int kk, int buf) {
     const int k0 = kk * BK;
     const int tap = k0 / Cin, ci0 = k0 % Cin;
-    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-    for (int c = tid; c < BM * 4; c += THREADS) {
-      const int r = c >> 2, part = c & 3;
-      const int m = m0 + r;
-      bool valid = false;
-      const bf16 *src = X;
-      if (m < M) {
-        const int x = m % W, y = (m / W) % H, n = m / (W * H);
-        const int ys = y + dy, xs = x + dx;
-        if (ys >= 0 && ys < H && xs >= 0 && xs < W) {
-          valid = true;
-          src = X + (((long long)n * H + ys) * W + xs) * Cin + ci0 + part * 8;
-        }
-      }
-      cp_async16(&sA[buf][r * AS + part * 8], src, valid);
+    const int ys = py + tap / 3 - 1, xs = px + tap % 3 - 1;
+    const bool v = mvalid && ys >= 0 && ys < H && xs >= 0 && xs < W;
+    const bf16 *src = v ? X + (((long long)pimg * H + ys) * W + xs) * Cin + ci0 : X;
+    unsigned char *sa = smem + buf * STAGE;
+    unsigned char *sb = sa + A_BYTES;
+#pragma unroll
+    for (int j = 0; j < KCH; ++j) cp_async16(sa + ((tid >> 3) * KCH + j) * 128 + (tid & 7) * 16, src + 8 * j, v);
+    for (int c = tid; c < N * KCH; c += 128) {
+      const int row = c / KCH, j = c % KCH;
+      cp_async16(sb + ((row >> 3) * KCH + j) * 128 + (row & 7) * 16, Wk + (long long)(n0 + row) * ldw + k0 + 8 * j,
+                 true);
     }
-    for (int c = tid; c < BK * (BN / 8); c += THREADS) {
-      const int r = c / (BN / 8), part = c % (BN / 8);
-      cp_async16(&sB[buf][r * BS + part * 8], Wt + (long long)(k0 + r) * Cout + n0 + part * 8, true);
-    }
-    cp_async_commit();
   };
 
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
-
-  load_stage(0, 0);
-  for (int kk = 0; kk < nk; ++kk) {
-    if (kk + 1 < nk) {
-      load_stage(kk + 1, (kk + 1) & 1);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
-    __syncthreads();
-    const bf16 *a = sA[kk & 1];
-    const bf16 *b = sB[kk & 1];
-#pragma unroll
-    for (int ks = 0; ks < BK; ks += 16) {
-      uint32_t af[2][4], bfr[4][2];
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-        ldsm_x4(af[i][0], af[i][1], af[i][2], af[i][3],
-                a + (wm * 32 + i * 16 + (lane & 15)) * AS + ks + (lane >> 4) * 8);
-#pragma unroll
-      for (int j = 0; j < 4; j += 2)
-        ldsm_x4_t(bfr[j][0], bfr[j][1], bfr[j + 1][0], bfr[j + 1][1],
-                  b + (ks + (lane & 7) + ((lane >> 3) & 1) * 8) * BS + wn * 32 + j * 8 + (lane >> 4) * 8);
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 4; ++j) mma_bf16(acc[i][j], af[i], bfr[j][0], bfr[j][1]);
-    }
-    __syncthreads();
+  if (tid == 0) {
+    for (int s2 = 0; s2 < STAGES; ++s2) tc::mbar_init(&bar[s2], 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(&tmem_base)),
+                 "r"(TCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tmem_base;
+  constexpr uint32_t IDESC = tc::instr_desc<BM, N>();
+
+  for (int s2 = 0; s2 < STAGES - 1; ++s2) {
+    if (s2 < nk) load(s2, s2);
+    cp_async_commit();
+  }
+  bool failed = false;
+  for (int kk = 0; kk < nk; ++kk) {
+    const int nxt = kk + STAGES - 1;
+    bool timed_out = false;
+    if (nxt < nk) {
+      // the stage's buffer was last read by the MMAs of stage kk - 1
+      if (kk >= 1) timed_out = !tc::mbar_wait(&bar[(kk - 1) % STAGES], (uint32_t)((kk - 1) / STAGES) & 1u);
+      load(nxt, nxt % STAGES);
+    }
+    cp_async_commit();
+    cp_async_wait<STAGES - 1>();  // stage kk has landed
+    tc::fence_async_smem();
+    if (__syncthreads_or(timed_out)) {
+      failed = true;
+      break;
+    }
+    if (tid == 0) {
+      tc::fence_after();
+      const uint32_t a0 = smem_addr(smem + (kk % STAGES) * STAGE);
+      const uint32_t b0 = a0 + A_BYTES;
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+      for (int ks = 0; ks < BK / 16; ++ks)  // K = 16 per MMA: two core matrices along K
+        tc::mma(tmem, tc::smem_desc(a0 + ks * 256, 128, KCH * 128), tc::smem_desc(b0 + ks * 256, 128, KCH * 128),
+                IDESC, (kk > 0 || ks > 0) ? 1u : 0u);
+      tc::commit(&bar[kk % STAGES]);
+    }
+  }
+  if (!failed) failed = __syncthreads_or(!tc::mbar_wait(&bar[(nk - 1) % STAGES], (uint32_t)((nk - 1) / STAGES) & 1u));
+  if (failed) {
+    if (tid == 0) atomicExch(err, 1);
+    cp_async_wait<0>();
+  } else {
+    tc::fence_after();
+    // warp w owns TMEM lanes 32 w .. 32 w + 31 = rows (pixels) of the tile
+    const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+    for (int c0 = 0; c0 < N; c0 += 16) {
+      float v[16];
+      tc::ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      if (row < M) {
+        uint32_t packed[8];
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int c = n0 + wn * 32 + j * 8 + (lane & 3) * 2;
-      const float b0 = bias ? bias[c] : 0.f, b1 = bias ? bias[c + 1] : 0.f;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int r = m0 + wm * 32 + i * 16 + (lane >> 2) + h * 8;
-        if (r >= M) continue;
-        float v0 = acc[i][j][2 * h] + b0, v1 = acc[i][j][2 * h + 1] + b1;
-        if (relu) {
-          v0 = fmaxf(v0, 0.f);
-          v1 = fmaxf(v1, 0.f);
+        for (int j = 0; j < 8; ++j) {
+          float x0 = v[2 * j] + (bias ? bias[n0 + c0 + 2 * j] : 0.f);
+          float x1 = v[2 * j + 1] + (bias ? bias[n0 + c0 + 2 * j + 1] : 0.f);
+          if (relu) {
+            x0 = fmaxf(x0, 0.f);
+            x1 = fmaxf(x1, 0.f);
+          }
+          const __nv_bfloat162 h2 = __floats2bfloat162_rn(x0, x1);
+          packed[j] = *reinterpret_cast<const uint32_t *>(&h2);
         }
-        *reinterpret_cast<__nv_bfloat162 *>(Y + (long long)r * Cout + c) = __floats2bfloat162_rn(v0, v1);
+        uint4 *dst = reinterpret_cast<uint4 *>(Y + (long long)row * Cout + n0 + c0);
+        dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+        dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
       }
     }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TCOLS) : "memory");
 }
 
 // dW[tap*Cin + ci][co] += sum over a chunk of pixels of X(shifted)[ci] * G[co].
@@ -432,8 +540,10 @@ __global__ void k_adam(float *p, const float *g, float *m, float *v, long long n
     p[e] -= lr * (mn / c1) / (sqrtf(vn / c2) + eps);
   }
 }
-// BF16 copies of a conv layer's weights: forward [tap][ci][co] (same order as
-// the FP32 master) and data-gradient [tap'][co][ci] with tap' = 8 - tap.
+// BF16 copies of a conv layer's weights, K-major for the tensor cores:
+// forward wf[co][tap * Cin + ci] and data-gradient wd[ci][tap' * Cout + co]
+// with tap' = 8 - tap (the data gradient of a 'same' 3x3 convolution is the
+// convolution of the output gradient with the flipped, transposed kernel).
 __global__ void k_weights_bf16(const float *w, bf16 *wf, bf16 *wd, int Cin_real, int Cin, int Cout) {
   GRID_STRIDE(e, 9LL * Cin * Cout) {
     const int co = (int)(e % Cout);
@@ -441,8 +551,8 @@ __global__ void k_weights_bf16(const float *w, bf16 *wf, bf16 *wd, int Cin_real,
     const int tap = (int)(e / ((long long)Cout * Cin));
     const float val = ci < Cin_real ? w[((long long)tap * Cin_real + ci) * Cout + co] : 0.f;
     const bf16 b = __float2bfloat16_rn(val);
-    wf[e] = b;
-    wd[((long long)(8 - tap) * Cout + co) * Cin + ci] = b;
+    wf[(long long)co * 9 * Cin + (long long)tap * Cin + ci] = b;
+    wd[(long long)ci * 9 * Cout + (long long)(8 - tap) * Cout + co] = b;
   }
 }
 // gradient of the padded first layer back to the real input channels
@@ -489,6 +599,7 @@ struct tacchi_nn {
   std::vector<bf16 *> pooled, gpooled;  // per encoder level < L-1
   std::vector<bf16 *> cat, gcat, gup;   // per decoder level
   float *out = nullptr, *gout = nullptr, *loss = nullptr, *h_loss = nullptr;
+  int *err = nullptr;  // device: a tensor-core wait gave up
   size_t device_bytes = 0;
 };
 
@@ -502,23 +613,54 @@ cudaError_t nalloc(tacchi_nn *n, T **ptr, size_t count) {
 }
 
 tacchi_status st_of(cudaError_t e) { return e == cudaSuccess ? TACCHI_OK : TACCHI_ERR_CUDA; }
+
+// Synchronise the network's stream and report a tensor-core wait that gave up
+// (sticky until the network is destroyed).
+tacchi_status nn_sync(tacchi_nn *n) {
+  if (cudaStreamSynchronize(n->stream) != cudaSuccess) return TACCHI_ERR_CUDA;
+  int e = 0;
+  if (cudaMemcpy(&e, n->err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return TACCHI_ERR_CUDA;
+  return e ? TACCHI_ERR_TIMEOUT : TACCHI_OK;
+}
 #define NCK(x)                                 \
   do {                                         \
     cudaError_t e_ = (x);                      \
     if (e_ != cudaSuccess) return st_of(e_);   \
   } while (0)
 
-cudaError_t conv_fwd(const bf16 *X, const bf16 *Wt, const float *bias, bf16 *Y, int nimg, int H, int W, int Cin,
-                     int Cout, int relu, cudaStream_t s) {
-  const int M = nimg * H * W;
-  if (Cout % 64 == 0) {
-    dim3 grid((M + 127) / 128, Cout / 64);
-    k_conv3x3<64><<<grid, 256, 0, s>>>(X, Wt, bias, Y, nimg, H, W, Cin, Cout, relu);
-  } else {
-    dim3 grid((M + 127) / 128, Cout / 32);
-    k_conv3x3<32><<<grid, 128, 0, s>>>(X, Wt, bias, Y, nimg, H, W, Cin, Cout, relu);
+constexpr int kConvStages = 4;
+
+template <int N>
+constexpr int conv_smem() {
+  return kConvStages * (128 * 32 * 2 + N * 32 * 2);
+}
+
+template <int N>
+cudaError_t conv_launch(const bf16 *X, const bf16 *Wk, const float *bias, bf16 *Y, int nimg, int H, int W, int Cin,
+                        int Cout, int relu, int *err, cudaStream_t s) {
+  static bool ready = false;  // the dynamic shared memory limit, once per instantiation
+  if (!ready) {
+    const cudaError_t e = cudaFuncSetAttribute(k_conv3x3_tc<N, kConvStages>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, conv_smem<N>());
+    if (e != cudaSuccess) return e;
+    ready = true;
   }
+  const long long M = (long long)nimg * H * W;
+  dim3 grid((unsigned)((M + 127) / 128), (unsigned)(Cout / N));
+  k_conv3x3_tc<N, kConvStages><<<grid, 128, conv_smem<N>(), s>>>(X, Wk, bias, Y, nimg, H, W, Cin, Cout, relu, err);
   return cudaGetLastError();
+}
+
+// Output-channel tile: the largest UMMA width (a multiple of 16, at most 256)
+// that divides Cout (a multiple of 32).
+cudaError_t conv_fwd(const bf16 *X, const bf16 *Wk, const float *bias, bf16 *Y, int nimg, int H, int W, int Cin,
+                     int Cout, int relu, int *err, cudaStream_t s) {
+  if (Cout % 256 == 0) return conv_launch<256>(X, Wk, bias, Y, nimg, H, W, Cin, Cout, relu, err, s);
+  if (Cout % 192 == 0) return conv_launch<192>(X, Wk, bias, Y, nimg, H, W, Cin, Cout, relu, err, s);
+  if (Cout % 128 == 0) return conv_launch<128>(X, Wk, bias, Y, nimg, H, W, Cin, Cout, relu, err, s);
+  if (Cout % 96 == 0) return conv_launch<96>(X, Wk, bias, Y, nimg, H, W, Cin, Cout, relu, err, s);
+  if (Cout % 64 == 0) return conv_launch<64>(X, Wk, bias, Y, nimg, H, W, Cin, Cout, relu, err, s);
+  return conv_launch<32>(X, Wk, bias, Y, nimg, H, W, Cin, Cout, relu, err, s);
 }
 
 cudaError_t conv_wgrad(const bf16 *X, const bf16 *G, float *dW, int nimg, int H, int W, int Cin, int Cout,
@@ -579,6 +721,7 @@ void release_nn(tacchi_nn *n) {
   cudaFree(n->out);
   cudaFree(n->gout);
   cudaFree(n->loss);
+  cudaFree(n->err);
   if (n->h_loss) cudaFreeHost(n->h_loss);
   delete n;
 }
@@ -595,7 +738,7 @@ tacchi_status forward(tacchi_nn *n, int batch, const float *x) {
   for (int l = 0; l < n->L; ++l) {
     for (int q = 0; q < 2; ++q, ++k) {
       ConvLayer &cl = n->convs[k];
-      NCK(conv_fwd(in, cl.wf, n->p + cl.b_off, n->act[k + 1], batch, H, W, cl.cin, cl.cout, 1, s));
+      NCK(conv_fwd(in, cl.wf, n->p + cl.b_off, n->act[k + 1], batch, H, W, cl.cin, cl.cout, 1, n->err, s));
       in = n->act[k + 1];
     }
     if (l < n->L - 1) {
@@ -618,7 +761,7 @@ tacchi_status forward(tacchi_nn *n, int batch, const float *x) {
     in = n->cat[l];
     for (int q = 0; q < 2; ++q, ++k) {
       ConvLayer &cl = n->convs[k];
-      NCK(conv_fwd(in, cl.wf, n->p + cl.b_off, n->act[k + 1], batch, H, W, cl.cin, cl.cout, 1, s));
+      NCK(conv_fwd(in, cl.wf, n->p + cl.b_off, n->act[k + 1], batch, H, W, cl.cin, cl.cout, 1, n->err, s));
       in = n->act[k + 1];
     }
   }
@@ -657,7 +800,7 @@ tacchi_status backward(tacchi_nn *n, int batch, const float *target) {
       bf16 *gin = q == 0 ? n->gact[k] : n->gcat[l];
       NCK(conv_wgrad(xin, gcur, n->g + cl.w_off, batch, H, W, cl.cin, cl.cout, s));
       NCK(bias_grad(gcur, n->g + cl.b_off, P, cl.cout, s));
-      NCK(conv_fwd(gcur, cl.wd, nullptr, gin, batch, H, W, cl.cout, cl.cin, 0, s));
+      NCK(conv_fwd(gcur, cl.wd, nullptr, gin, batch, H, W, cl.cout, cl.cin, 0, n->err, s));
       gcur = gin;
     }
     // split the concatenation gradient: upsampled part and skip part
@@ -703,7 +846,7 @@ tacchi_status backward(tacchi_nn *n, int batch, const float *target) {
         NCK(cudaGetLastError());
       } else {
         bf16 *gin = q == 0 ? n->gact[k] : n->gpooled[l - 1];
-        NCK(conv_fwd(gcur, cl.wd, nullptr, gin, batch, H, W, cl.cout, cl.cin, 0, s));
+        NCK(conv_fwd(gcur, cl.wd, nullptr, gin, batch, H, W, cl.cout, cl.cin, 0, n->err, s));
         gcur = gin;
       }
     }
@@ -821,7 +964,8 @@ tacchi_status tacchi_nn_create(int levels, const int *widths, int in_channels, i
   }
   ok = ok && nalloc(n, &n->out, B * height * width * out_channels) == cudaSuccess &&
        nalloc(n, &n->gout, B * height * width * out_channels) == cudaSuccess &&
-       nalloc(n, &n->loss, 1) == cudaSuccess && cudaMallocHost((void **)&n->h_loss, sizeof(float)) == cudaSuccess;
+       nalloc(n, &n->loss, 1) == cudaSuccess && nalloc(n, &n->err, 1) == cudaSuccess &&
+       cudaMallocHost((void **)&n->h_loss, sizeof(float)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     return fail(TACCHI_ERR_OOM);
@@ -845,6 +989,7 @@ tacchi_status tacchi_nn_create(int levels, const int *widths, int in_channels, i
   for (long long e = 0; e < (long long)widths[0] * out_channels; ++e) hp[n->head_w + e] = (float)(sdh * gauss());
   if (cudaMemcpy(n->p, hp.data(), sizeof(float) * off, cudaMemcpyHostToDevice) != cudaSuccess ||
       cudaMemset(n->m, 0, sizeof(float) * off) != cudaSuccess || cudaMemset(n->v, 0, sizeof(float) * off) != cudaSuccess ||
+      cudaMemset(n->err, 0, sizeof(int)) != cudaSuccess ||
       refresh_weights(n) != cudaSuccess || cudaStreamSynchronize(n->stream) != cudaSuccess)
     return fail(TACCHI_ERR_CUDA);
   *out = n;
@@ -862,8 +1007,7 @@ tacchi_status tacchi_nn_num_params(tacchi_nn_handle n, int64_t *out) {
 tacchi_status tacchi_nn_get_params(tacchi_nn_handle n, int which, float *host) {
   if (!n || !host || which < 0 || which > 1) return TACCHI_ERR_INVALID_ARG;
   NCK(cudaMemcpyAsync(host, which ? n->g : n->p, sizeof(float) * n->nparams, cudaMemcpyDeviceToHost, n->stream));
-  NCK(cudaStreamSynchronize(n->stream));
-  return TACCHI_OK;
+  return nn_sync(n);
 }
 
 tacchi_status tacchi_nn_set_params(tacchi_nn_handle n, const float *host) {
@@ -873,8 +1017,7 @@ tacchi_status tacchi_nn_set_params(tacchi_nn_handle n, const float *host) {
   NCK(cudaMemsetAsync(n->v, 0, sizeof(float) * n->nparams, n->stream));
   n->t = 0;
   NCK(refresh_weights(n));
-  NCK(cudaStreamSynchronize(n->stream));
-  return TACCHI_OK;
+  return nn_sync(n);
 }
 
 tacchi_status tacchi_nn_forward(tacchi_nn_handle n, int batch, const float *x_dev, float *y_dev) {
@@ -894,7 +1037,8 @@ tacchi_status tacchi_nn_gradients(tacchi_nn_handle n, int batch, const float *x_
   if (s != TACCHI_OK) return s;
   if (loss_host) {
     NCK(cudaMemcpyAsync(n->h_loss, n->loss, sizeof(float), cudaMemcpyDeviceToHost, n->stream));
-    NCK(cudaStreamSynchronize(n->stream));
+    const tacchi_status st = nn_sync(n);
+    if (st != TACCHI_OK) return st;
     *loss_host = *n->h_loss / (float)((long long)batch * n->H * n->W * n->cout);
   }
   return TACCHI_OK;
@@ -913,7 +1057,8 @@ tacchi_status tacchi_nn_train_step(tacchi_nn_handle n, int batch, const float *x
   NCK(refresh_weights(n));
   if (loss_host) {
     NCK(cudaMemcpyAsync(n->h_loss, n->loss, sizeof(float), cudaMemcpyDeviceToHost, n->stream));
-    NCK(cudaStreamSynchronize(n->stream));
+    const tacchi_status st = nn_sync(n);
+    if (st != TACCHI_OK) return st;
     *loss_host = *n->h_loss / (float)((long long)batch * n->H * n->W * n->cout);
   }
   return TACCHI_OK;
