@@ -166,16 +166,19 @@ struct XferPlan {
   static constexpr int VN = VX * VY * VZ;
   static constexpr int TX = BX + 6, TY = BY + 6, TZ = BZ + 6;       // P2G tile, nodes [B0-2, B0+B+4)
   static constexpr int TN = TX * TY * TZ;
-  static constexpr int MAXP = 16 * BX * BY * BZ;                    // particles grouped in smem
+  static constexpr int MAXP = 12 * BX * BY * BZ;                    // particles grouped in smem (1.5x nominal)
   static constexpr int PER = (NE + 1 + THREADS - 1) / THREADS;      // scan entries per thread
   // byte offsets in dynamic shared memory
   static constexpr size_t OFF_TILE = 0;                             // float [4][TN]; first u32 key[MAXP]
   static constexpr size_t OFF_V = OFF_TILE + 16 * (size_t)TN;       // float4 [VN]
   static constexpr size_t OFF_LIST = OFF_V + 16 * (size_t)VN;       // u32 [MAXP] particles by cell
-  static constexpr size_t OFF_CNT = OFF_LIST + 4 * (size_t)MAXP;    // u32 [NE] count, then start
+  static constexpr size_t OFF_PID = OFF_LIST + 4 * (size_t)MAXP;    // u32 [MAXP] particle ids in idx order
+  static constexpr size_t OFF_CNT = OFF_PID + 4 * (size_t)MAXP;     // u32 [NE] count, then start
   static constexpr size_t OFF_START = OFF_CNT + 4 * (size_t)NE;     // u32 [NE + 1]
   static constexpr size_t OFF_CELLS = OFF_START + 4 * (size_t)(NE + 1);  // u16 [NE] non-empty cells
-  static constexpr size_t BYTES = OFF_CELLS + 2 * (size_t)NE + 16;
+  // per-thread staging of the next particle record: float4 [2 slots][3][THREADS]
+  static constexpr size_t OFF_STAGE = (OFF_CELLS + 2 * (size_t)NE + 15) / 16 * 16;
+  static constexpr size_t BYTES = OFF_STAGE + 16 * 2 * 3 * (size_t)THREADS;
   static_assert(4 * TN >= MAXP, "the P2G tile doubles as the key scratch");
 };
 
@@ -254,6 +257,23 @@ __device__ __forceinline__ void scatter_particle(float *tile, int TN, int TX, in
     }
 }
 
+// 16-byte asynchronous copy global -> shared (L2 only), and its group fences.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16_zfill(void *smem, const void *gmem, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem), "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
 // Resident transfer CTAs per SM the register allocation is bounded for.
 #ifndef TACCHI_XFER_MIN_BLOCKS
 #define TACCHI_XFER_MIN_BLOCKS 2
@@ -270,6 +290,7 @@ __global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer(Batch 
   uint32_t *s_key = reinterpret_cast<uint32_t *>(smem + P::OFF_TILE);
   float4 *vt = reinterpret_cast<float4 *>(smem + P::OFF_V);
   uint32_t *s_list = reinterpret_cast<uint32_t *>(smem + P::OFF_LIST);
+  uint32_t *s_pid = reinterpret_cast<uint32_t *>(smem + P::OFF_PID);
   uint32_t *s_cnt = reinterpret_cast<uint32_t *>(smem + P::OFF_CNT);
   uint32_t *s_start = reinterpret_cast<uint32_t *>(smem + P::OFF_START);
   uint16_t *s_cells = reinterpret_cast<uint16_t *>(smem + P::OFF_CELLS);
@@ -299,6 +320,18 @@ __global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer(Batch 
   float4 *__restrict__ gps = b.ps;
   const uint8_t *__restrict__ gfl = b.flags;
 
+  // ---- grid velocities of nodes [B0-1, B0+B+3) into the V tile, copied
+  // asynchronously while the particles are grouped (zeros outside the grid)
+  if (DO_G2P) {
+    const float4 *gv = b.gv + node_off;
+    for (int t = tid; t < P::VN; t += P::THREADS) {
+      const int x = B0x - 1 + t % VX, y = B0y - 1 + (t / VX) % VY, z = B0z - 1 + t / (VX * VY);
+      const bool in = x >= 0 && y >= 0 && z >= 0 && x < G0 && y < G1 && z < G2;
+      cp_async16_zfill(vt + t, in ? gv + ((long long)z * G1 + y) * G0 + x : gv, in);
+    }
+  }
+  cp_async_commit();
+
   // ---- group the block's particles by home cell
   for (int c = tid; c < P::NE; c += P::THREADS) s_cnt[c] = 0;
   if (tid == 0) {
@@ -309,7 +342,7 @@ __global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer(Batch 
   if (n <= (uint32_t)P::MAXP) {
     // GB particles per thread per round, so that their id and position loads
     // are all in flight together
-    constexpr int GB = 8;
+    constexpr int GB = 16;
     for (uint32_t l0 = 0; l0 < n; l0 += GB * P::THREADS) {
       uint32_t pp[GB];
       float4 px[GB];
@@ -327,6 +360,7 @@ __global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer(Batch 
       for (int g = 0; g < GB; ++g) {
         const uint32_t l = l0 + g * P::THREADS + tid;
         if (l >= n) continue;
+        s_pid[l] = pp[g];
         const int ex = (int)floorf(px[g].x - 0.5f) - (B0x - 1);
         const int ey = (int)floorf(px[g].y - 0.5f) - (B0y - 1);
         const int ez = (int)floorf(px[g].z - 0.5f) - (B0z - 1);
@@ -348,7 +382,7 @@ __global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer(Batch 
     ncells = block_scan_compact<P::THREADS, P::PER>(s_cnt, s_start, s_cells, P::NE, s_warp);
     for (uint32_t l = tid; l < n; l += P::THREADS) {
       const uint32_t key = s_key[l];
-      s_list[s_start[key & 0xFFFu] + (key >> 12)] = b.idx[start + l];
+      s_list[s_start[key & 0xFFFu] + (key >> 12)] = s_pid[l];
     }
   }
   __syncthreads();
@@ -356,17 +390,7 @@ __global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer(Batch 
     float4 *tile4 = reinterpret_cast<float4 *>(tile);
     for (int t = tid; t < TN; t += P::THREADS) tile4[t] = make_float4(0.f, 0.f, 0.f, 0.f);
   }
-  if (DO_G2P) {  // grid velocities of nodes [B0-1, B0+B+3) into the V tile
-    const float4 *gv = b.gv + node_off;
-#pragma unroll 4
-    for (int t = tid; t < P::VN; t += P::THREADS) {
-      const int x = B0x - 1 + t % VX, y = B0y - 1 + (t / VX) % VY, z = B0z - 1 + t / (VX * VY);
-      float4 V = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (x >= 0 && y >= 0 && z >= 0 && x < G0 && y < G1 && z < G2)
-        V = __ldg(gv + ((long long)z * G1 + y) * G0 + x);
-      vt[t] = V;
-    }
-  }
+  cp_async_wait<0>();  // this thread's part of the V tile
   __syncthreads();
 
   // ---- one cell per thread (or, without grouping, one particle per thread)
@@ -393,22 +417,37 @@ __global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer(Batch 
 #pragma unroll
       for (int e = 0; e < 27; ++e) acc01[e] = acc2w[e] = make_float2(0.f, 0.f);
     }
-    // the state of particle q+1 is loaded while particle q computes
+    // the record of particle q+1 is copied into this thread's staging slot
+    // while particle q computes
+    float4 *stage = reinterpret_cast<float4 *>(smem + P::OFF_STAGE) + tid;
+    auto fetch = [&](uint32_t pp, int slot) {
+      const float4 *src = gps + 3 * (long long)pp;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) cp_async16(stage + (slot * 3 + j) * P::THREADS, src + j);
+      cp_async_commit();
+    };
     uint32_t pn = grouped ? s_list[q0] : b.idx[start + q0];
-    float un[3], Hnx[9];
-    load_particle(gps, pn, un, Hnx);
+    fetch(pn, 0);
     uint32_t fln = DO_G2P ? gfl[pn] : 0u;
     for (uint32_t q = q0; q < q1; ++q) {
       const uint32_t p = pn;
       const uint32_t fl = fln;
-      float u[3] = {un[0], un[1], un[2]};
-      float H[9];
-#pragma unroll
-      for (int e = 0; e < 9; ++e) H[e] = Hnx[e];
+      const int slot = (int)((q - q0) & 1u);
       if (q + 1 < q1) {
         pn = grouped ? s_list[q + 1] : b.idx[start + q + 1];
-        load_particle(gps, pn, un, Hnx);
+        fetch(pn, slot ^ 1);
         if (DO_G2P) fln = gfl[pn];
+        cp_async_wait<1>();
+      } else {
+        cp_async_wait<0>();
+      }
+      float u[3], H[9];
+      {
+        const float4 a = stage[(slot * 3 + 0) * P::THREADS], bq = stage[(slot * 3 + 1) * P::THREADS],
+                     cq = stage[(slot * 3 + 2) * P::THREADS];
+        u[0] = a.x; u[1] = a.y; u[2] = a.z;
+        H[0] = a.w; H[1] = bq.x; H[2] = bq.y; H[3] = bq.z; H[4] = bq.w;
+        H[5] = cq.x; H[6] = cq.y; H[7] = cq.z; H[8] = cq.w;
       }
       int bs[3];
 #pragma unroll
