@@ -177,7 +177,8 @@ struct XferPlan {
   static constexpr size_t OFF_START = OFF_CNT + 4 * (size_t)NE;     // u32 [NE + 1]
   static constexpr size_t OFF_CELLS = OFF_START + 4 * (size_t)(NE + 1);  // u16 [NE] non-empty cells
   // per-thread staging of the next particle record: float4 [2 slots][3][THREADS]
-  static constexpr size_t OFF_STAGE = (OFF_CELLS + 2 * (size_t)NE + 15) / 16 * 16;
+  static constexpr size_t OFF_ORDER = OFF_CELLS + 2 * (size_t)NE;   // u16 [NE] cells, heaviest class first
+  static constexpr size_t OFF_STAGE = (OFF_ORDER + 2 * (size_t)NE + 15) / 16 * 16;
   static constexpr size_t BYTES = OFF_STAGE + 16 * 2 * 3 * (size_t)THREADS;
   static_assert(4 * TN >= MAXP, "the P2G tile doubles as the key scratch");
 };
@@ -229,6 +230,60 @@ __device__ __forceinline__ uint32_t block_scan_compact(const uint32_t *a, uint32
   if (tid == 0) out[n] = tot & 0xFFFFFu;
   __syncthreads();
   return tot >> 20;
+}
+
+// Stable partition of the n non-empty cells (cells[0..n), index order) into
+// four classes by particle count, heaviest first: >= 11, 9-10, 7-8, <= 6.
+// The thread-per-cell loop then runs cells of similar count side by side in
+// a warp, so that lanes and warps finish together when the particles of a
+// strained block have spread unevenly over its cells (at rest every cell
+// holds 8).  Within a class the index order (and the locality of
+// neighbouring cells in a warp) is kept.  All threads of the CTA call it.
+template <int THREADS, int PER>
+__device__ __forceinline__ void order_cells_by_load(const uint16_t *cells, const uint32_t *start, int n,
+                                                    uint16_t *order, unsigned long long *warp_buf) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NWARP = THREADS / 32;
+  auto cls = [](uint32_t k) { return k >= 11 ? 0 : (k >= 9 ? 1 : (k >= 7 ? 2 : 3)); };
+  int myc[PER];
+  unsigned long long cnt = 0;  // four 16-bit class counts of this thread's chunk
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int i = tid * PER + q;
+    myc[q] = -1;
+    if (i < n) {
+      const uint32_t c = cells[i];
+      myc[q] = cls(start[c + 1] - start[c]);
+      cnt += 1ull << (16 * myc[q]);
+    }
+  }
+  unsigned long long x = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_buf[warp] = x;
+  __syncthreads();
+  unsigned long long pre = x - cnt, tot = 0;
+  for (int w = 0; w < NWARP; ++w) {
+    if (w < warp) pre += warp_buf[w];
+    tot += warp_buf[w];
+  }
+  // class base = sum of the totals of the heavier classes
+  uint32_t base[4];
+  base[0] = 0;
+#pragma unroll
+  for (int k = 1; k < 4; ++k) base[k] = base[k - 1] + (uint32_t)((tot >> (16 * (k - 1))) & 0xFFFFu);
+  uint32_t run[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) run[k] = base[k] + (uint32_t)((pre >> (16 * k)) & 0xFFFFu);
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int i = tid * PER + q;
+    if (i < n) order[run[myc[q]]++] = cells[i];
+  }
+  __syncthreads();
 }
 
 // P2G of one particle straight into the shared tile (particles that change
@@ -294,7 +349,9 @@ __global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer(Batch 
   uint32_t *s_cnt = reinterpret_cast<uint32_t *>(smem + P::OFF_CNT);
   uint32_t *s_start = reinterpret_cast<uint32_t *>(smem + P::OFF_START);
   uint16_t *s_cells = reinterpret_cast<uint16_t *>(smem + P::OFF_CELLS);
+  uint16_t *s_order = reinterpret_cast<uint16_t *>(smem + P::OFF_ORDER);
   __shared__ uint32_t s_warp[P::THREADS / 32];
+  __shared__ unsigned long long s_warp64[P::THREADS / 32];
   __shared__ int s_moved, s_overflow;
 
   const long long gblk = blockIdx.x;
@@ -384,6 +441,7 @@ __global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer(Batch 
       const uint32_t key = s_key[l];
       s_list[s_start[key & 0xFFFu] + (key >> 12)] = s_pid[l];
     }
+    order_cells_by_load<P::THREADS, P::PER>(s_cells, s_start, (int)ncells, s_order, s_warp64);
   }
   __syncthreads();
   if (DO_P2G) {
@@ -395,11 +453,16 @@ __global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer(Batch 
 
   // ---- one cell per thread (or, without grouping, one particle per thread)
   const uint32_t nwork = grouped ? ncells : n;
-  for (uint32_t wk = tid; wk < nwork; wk += P::THREADS) {
+  // round r gives thread t the cell at position r * THREADS + t, mirrored on
+  // odd rounds, so the warp that took the heaviest cells of one round takes
+  // the lightest of the next
+  for (uint32_t r0 = 0; r0 < nwork; r0 += P::THREADS) {
+    const uint32_t wk = r0 + (((r0 / P::THREADS) & 1u) ? (uint32_t)(P::THREADS - 1 - tid) : (uint32_t)tid);
+    if (wk >= nwork) continue;
     uint32_t q0, q1;
     int cx, cy, cz;
     if (grouped) {
-      const uint32_t c = s_cells[wk];
+      const uint32_t c = s_order[wk];
       q0 = s_start[c];
       q1 = s_start[c + 1];
       cx = (int)(c % P::EX);

@@ -111,6 +111,9 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
   }
   return false;
 }
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(bar)) : "memory");
+}
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
@@ -149,44 +152,77 @@ __device__ __forceinline__ void ld16(uint32_t taddr, float v[16]) {
 // convolution as an implicit GEMM: row m = pixel (n, y, x), K = 9 taps x Cin,
 // A[m][k] = X at pixel m shifted by tap(k) = 3 dy + dx in channel ci(k)
 // (zero outside the image), k = tap * Cin + ci; Wk is K-major [Cout][9 Cin].
-// One CTA of 128 threads computes 128 pixels x N output channels: each stage
-// copies a 32-channel slice of one tap (A: 128 x 64 B, B: N x 64 B) with
-// cp.async, one thread issues two 128 x N x 16 MMAs into TMEM and commits
-// them to the stage's mbarrier, which frees the stage for a later copy.  The
-// epilogue reads TMEM lane = pixel, adds the bias, applies ReLU and stores
-// BF16.  Requires Cin % 32 == 0, Cout % N == 0.  A wait that gives up sets
-// *err, abandons the tile and frees TMEM.
-template <int N, int STAGES>
+// One CTA of 128 threads computes 128 pixels x N output channels through a
+// ring of STAGES shared-memory stages, each a 32-channel slice of one tap
+// (A: 128 x 64 B, B: N x 64 B):
+//   every thread copies its share of stage `it` with cp.async once the MMAs
+//   that last read that buffer have completed (the buffer's "empty"
+//   mbarrier, armed by tcgen05.commit); LAG iterations later, when its copies
+//   have landed, it fences them for the tensor core and arrives on the
+//   stage's "full" mbarrier;
+//   thread 0 waits for "full", issues the stage's two 128 x N x 16 MMAs into
+//   tensor memory and commits them to "empty".
+// Copies run up to LAG stages ahead of the MMAs and no CTA-wide barrier sits
+// in the loop.  A thread whose wait gave up waits no more (and thread 0 stops
+// issuing), so a failure costs one bounded wait per thread, not one per stage.  The epilogue reads TMEM lane = pixel, adds the bias, applies
+// ReLU and stores BF16.  Requires Cin % 32 == 0, Cout % N == 0.  A wait that
+// gives up sets *err, abandons the tile and frees TMEM.
+template <int N, int STAGES, int TCOLS>
 __global__ void __launch_bounds__(128) k_conv3x3_tc(const bf16 *__restrict__ X, const bf16 *__restrict__ Wk,
                                                     const float *__restrict__ bias, bf16 *__restrict__ Y, int nimg,
-                                                    int H, int W, int Cin, int Cout, int relu, int *err) {
+                                                    int H, int W, int Cin, int Cout, int relu, int tiles, int *err) {
   constexpr int BM = 128, BK = 32, KCH = BK / 8;
   constexpr int A_BYTES = BM * BK * 2, B_BYTES = N * BK * 2, STAGE = A_BYTES + B_BYTES;
-  constexpr int TCOLS = N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
+  constexpr int LAG = STAGES - 2;
   static_assert(N % 16 == 0 && N >= 32 && N <= 256, "UMMA N for M = 128");
+  static_assert(STAGES >= 3, "the ring needs a stage being filled, one landing and one in the MMA");
+  static_assert(TCOLS >= N && (TCOLS & (TCOLS - 1)) == 0 && TCOLS <= 512, "tensor-memory allocation");
   extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ __align__(8) uint64_t bar[STAGES];
+  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES];
   __shared__ uint32_t tmem_base;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int M = nimg * H * W;
-  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * N;
+  const int n0 = blockIdx.y * N;
   const int nk = 9 * Cin / BK;
+  const int mtiles = (M + BM - 1) / BM;
+  const int t_first = blockIdx.x * tiles;
+  const int nt = min(tiles, mtiles - t_first);  // tiles of this CTA, accumulated side by side in TMEM
+  const int total = nt * nk;
   const long long ldw = 9LL * Cin;
 
-  // this thread copies the A row of pixel m0 + tid
-  const int m = m0 + tid;
-  const bool mvalid = m < M;
-  const int px = mvalid ? m % W : 0, py = mvalid ? (m / W) % H : 0, pimg = mvalid ? m / (W * H) : 0;
-  auto load = [&](int kk, int buf) {
+  // A copies: at step j of a stage, thread t moves 16-byte chunk t % 4 of
+  // tile row (pixel) 32 j + t / 4, so that a warp's 32 requests cover eight
+  // whole 64-byte rows (full 32-byte sectors from L2)
+  int cur_tile = -1;
+  int rpx[KCH], rpy[KCH], rimg[KCH];
+  bool rvalid[KCH];
+  auto load = [&](int s2, int buf) {
+    const int t = s2 / nk, kk = s2 - t * nk;
+    if (t != cur_tile) {
+      cur_tile = t;
+#pragma unroll
+      for (int j = 0; j < KCH; ++j) {
+        const int m = (t_first + t) * BM + 32 * j + (tid >> 2);
+        rvalid[j] = m < M;
+        rpx[j] = rvalid[j] ? m % W : 0;
+        rpy[j] = rvalid[j] ? (m / W) % H : 0;
+        rimg[j] = rvalid[j] ? m / (W * H) : 0;
+      }
+    }
     const int k0 = kk * BK;
     const int tap = k0 / Cin, ci0 = k0 % Cin;
-    const int ys = py + tap / 3 - 1, xs = px + tap % 3 - 1;
-    const bool v = mvalid && ys >= 0 && ys < H && xs >= 0 && xs < W;
-    const bf16 *src = v ? X + (((long long)pimg * H + ys) * W + xs) * Cin + ci0 : X;
+    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
     unsigned char *sa = smem + buf * STAGE;
     unsigned char *sb = sa + A_BYTES;
+    const int part = tid & 3;
 #pragma unroll
-    for (int j = 0; j < KCH; ++j) cp_async16(sa + ((tid >> 3) * KCH + j) * 128 + (tid & 7) * 16, src + 8 * j, v);
+    for (int j = 0; j < KCH; ++j) {
+      const int r = 32 * j + (tid >> 2);
+      const int ys = rpy[j] + dy, xs = rpx[j] + dx;
+      const bool v = rvalid[j] && ys >= 0 && ys < H && xs >= 0 && xs < W;
+      const bf16 *src = v ? X + (((long long)rimg[j] * H + ys) * W + xs) * Cin + ci0 + 8 * part : X;
+      cp_async16(sa + ((r >> 3) * KCH + part) * 128 + (r & 7) * 16, src, v);
+    }
     for (int c = tid; c < N * KCH; c += 128) {
       const int row = c / KCH, j = c % KCH;
       cp_async16(sb + ((row >> 3) * KCH + j) * 128 + (row & 7) * 16, Wk + (long long)(n0 + row) * ldw + k0 + 8 * j,
@@ -195,7 +231,10 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(const bf16 *__restrict__ X, 
   };
 
   if (tid == 0) {
-    for (int s2 = 0; s2 < STAGES; ++s2) tc::mbar_init(&bar[s2], 1);
+    for (int s2 = 0; s2 < STAGES; ++s2) {
+      tc::mbar_init(&full[s2], 128);
+      tc::mbar_init(&empty[s2], 1);
+    }
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 0) {
@@ -210,65 +249,68 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(const bf16 *__restrict__ X, 
   const uint32_t tmem = tmem_base;
   constexpr uint32_t IDESC = tc::instr_desc<BM, N>();
 
-  for (int s2 = 0; s2 < STAGES - 1; ++s2) {
-    if (s2 < nk) load(s2, s2);
-    cp_async_commit();
-  }
-  bool failed = false;
-  for (int kk = 0; kk < nk; ++kk) {
-    const int nxt = kk + STAGES - 1;
-    bool timed_out = false;
-    if (nxt < nk) {
-      // the stage's buffer was last read by the MMAs of stage kk - 1
-      if (kk >= 1) timed_out = !tc::mbar_wait(&bar[(kk - 1) % STAGES], (uint32_t)((kk - 1) / STAGES) & 1u);
-      load(nxt, nxt % STAGES);
+  bool ok = true;
+  for (int it = 0; it < total + LAG; ++it) {
+    if (it < total) {
+      const int buf = it % STAGES;
+      // the MMAs of stage it - STAGES read this buffer last
+      if (ok && it >= STAGES) ok = tc::mbar_wait(&empty[buf], (uint32_t)(it / STAGES - 1) & 1u);
+      load(it, buf);
     }
-    cp_async_commit();
-    cp_async_wait<STAGES - 1>();  // stage kk has landed
-    tc::fence_async_smem();
-    if (__syncthreads_or(timed_out)) {
-      failed = true;
-      break;
-    }
-    if (tid == 0) {
-      tc::fence_after();
-      const uint32_t a0 = smem_addr(smem + (kk % STAGES) * STAGE);
-      const uint32_t b0 = a0 + A_BYTES;
+    cp_async_commit();  // one group per iteration, possibly empty
+    const int j = it - LAG;
+    if (j >= 0) {
+      cp_async_wait<LAG>();  // this thread's copies of stage j have landed
+      tc::fence_async_smem();
+      tc::mbar_arrive(&full[j % STAGES]);
+      if (tid == 0) {
+        if (ok) ok = tc::mbar_wait(&full[j % STAGES], (uint32_t)(j / STAGES) & 1u);
+        if (ok) {
+          tc::fence_after();
+          const int t = j / nk, kk = j - t * nk;
+          const uint32_t a0 = smem_addr(smem + (j % STAGES) * STAGE);
+          const uint32_t b0 = a0 + A_BYTES;
 #pragma unroll
-      for (int ks = 0; ks < BK / 16; ++ks)  // K = 16 per MMA: two core matrices along K
-        tc::mma(tmem, tc::smem_desc(a0 + ks * 256, 128, KCH * 128), tc::smem_desc(b0 + ks * 256, 128, KCH * 128),
-                IDESC, (kk > 0 || ks > 0) ? 1u : 0u);
-      tc::commit(&bar[kk % STAGES]);
+          for (int ks = 0; ks < BK / 16; ++ks)  // K = 16 per MMA: two core matrices along K
+            tc::mma(tmem + (uint32_t)(t * N), tc::smem_desc(a0 + ks * 256, 128, KCH * 128),
+                    tc::smem_desc(b0 + ks * 256, 128, KCH * 128), IDESC, (kk > 0 || ks > 0) ? 1u : 0u);
+          tc::commit(&empty[j % STAGES]);
+        }
+      }
     }
   }
-  if (!failed) failed = __syncthreads_or(!tc::mbar_wait(&bar[(nk - 1) % STAGES], (uint32_t)((nk - 1) / STAGES) & 1u));
+  if (tid == 0 && ok) ok = tc::mbar_wait(&empty[(total - 1) % STAGES], (uint32_t)((total - 1) / STAGES) & 1u);
+  const bool failed = __syncthreads_or(!ok);
   if (failed) {
     if (tid == 0) atomicExch(err, 1);
     cp_async_wait<0>();
   } else {
     tc::fence_after();
-    // warp w owns TMEM lanes 32 w .. 32 w + 31 = rows (pixels) of the tile
-    const int row = m0 + warp * 32 + lane;
+    // warp w owns TMEM lanes 32 w .. 32 w + 31 = rows (pixels) of each tile
 #pragma unroll 1
-    for (int c0 = 0; c0 < N; c0 += 16) {
-      float v[16];
-      tc::ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
-      if (row < M) {
-        uint32_t packed[8];
+    for (int t = 0; t < nt; ++t) {
+      const int row = (t_first + t) * BM + warp * 32 + lane;
+#pragma unroll 1
+      for (int c0 = 0; c0 < N; c0 += 16) {
+        float v[16];
+        tc::ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * N + c0), v);
+        if (row < M) {
+          uint32_t packed[8];
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          float x0 = v[2 * j] + (bias ? bias[n0 + c0 + 2 * j] : 0.f);
-          float x1 = v[2 * j + 1] + (bias ? bias[n0 + c0 + 2 * j + 1] : 0.f);
-          if (relu) {
-            x0 = fmaxf(x0, 0.f);
-            x1 = fmaxf(x1, 0.f);
+          for (int q = 0; q < 8; ++q) {
+            float x0 = v[2 * q] + (bias ? bias[n0 + c0 + 2 * q] : 0.f);
+            float x1 = v[2 * q + 1] + (bias ? bias[n0 + c0 + 2 * q + 1] : 0.f);
+            if (relu) {
+              x0 = fmaxf(x0, 0.f);
+              x1 = fmaxf(x1, 0.f);
+            }
+            const __nv_bfloat162 h2 = __floats2bfloat162_rn(x0, x1);
+            packed[q] = *reinterpret_cast<const uint32_t *>(&h2);
           }
-          const __nv_bfloat162 h2 = __floats2bfloat162_rn(x0, x1);
-          packed[j] = *reinterpret_cast<const uint32_t *>(&h2);
+          uint4 *dst = reinterpret_cast<uint4 *>(Y + (long long)row * Cout + n0 + c0);
+          dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+          dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
         }
-        uint4 *dst = reinterpret_cast<uint4 *>(Y + (long long)row * Cout + n0 + c0);
-        dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-        dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
       }
     }
   }
@@ -380,74 +422,112 @@ __global__ void __launch_bounds__((BN / 16) * 32) k_conv3x3_wgrad(const bf16 *__
                                i += (long long)gridDim.x * blockDim.x)
 
 // x fp32 [P][cin] -> bf16 [P][cpad] (zero padded channels)
-__global__ void k_pack_input(const float *x, bf16 *y, long long P, int cin, int cpad) {
-  GRID_STRIDE(e, P * cpad) {
-    const long long p = e / cpad;
-    const int c = (int)(e % cpad);
-    y[e] = __float2bfloat16_rn(c < cin ? x[p * cin + c] : 0.f);
+// Eight BF16 channels (16 bytes) per thread in the kernels below; every
+// channel count is a multiple of 32.
+__device__ __forceinline__ void unpack8(const uint4 &u, float f[8]) {
+  const __nv_bfloat162 *h = reinterpret_cast<const __nv_bfloat162 *>(&u);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const float2 t = __bfloat1622float2(h[k]);
+    f[2 * k] = t.x;
+    f[2 * k + 1] = t.y;
   }
 }
-// g = g * (y > 0)
-__global__ void k_relu_mask(bf16 *g, const bf16 *y, long long n) {
-  GRID_STRIDE(e, n) {
-    if (!(__bfloat162float(y[e]) > 0.f)) g[e] = __float2bfloat16_rn(0.f);
+__device__ __forceinline__ uint4 pack8(const float f[8]) {
+  uint4 u;
+  __nv_bfloat162 *h = reinterpret_cast<__nv_bfloat162 *>(&u);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) h[k] = __floats2bfloat162_rn(f[2 * k], f[2 * k + 1]);
+  return u;
+}
+#define GRID_STRIDE_U(i, n) for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < (n); i += gridDim.x * blockDim.x)
+
+// x fp32 [P][cin] -> bf16 [P][cpad] (zero padded channels); chunks of 8
+__global__ void k_pack_input(const float *x, bf16 *y, unsigned P, int cin, int cpad) {
+  const unsigned cc = (unsigned)cpad / 8;
+  GRID_STRIDE_U(e, P * cc) {
+    const unsigned p = e / cc, c0 = (e % cc) * 8;
+    float f[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) f[k] = (int)c0 + k < cin ? x[(long long)p * cin + c0 + k] : 0.f;
+    reinterpret_cast<uint4 *>(y)[e] = pack8(f);
   }
 }
+// g = g * (y > 0), n8 = elements / 8
+__global__ void k_relu_mask(bf16 *g, const bf16 *y, unsigned n8) {
+  GRID_STRIDE_U(e, n8) {
+    float gv[8], yv[8];
+    unpack8(reinterpret_cast<const uint4 *>(g)[e], gv);
+    unpack8(reinterpret_cast<const uint4 *>(y)[e], yv);
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      if (!(yv[k] > 0.f)) gv[k] = 0.f;
+    reinterpret_cast<uint4 *>(g)[e] = pack8(gv);
+  }
+}
+// y[n][H/2][W/2][C] = mean of the 2 x 2 block
 __global__ void k_avgpool(const bf16 *x, bf16 *y, int nimg, int H, int W, int C) {
-  const int Ho = H / 2, Wo = W / 2;
-  GRID_STRIDE(e, (long long)nimg * Ho * Wo * C) {
-    const int c = (int)(e % C);
-    long long p = e / C;
-    const int xo = (int)(p % Wo), yo = (int)((p / Wo) % Ho);
-    const long long n = p / ((long long)Wo * Ho);
-    const long long b = ((n * H + 2 * yo) * W + 2 * xo) * C + c;
-    const float s = __bfloat162float(x[b]) + __bfloat162float(x[b + C]) + __bfloat162float(x[b + (long long)W * C]) +
-                    __bfloat162float(x[b + (long long)W * C + C]);
-    y[e] = __float2bfloat16_rn(0.25f * s);
+  const unsigned Ho = H / 2, Wo = W / 2, cc = C / 8;
+  GRID_STRIDE_U(e, (unsigned)nimg * Ho * Wo * cc) {
+    const unsigned c = e % cc, q = e / cc;
+    const unsigned xo = q % Wo, yo = (q / Wo) % Ho, n = q / (Wo * Ho);
+    const uint4 *src = reinterpret_cast<const uint4 *>(x + (((long long)n * H + 2 * yo) * W + 2 * xo) * C) + c;
+    const long long row = (long long)W * C / 8;
+    float a[8], b2[8], c2[8], d[8], o[8];
+    unpack8(src[0], a);
+    unpack8(src[C / 8], b2);
+    unpack8(src[row], c2);
+    unpack8(src[row + C / 8], d);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) o[k] = 0.25f * (a[k] + b2[k] + c2[k] + d[k]);
+    reinterpret_cast<uint4 *>(y)[e] = pack8(o);
   }
 }
 // gradient of avgpool, added into gx (which already holds the skip gradient)
 __global__ void k_avgpool_bwd_add(const bf16 *gy, bf16 *gx, int nimg, int H, int W, int C) {
-  const int Ho = H / 2, Wo = W / 2;
-  GRID_STRIDE(e, (long long)nimg * H * W * C) {
-    const int c = (int)(e % C);
-    long long p = e / C;
-    const int x = (int)(p % W), y = (int)((p / W) % H);
-    const long long n = p / ((long long)W * H);
-    const float g = 0.25f * __bfloat162float(gy[((n * Ho + y / 2) * Wo + x / 2) * C + c]);
-    gx[e] = __float2bfloat16_rn(__bfloat162float(gx[e]) + g);
+  const unsigned Ho = H / 2, Wo = W / 2, cc = C / 8;
+  GRID_STRIDE_U(e, (unsigned)nimg * H * W * cc) {
+    const unsigned c = e % cc, q = e / cc;
+    const unsigned x = q % W, y = (q / W) % H, n = q / (W * H);
+    float gv[8], xv[8];
+    unpack8(reinterpret_cast<const uint4 *>(gy + (((long long)n * Ho + y / 2) * Wo + x / 2) * C)[c], gv);
+    unpack8(reinterpret_cast<const uint4 *>(gx)[e], xv);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) xv[k] += 0.25f * gv[k];
+    reinterpret_cast<uint4 *>(gx)[e] = pack8(xv);
   }
 }
 // out [n][2H][2W][C1 + C2] = [upsample(a) (C1) | skip (C2)]
 __global__ void k_upsample_concat(const bf16 *a, const bf16 *skip, bf16 *out, int nimg, int H, int W, int C1, int C2) {
-  const int Ho = 2 * H, Wo = 2 * W, C = C1 + C2;
-  GRID_STRIDE(e, (long long)nimg * Ho * Wo * C) {
-    const int c = (int)(e % C);
-    long long p = e / C;
-    const int x = (int)(p % Wo), y = (int)((p / Wo) % Ho);
-    const long long n = p / ((long long)Wo * Ho);
-    out[e] = c < C1 ? a[((n * H + y / 2) * W + x / 2) * C1 + c] : skip[((n * Ho + y) * Wo + x) * C2 + (c - C1)];
+  const unsigned Ho = 2 * H, Wo = 2 * W, cc = (C1 + C2) / 8, c1 = C1 / 8;
+  GRID_STRIDE_U(e, (unsigned)nimg * Ho * Wo * cc) {
+    const unsigned c = e % cc, q = e / cc;
+    const unsigned x = q % Wo, y = (q / Wo) % Ho, n = q / (Wo * Ho);
+    const uint4 v = c < c1 ? reinterpret_cast<const uint4 *>(a + (((long long)n * H + y / 2) * W + x / 2) * C1)[c]
+                           : reinterpret_cast<const uint4 *>(skip + (long long)q * C2)[c - c1];
+    reinterpret_cast<uint4 *>(out)[e] = v;
   }
 }
 // split the gradient of the concatenation: ga = upsample^T of the first C1
 // channels (H x W output), gs = the remaining C2 channels
 __global__ void k_upsample_concat_bwd(const bf16 *g, bf16 *ga, bf16 *gs, int nimg, int H, int W, int C1, int C2) {
-  const int Ho = 2 * H, Wo = 2 * W, C = C1 + C2;
-  GRID_STRIDE(e, (long long)nimg * H * W * C1) {
-    const int c = (int)(e % C1);
-    long long p = e / C1;
-    const int x = (int)(p % W), y = (int)((p / W) % H);
-    const long long n = p / ((long long)W * H);
-    float s = 0.f;
+  const unsigned Ho = 2 * H, Wo = 2 * W, cc = (C1 + C2) / 8, c1 = C1 / 8, c2 = C2 / 8;
+  GRID_STRIDE_U(e, (unsigned)nimg * H * W * c1) {
+    const unsigned c = e % c1, q = e / c1;
+    const unsigned x = q % W, y = (q / W) % H, n = q / (W * H);
+    const uint4 *src = reinterpret_cast<const uint4 *>(g) + ((long long)(n * Ho + 2 * y) * Wo + 2 * x) * cc + c;
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f}, t[8];
 #pragma unroll
-    for (int q = 0; q < 4; ++q)
-      s += __bfloat162float(g[((n * Ho + 2 * y + (q >> 1)) * Wo + 2 * x + (q & 1)) * C + c]);
-    ga[e] = __float2bfloat16_rn(s);
+    for (int dq = 0; dq < 4; ++dq) {
+      unpack8(src[((long long)(dq >> 1) * Wo + (dq & 1)) * cc], t);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) s[k] += t[k];
+    }
+    reinterpret_cast<uint4 *>(ga)[e] = pack8(s);
   }
-  GRID_STRIDE(e2, (long long)nimg * Ho * Wo * C2) {
-    const int c = (int)(e2 % C2);
-    const long long p = e2 / C2;
-    gs[e2] = g[p * C + C1 + c];
+  GRID_STRIDE_U(e2, (unsigned)nimg * Ho * Wo * c2) {
+    const unsigned c = e2 % c2, q = e2 / c2;
+    reinterpret_cast<uint4 *>(gs)[e2] = reinterpret_cast<const uint4 *>(g)[(long long)q * cc + c1 + c];
   }
 }
 // db[c] += sum over pixels of g[p][c]
@@ -467,14 +547,24 @@ __global__ void k_bias_grad(const bf16 *g, float *db, long long P, int C) {
     atomicAdd(db + threadIdx.x, t);
   }
 }
-// head: y[p][o] = b[o] + sum_i W[i][o] x[p][i] (FP32 out)
-__global__ void k_head_fwd(const bf16 *x, const float *Wh, const float *bh, float *y, long long P, int Ci, int Co) {
-  GRID_STRIDE(e, P * Co) {
-    const long long p = e / Co;
-    const int o = (int)(e % Co);
-    float s = bh[o];
-    for (int i = 0; i < Ci; ++i) s += Wh[i * Co + o] * __bfloat162float(x[p * Ci + i]);
-    y[e] = s;
+// head: y[p][o] = b[o] + sum_i W[i][o] x[p][i] (FP32 out); one pixel per
+// thread, Ci a multiple of 8, Co <= 16
+__global__ void k_head_fwd(const bf16 *x, const float *Wh, const float *bh, float *y, unsigned P, int Ci, int Co) {
+  GRID_STRIDE_U(p, P) {
+    float acc[16];
+#pragma unroll
+    for (int o = 0; o < 16; ++o) acc[o] = o < Co ? bh[o] : 0.f;
+    const uint4 *xp = reinterpret_cast<const uint4 *>(x + (long long)p * Ci);
+    for (int c = 0; c < Ci / 8; ++c) {
+      float xv[8];
+      unpack8(xp[c], xv);
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+#pragma unroll
+        for (int o = 0; o < 16; ++o)
+          if (o < Co) acc[o] += Wh[(c * 8 + k) * Co + o] * xv[k];
+    }
+    for (int o = 0; o < Co; ++o) y[(long long)p * Co + o] = acc[o];
   }
 }
 // loss: sum of squared errors (atomic) and gy = 2 (y - t) / count
@@ -628,26 +718,38 @@ tacchi_status nn_sync(tacchi_nn *n) {
     if (e_ != cudaSuccess) return st_of(e_);   \
   } while (0)
 
-constexpr int kConvStages = 4;
-
+// Ring depth per tile width: about 60-100 KB of shared memory, so that two
+// or three CTAs share an SM and their tensor-memory columns fit its 512.
+// (Several 128-pixel tiles per CTA, accumulated side by side in tensor
+// memory, measured slower: the copies' latency, not the per-CTA set-up,
+// bounds the kernel, and fewer CTAs keep fewer stages in flight.)
+template <int N>
+constexpr int conv_stages() {
+  return N <= 128 ? 6 : 4;
+}
+template <int N>
+constexpr int conv_tcols() {
+  return N <= 32 ? 32 : (N <= 64 ? 64 : (N <= 128 ? 128 : 256));
+}
 template <int N>
 constexpr int conv_smem() {
-  return kConvStages * (128 * 32 * 2 + N * 32 * 2);
+  return conv_stages<N>() * (128 * 32 * 2 + N * 32 * 2);
 }
 
 template <int N>
 cudaError_t conv_launch(const bf16 *X, const bf16 *Wk, const float *bias, bf16 *Y, int nimg, int H, int W, int Cin,
                         int Cout, int relu, int *err, cudaStream_t s) {
+  constexpr int S = conv_stages<N>(), TC = conv_tcols<N>();
   static bool ready = false;  // the dynamic shared memory limit, once per instantiation
   if (!ready) {
-    const cudaError_t e = cudaFuncSetAttribute(k_conv3x3_tc<N, kConvStages>,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize, conv_smem<N>());
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_conv3x3_tc<N, S, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, conv_smem<N>());
     if (e != cudaSuccess) return e;
     ready = true;
   }
   const long long M = (long long)nimg * H * W;
   dim3 grid((unsigned)((M + 127) / 128), (unsigned)(Cout / N));
-  k_conv3x3_tc<N, kConvStages><<<grid, 128, conv_smem<N>(), s>>>(X, Wk, bias, Y, nimg, H, W, Cin, Cout, relu, err);
+  k_conv3x3_tc<N, S, TC><<<grid, 128, conv_smem<N>(), s>>>(X, Wk, bias, Y, nimg, H, W, Cin, Cout, relu, 1, err);
   return cudaGetLastError();
 }
 
@@ -730,7 +832,7 @@ void release_nn(tacchi_nn *n) {
 tacchi_status forward(tacchi_nn *n, int batch, const float *x) {
   cudaStream_t s = n->stream;
   const long long P0 = (long long)batch * n->H * n->W;
-  k_pack_input<<<grid_for(P0 * n->cin), 256, 0, s>>>(x, n->act[0], P0, n->cin_real, n->cin);
+  k_pack_input<<<grid_for(P0 * n->cin / 8), 256, 0, s>>>(x, n->act[0], (unsigned)P0, n->cin_real, n->cin);
   NCK(cudaGetLastError());
   int k = 0;
   int H = n->H, W = n->W;
@@ -742,7 +844,7 @@ tacchi_status forward(tacchi_nn *n, int batch, const float *x) {
       in = n->act[k + 1];
     }
     if (l < n->L - 1) {
-      k_avgpool<<<grid_for((long long)batch * H * W * n->widths[l] / 4), 256, 0, s>>>(in, n->pooled[l], batch, H, W,
+      k_avgpool<<<grid_for((long long)batch * H * W * n->widths[l] / 32), 256, 0, s>>>(in, n->pooled[l], batch, H, W,
                                                                                        n->widths[l]);
       NCK(cudaGetLastError());
       in = n->pooled[l];
@@ -753,7 +855,7 @@ tacchi_status forward(tacchi_nn *n, int batch, const float *x) {
   for (int l = n->L - 2; l >= 0; --l) {
     const int C1 = n->widths[l + 1], C2 = n->widths[l];
     const bf16 *skip = n->act[2 * l + 2];  // output of enc{l}b
-    k_upsample_concat<<<grid_for((long long)batch * 4 * H * W * (C1 + C2)), 256, 0, s>>>(in, skip, n->cat[l], batch, H,
+    k_upsample_concat<<<grid_for((long long)batch * 4 * H * W * (C1 + C2) / 8), 256, 0, s>>>(in, skip, n->cat[l], batch, H,
                                                                                          W, C1, C2);
     NCK(cudaGetLastError());
     H *= 2;
@@ -765,7 +867,7 @@ tacchi_status forward(tacchi_nn *n, int batch, const float *x) {
       in = n->act[k + 1];
     }
   }
-  k_head_fwd<<<grid_for(P0 * n->cout), 256, 0, s>>>(in, n->p + n->head_w, n->p + n->head_b, n->out, P0,
+  k_head_fwd<<<grid_for(P0), 256, 0, s>>>(in, n->p + n->head_w, n->p + n->head_b, n->out, (unsigned)P0,
                                                      n->widths[0], n->cout);
   NCK(cudaGetLastError());
   return TACCHI_OK;
@@ -781,7 +883,9 @@ tacchi_status backward(tacchi_nn *n, int batch, const float *target) {
   NCK(cudaGetLastError());
   const int nk = (int)n->convs.size();
   const int C0 = n->widths[0];
-  k_head_bwd<<<grid_for(P0 * C0), 256, (C0 * n->cout + n->cout) * sizeof(float), s>>>(
+  // a bounded grid: each thread loops over many pixels with its sums in
+  // registers before the per-block reduction
+  k_head_bwd<<<std::min<unsigned>(grid_for(P0 * C0), 1216u), 256, (C0 * n->cout + n->cout) * sizeof(float), s>>>(
       n->act[nk], n->gout, n->p + n->head_w, n->gact[nk], n->g + n->head_w, n->g + n->head_b, P0, C0, n->cout);
   NCK(cudaGetLastError());
 
@@ -794,7 +898,7 @@ tacchi_status backward(tacchi_nn *n, int batch, const float *target) {
     for (int q = 0; q < 2; ++q, --k) {
       ConvLayer &cl = n->convs[k];
       const long long P = (long long)batch * H * W;
-      k_relu_mask<<<grid_for(P * cl.cout), 256, 0, s>>>(gcur, n->act[k + 1], P * cl.cout);
+      k_relu_mask<<<grid_for(P * cl.cout / 8), 256, 0, s>>>(gcur, n->act[k + 1], (unsigned)(P * cl.cout / 8));
       NCK(cudaGetLastError());
       const bf16 *xin = q == 0 ? n->act[k] : n->cat[l];
       bf16 *gin = q == 0 ? n->gact[k] : n->gcat[l];
@@ -806,7 +910,7 @@ tacchi_status backward(tacchi_nn *n, int batch, const float *target) {
     // split the concatenation gradient: upsampled part and skip part
     const int C1 = n->widths[l + 1], C2 = n->widths[l];
     bf16 *gskip = n->gact[2 * l + 2];  // gradient of enc{l}b output (skip part first)
-    k_upsample_concat_bwd<<<grid_for((long long)batch * H * W * C2), 256, 0, s>>>(gcur, n->gup[l], gskip, batch, H / 2,
+    k_upsample_concat_bwd<<<grid_for((long long)batch * H * W * C2 / 8), 256, 0, s>>>(gcur, n->gup[l], gskip, batch, H / 2,
                                                                                   W / 2, C1, C2);
     NCK(cudaGetLastError());
     gcur = n->gup[l];  // gradient of the level l+1 output (decoder or bottom)
@@ -819,7 +923,7 @@ tacchi_status backward(tacchi_nn *n, int batch, const float *target) {
     if (l < n->L - 1) {
       // gradient of enc{l}b output = skip gradient (already in gact) + pool^T
       bf16 *genc = n->gact[2 * l + 2];
-      k_avgpool_bwd_add<<<grid_for((long long)batch * H * W * n->widths[l]), 256, 0, s>>>(gcur, genc, batch, H, W,
+      k_avgpool_bwd_add<<<grid_for((long long)batch * H * W * n->widths[l] / 8), 256, 0, s>>>(gcur, genc, batch, H, W,
                                                                                          n->widths[l]);
       NCK(cudaGetLastError());
       gcur = genc;
@@ -833,7 +937,7 @@ tacchi_status backward(tacchi_nn *n, int batch, const float *target) {
     for (int q = 0; q < 2; ++q, --k) {
       ConvLayer &cl = n->convs[k];
       const long long P = (long long)batch * H * W;
-      k_relu_mask<<<grid_for(P * cl.cout), 256, 0, s>>>(gcur, n->act[k + 1], P * cl.cout);
+      k_relu_mask<<<grid_for(P * cl.cout / 8), 256, 0, s>>>(gcur, n->act[k + 1], (unsigned)(P * cl.cout / 8));
       NCK(cudaGetLastError());
       const bf16 *xin = (q == 1 && l > 0) ? n->pooled[l - 1] : n->act[k];
       float *dW = (k == 0) ? n->convs[0].dwpad : n->g + cl.w_off;
@@ -872,7 +976,13 @@ tacchi_status tacchi_nn_create(int levels, const int *widths, int in_channels, i
   if (256 % widths[0]) return TACCHI_ERR_INVALID_ARG;  // the head kernel keeps one channel per thread
   for (int l = 0; l < levels; ++l)
     if (widths[l] < 32 || widths[l] % 32 || widths[l] > 1024) return TACCHI_ERR_INVALID_ARG;
-  if ((double)max_batch * height * width * widths[0] > 4.0e9) return TACCHI_ERR_INVALID_ARG;
+  // elementwise kernels index 8-channel chunks of a level's tensors with
+  // 32-bit integers: every level (with its concatenation) stays below 2^32
+  for (int l = 0; l < levels; ++l) {
+    const double P = (double)max_batch * (height >> l) * (width >> l);
+    const int c = widths[l] + (l + 1 < levels ? widths[l + 1] : 0);
+    if (P * c > 4.0e9) return TACCHI_ERR_INVALID_ARG;
+  }
   tacchi_nn *n = new (std::nothrow) tacchi_nn();
   if (!n) return TACCHI_ERR_OOM;
   n->stream = (cudaStream_t)stream;
