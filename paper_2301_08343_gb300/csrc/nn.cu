@@ -14,15 +14,18 @@
 // Kernels:
 //   k_conv3x3_tc   implicit-GEMM 3x3 convolution on the 5th-generation tensor
 //                  cores: rows = pixels, columns = output channels, K = 9 x
-//                  C_in; tcgen05.mma BF16 x BF16 -> FP32 in tensor memory,
-//                  operands staged by cp.async in a 4-stage ring released by
-//                  MMA-completion mbarriers, bias+ReLU+BF16 epilogue from
-//                  tcgen05.ld.  The data gradient runs the same kernel on the
-//                  output gradient with the weights flipped and transposed.
+//                  C_in; TMA tile loads (the image border as zero fill) into
+//                  a ring of 64-byte-swizzled stages, one producer thread and
+//                  one tcgen05.mma issuer synchronised by full/empty
+//                  mbarriers, the FP32 accumulator in tensor memory, and a
+//                  bias+ReLU+BF16 epilogue from tcgen05.ld.  The data gradient
+//                  runs the same kernel on the output gradient with the
+//                  weights flipped and transposed.
 //   k_conv3x3_wgrad  weight gradient: rows = (tap, C_in), columns = C_out,
 //                  K = pixels, split over pixel chunks with FP32 atomics.
 //   elementwise kernels for ReLU masks, pooling, upsampling, concatenation,
 //   bias gradients, the 1x1 head, the loss and Adam.
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
@@ -79,12 +82,39 @@ __device__ __forceinline__ void mma_bf16(float d[4], const uint32_t a[4], uint32
 // K_CH * 128 B.
 namespace tc {
 
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+// K-major operand whose rows are 64 bytes (32 BF16 along K) with the 64-byte
+// swizzle the TMA applies (16-byte chunk j of row r stored at chunk
+// j ^ ((r >> 1) & 3)): 8-row groups 512 bytes apart (stride-dimension
+// offset); the leading-dimension offset is unused while an MMA's K (32
+// bytes) stays inside the 64-byte row.  A K step inside the row advances the
+// start address; the tile must sit on a 512-byte boundary.
+__device__ __forceinline__ uint64_t smem_desc_sw64(uint32_t addr) {
   uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;  // descriptor version; base offset 0, no swizzle
+  d |= (uint64_t)1 << 16;               // leading-dimension offset (unused): 16 bytes
+  d |= (uint64_t)(512 >> 4) << 32;      // stride-dimension offset: 512 bytes
+  d |= (uint64_t)1 << 46;               // descriptor version; base offset 0
+  d |= (uint64_t)4 << 61;               // 64-byte swizzle
   return d;
+}
+
+// 2D / 4D tiled TMA loads completing on an mbarrier (transaction bytes).
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, int c0, int c1, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];\n" ::"r"(
+          smem_addr(dst)),
+      "l"(map), "r"(c0), "r"(c1), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
+                                            uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
+      "[%6];\n" ::"r"(smem_addr(dst)),
+      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_addr(bar))
+      : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
 }
 
 // Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), A and
@@ -111,12 +141,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
   }
   return false;
 }
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(bar)) : "memory");
-}
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory"); }
-__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }
 
 // D (TMEM) (+)= A (smem) * B (smem)^T, issued by one thread.
 __device__ __forceinline__ void mma(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t accumulate) {
@@ -152,89 +178,48 @@ __device__ __forceinline__ void ld16(uint32_t taddr, float v[16]) {
 // convolution as an implicit GEMM: row m = pixel (n, y, x), K = 9 taps x Cin,
 // A[m][k] = X at pixel m shifted by tap(k) = 3 dy + dx in channel ci(k)
 // (zero outside the image), k = tap * Cin + ci; Wk is K-major [Cout][9 Cin].
-// One CTA of 128 threads computes 128 pixels x N output channels through a
-// ring of STAGES shared-memory stages, each a 32-channel slice of one tap
-// (A: 128 x 64 B, B: N x 64 B):
-//   every thread copies its share of stage `it` with cp.async once the MMAs
-//   that last read that buffer have completed (the buffer's "empty"
-//   mbarrier, armed by tcgen05.commit); LAG iterations later, when its copies
-//   have landed, it fences them for the tensor core and arrives on the
-//   stage's "full" mbarrier;
-//   thread 0 waits for "full", issues the stage's two 128 x N x 16 MMAs into
-//   tensor memory and commits them to "empty".
-// Copies run up to LAG stages ahead of the MMAs and no CTA-wide barrier sits
-// in the loop.  A thread whose wait gave up waits no more (and thread 0 stops
-// issuing), so a failure costs one bounded wait per thread, not one per stage.  The epilogue reads TMEM lane = pixel, adds the bias, applies
-// ReLU and stores BF16.  Requires Cin % 32 == 0, Cout % N == 0.  A wait that
-// gives up sets *err, abandons the tile and frees TMEM.
+// One CTA computes 128 pixels x N output channels.  The 128 pixels are a box
+// of wb x hb x nb (x, y, image) of the NHWC activation, so the A slice of a
+// stage -- 32 channels of one tap -- is one 4D TMA load of that box shifted
+// by (dx, dy), the image border coming back as the TMA's zero fill; the B
+// slice (N x 32 of the weights) is one 2D TMA load.  Both land 64-byte
+// swizzled in a ring of STAGES shared-memory stages:
+//   thread 0 (producer) waits for a stage's "empty" mbarrier, arms its
+//   "full" mbarrier with the bytes to expect and issues the two loads;
+//   thread 32 (MMA issuer) waits for "full", issues the stage's two
+//   128 x N x 16 tcgen05.mma into tensor memory and commits them to "empty".
+// After the last stage the issuer commits to "done"; all four warps then read
+// TMEM lane = pixel, add the bias, apply ReLU and store BF16.  Requires Cin %
+// 32 == 0, Cout % N == 0.  A wait that gives up sets *err, abandons the tile
+// and frees TMEM.
 template <int N, int STAGES, int TCOLS>
-__global__ void __launch_bounds__(128) k_conv3x3_tc(const bf16 *__restrict__ X, const bf16 *__restrict__ Wk,
+__global__ void __launch_bounds__(128) k_conv3x3_tc(const __grid_constant__ CUtensorMap tmX,
+                                                    const __grid_constant__ CUtensorMap tmW,
                                                     const float *__restrict__ bias, bf16 *__restrict__ Y, int nimg,
-                                                    int H, int W, int Cin, int Cout, int relu, int tiles, int *err) {
-  constexpr int BM = 128, BK = 32, KCH = BK / 8;
+                                                    int H, int W, int Cin, int Cout, int relu, int *err) {
+  constexpr int BM = 128, BK = 32;
   constexpr int A_BYTES = BM * BK * 2, B_BYTES = N * BK * 2, STAGE = A_BYTES + B_BYTES;
-  constexpr int LAG = STAGES - 2;
   static_assert(N % 16 == 0 && N >= 32 && N <= 256, "UMMA N for M = 128");
-  static_assert(STAGES >= 3, "the ring needs a stage being filled, one landing and one in the MMA");
+  static_assert(STAGE % 1024 == 0, "stages keep the 512-byte alignment of the swizzled tiles");
   static_assert(TCOLS >= N && (TCOLS & (TCOLS - 1)) == 0 && TCOLS <= 512, "tensor-memory allocation");
-  extern __shared__ __align__(128) unsigned char smem[];
-  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES];
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], done;
   __shared__ uint32_t tmem_base;
+  // swizzled tiles need 512-byte alignment: round the dynamic base up
+  unsigned char *smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int M = nimg * H * W;
-  const int n0 = blockIdx.y * N;
+  const int m0 = blockIdx.x * BM, n0 = blockIdx.y * N;
   const int nk = 9 * Cin / BK;
-  const int mtiles = (M + BM - 1) / BM;
-  const int t_first = blockIdx.x * tiles;
-  const int nt = min(tiles, mtiles - t_first);  // tiles of this CTA, accumulated side by side in TMEM
-  const int total = nt * nk;
-  const long long ldw = 9LL * Cin;
-
-  // A copies: at step j of a stage, thread t moves 16-byte chunk t % 4 of
-  // tile row (pixel) 32 j + t / 4, so that a warp's 32 requests cover eight
-  // whole 64-byte rows (full 32-byte sectors from L2)
-  int cur_tile = -1;
-  int rpx[KCH], rpy[KCH], rimg[KCH];
-  bool rvalid[KCH];
-  auto load = [&](int s2, int buf) {
-    const int t = s2 / nk, kk = s2 - t * nk;
-    if (t != cur_tile) {
-      cur_tile = t;
-#pragma unroll
-      for (int j = 0; j < KCH; ++j) {
-        const int m = (t_first + t) * BM + 32 * j + (tid >> 2);
-        rvalid[j] = m < M;
-        rpx[j] = rvalid[j] ? m % W : 0;
-        rpy[j] = rvalid[j] ? (m / W) % H : 0;
-        rimg[j] = rvalid[j] ? m / (W * H) : 0;
-      }
-    }
-    const int k0 = kk * BK;
-    const int tap = k0 / Cin, ci0 = k0 % Cin;
-    const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-    unsigned char *sa = smem + buf * STAGE;
-    unsigned char *sb = sa + A_BYTES;
-    const int part = tid & 3;
-#pragma unroll
-    for (int j = 0; j < KCH; ++j) {
-      const int r = 32 * j + (tid >> 2);
-      const int ys = rpy[j] + dy, xs = rpx[j] + dx;
-      const bool v = rvalid[j] && ys >= 0 && ys < H && xs >= 0 && xs < W;
-      const bf16 *src = v ? X + (((long long)rimg[j] * H + ys) * W + xs) * Cin + ci0 + 8 * part : X;
-      cp_async16(sa + ((r >> 3) * KCH + part) * 128 + (r & 7) * 16, src, v);
-    }
-    for (int c = tid; c < N * KCH; c += 128) {
-      const int row = c / KCH, j = c % KCH;
-      cp_async16(sb + ((row >> 3) * KCH + j) * 128 + (row & 7) * 16, Wk + (long long)(n0 + row) * ldw + k0 + 8 * j,
-                 true);
-    }
-  };
+  // the tile's first pixel: a corner of the wb x hb x nb box
+  const int bx0 = m0 % W, by0 = (m0 / W) % H, bn0 = m0 / (W * H);
 
   if (tid == 0) {
     for (int s2 = 0; s2 < STAGES; ++s2) {
-      tc::mbar_init(&full[s2], 128);
+      tc::mbar_init(&full[s2], 1);
       tc::mbar_init(&empty[s2], 1);
     }
+    tc::mbar_init(&done, 1);
     asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
   if (warp == 0) {
@@ -247,70 +232,64 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(const bf16 *__restrict__ X, 
   __syncthreads();
   tc::fence_after();
   const uint32_t tmem = tmem_base;
-  constexpr uint32_t IDESC = tc::instr_desc<BM, N>();
-
   bool ok = true;
-  for (int it = 0; it < total + LAG; ++it) {
-    if (it < total) {
-      const int buf = it % STAGES;
-      // the MMAs of stage it - STAGES read this buffer last
-      if (ok && it >= STAGES) ok = tc::mbar_wait(&empty[buf], (uint32_t)(it / STAGES - 1) & 1u);
-      load(it, buf);
+
+  if (tid == 0) {  // producer
+    for (int kk = 0; kk < nk && ok; ++kk) {
+      const int buf = kk % STAGES;
+      if (kk >= STAGES) ok = tc::mbar_wait(&empty[buf], (uint32_t)(kk / STAGES - 1) & 1u);
+      if (!ok) break;
+      const int k0 = kk * BK, tap = k0 / Cin, ci0 = k0 - tap * Cin;
+      unsigned char *sa = smem + buf * STAGE;
+      tc::mbar_expect_tx(&full[buf], (uint32_t)STAGE);
+      tc::tma_load_4d(sa, &tmX, ci0, bx0 + tap % 3 - 1, by0 + tap / 3 - 1, bn0, &full[buf]);
+      tc::tma_load_2d(sa + A_BYTES, &tmW, k0, n0, &full[buf]);
     }
-    cp_async_commit();  // one group per iteration, possibly empty
-    const int j = it - LAG;
-    if (j >= 0) {
-      cp_async_wait<LAG>();  // this thread's copies of stage j have landed
-      tc::fence_async_smem();
-      tc::mbar_arrive(&full[j % STAGES]);
-      if (tid == 0) {
-        if (ok) ok = tc::mbar_wait(&full[j % STAGES], (uint32_t)(j / STAGES) & 1u);
-        if (ok) {
-          tc::fence_after();
-          const int t = j / nk, kk = j - t * nk;
-          const uint32_t a0 = smem_addr(smem + (j % STAGES) * STAGE);
-          const uint32_t b0 = a0 + A_BYTES;
+  } else if (tid == 32) {  // MMA issuer
+    constexpr uint32_t IDESC = tc::instr_desc<BM, N>();
+    for (int kk = 0; kk < nk && ok; ++kk) {
+      const int buf = kk % STAGES;
+      ok = tc::mbar_wait(&full[buf], (uint32_t)(kk / STAGES) & 1u);
+      if (!ok) break;
+      tc::fence_after();
+      const uint32_t a0 = smem_addr(smem + buf * STAGE), b0 = a0 + A_BYTES;
 #pragma unroll
-          for (int ks = 0; ks < BK / 16; ++ks)  // K = 16 per MMA: two core matrices along K
-            tc::mma(tmem + (uint32_t)(t * N), tc::smem_desc(a0 + ks * 256, 128, KCH * 128),
-                    tc::smem_desc(b0 + ks * 256, 128, KCH * 128), IDESC, (kk > 0 || ks > 0) ? 1u : 0u);
-          tc::commit(&empty[j % STAGES]);
-        }
-      }
+      for (int ks = 0; ks < BK / 16; ++ks)  // K = 16 per MMA: 32 bytes along the 64-byte row
+        tc::mma(tmem, tc::smem_desc_sw64(a0 + 32 * ks), tc::smem_desc_sw64(b0 + 32 * ks), IDESC,
+                (kk > 0 || ks > 0) ? 1u : 0u);
+      tc::commit(&empty[buf]);
     }
+    if (ok) tc::commit(&done);
   }
-  if (tid == 0 && ok) ok = tc::mbar_wait(&empty[(total - 1) % STAGES], (uint32_t)((total - 1) / STAGES) & 1u);
+  // everyone waits for the accumulator (bounded), then the epilogue
+  if (ok) ok = tc::mbar_wait(&done, 0);
   const bool failed = __syncthreads_or(!ok);
   if (failed) {
     if (tid == 0) atomicExch(err, 1);
-    cp_async_wait<0>();
   } else {
     tc::fence_after();
-    // warp w owns TMEM lanes 32 w .. 32 w + 31 = rows (pixels) of each tile
+    // warp w owns TMEM lanes 32 w .. 32 w + 31 = rows (pixels) of the tile
+    const int row = m0 + warp * 32 + lane;
 #pragma unroll 1
-    for (int t = 0; t < nt; ++t) {
-      const int row = (t_first + t) * BM + warp * 32 + lane;
-#pragma unroll 1
-      for (int c0 = 0; c0 < N; c0 += 16) {
-        float v[16];
-        tc::ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(t * N + c0), v);
-        if (row < M) {
-          uint32_t packed[8];
+    for (int c0 = 0; c0 < N; c0 += 16) {
+      float v[16];
+      tc::ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      if (row < M) {
+        uint32_t packed[8];
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            float x0 = v[2 * q] + (bias ? bias[n0 + c0 + 2 * q] : 0.f);
-            float x1 = v[2 * q + 1] + (bias ? bias[n0 + c0 + 2 * q + 1] : 0.f);
-            if (relu) {
-              x0 = fmaxf(x0, 0.f);
-              x1 = fmaxf(x1, 0.f);
-            }
-            const __nv_bfloat162 h2 = __floats2bfloat162_rn(x0, x1);
-            packed[q] = *reinterpret_cast<const uint32_t *>(&h2);
+        for (int q = 0; q < 8; ++q) {
+          float x0 = v[2 * q] + (bias ? bias[n0 + c0 + 2 * q] : 0.f);
+          float x1 = v[2 * q + 1] + (bias ? bias[n0 + c0 + 2 * q + 1] : 0.f);
+          if (relu) {
+            x0 = fmaxf(x0, 0.f);
+            x1 = fmaxf(x1, 0.f);
           }
-          uint4 *dst = reinterpret_cast<uint4 *>(Y + (long long)row * Cout + n0 + c0);
-          dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
-          dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
+          const __nv_bfloat162 h2 = __floats2bfloat162_rn(x0, x1);
+          packed[q] = *reinterpret_cast<const uint32_t *>(&h2);
         }
+        uint4 *dst = reinterpret_cast<uint4 *>(Y + (long long)row * Cout + n0 + c0);
+        dst[0] = make_uint4(packed[0], packed[1], packed[2], packed[3]);
+        dst[1] = make_uint4(packed[4], packed[5], packed[6], packed[7]);
       }
     }
   }
@@ -718,14 +697,11 @@ tacchi_status nn_sync(tacchi_nn *n) {
     if (e_ != cudaSuccess) return st_of(e_);   \
   } while (0)
 
-// Ring depth per tile width: about 60-100 KB of shared memory, so that two
-// or three CTAs share an SM and their tensor-memory columns fit its 512.
-// (Several 128-pixel tiles per CTA, accumulated side by side in tensor
-// memory, measured slower: the copies' latency, not the per-CTA set-up,
-// bounds the kernel, and fewer CTAs keep fewer stages in flight.)
+// Ring depth per tile width: about 80-100 KB of shared memory, so that two
+// CTAs share an SM and their tensor-memory columns fit its 512.
 template <int N>
 constexpr int conv_stages() {
-  return N <= 128 ? 6 : 4;
+  return N <= 64 ? 8 : (N <= 128 ? 6 : 4);
 }
 template <int N>
 constexpr int conv_tcols() {
@@ -733,7 +709,24 @@ constexpr int conv_tcols() {
 }
 template <int N>
 constexpr int conv_smem() {
-  return conv_stages<N>() * (128 * 32 * 2 + N * 32 * 2);
+  return conv_stages<N>() * (128 * 32 * 2 + N * 32 * 2) + 1024;  // + alignment slack
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (the
+// library links only the CUDA runtime).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+EncodeTiledFn encode_tiled() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  }
+  return fn;
 }
 
 template <int N>
@@ -747,9 +740,30 @@ cudaError_t conv_launch(const bf16 *X, const bf16 *Wk, const float *bias, bf16 *
     if (e != cudaSuccess) return e;
     ready = true;
   }
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return cudaErrorNotSupported;
+  // the 128-pixel box of a tile: whole image rows (W and H are powers of two)
+  const int wb = W < 128 ? W : 128;
+  const int hb = H < 128 / wb ? H : 128 / wb;
+  const int nb = 128 / (wb * hb);
+  if (wb * hb * nb != 128 || W % wb || H % hb) return cudaErrorInvalidValue;
+  CUtensorMap tmX, tmW;
+  const cuuint64_t gdX[4] = {(cuuint64_t)Cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)nimg};
+  const cuuint64_t gsX[3] = {(cuuint64_t)Cin * 2, (cuuint64_t)W * Cin * 2, (cuuint64_t)H * W * Cin * 2};
+  const cuuint32_t bxX[4] = {32, (cuuint32_t)wb, (cuuint32_t)hb, (cuuint32_t)nb}, es[4] = {1, 1, 1, 1};
+  const cuuint64_t gdW[2] = {(cuuint64_t)9 * Cin, (cuuint64_t)Cout};
+  const cuuint64_t gsW[1] = {(cuuint64_t)9 * Cin * 2};
+  const cuuint32_t bxW[2] = {32, (cuuint32_t)N};
+  if (enc(&tmX, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)X, gdX, gsX, bxX, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+          CUDA_SUCCESS ||
+      enc(&tmW, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)Wk, gdW, gsW, bxW, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+          CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
   const long long M = (long long)nimg * H * W;
   dim3 grid((unsigned)((M + 127) / 128), (unsigned)(Cout / N));
-  k_conv3x3_tc<N, S, TC><<<grid, 128, conv_smem<N>(), s>>>(X, Wk, bias, Y, nimg, H, W, Cin, Cout, relu, 1, err);
+  k_conv3x3_tc<N, S, TC><<<grid, 128, conv_smem<N>(), s>>>(tmX, tmW, bias, Y, nimg, H, W, Cin, Cout, relu, err);
   return cudaGetLastError();
 }
 
