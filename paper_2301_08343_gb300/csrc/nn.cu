@@ -21,8 +21,10 @@
 //                  bias+ReLU+BF16 epilogue from tcgen05.ld.  The data gradient
 //                  runs the same kernel on the output gradient with the
 //                  weights flipped and transposed.
-//   k_conv3x3_wgrad  weight gradient: rows = (tap, C_in), columns = C_out,
-//                  K = pixels, split over pixel chunks with FP32 atomics.
+//   k_conv3x3_wgrad_tc  weight gradient on the same tensor-core machinery:
+//                  rows = (tap, C_in), columns = C_out, K = pixels, both
+//                  operands MN-major from TMA boxes, split over pixel chunks
+//                  whose partial sums meet in dW through float4 reductions.
 //   elementwise kernels for ReLU masks, pooling, upsampling, concatenation,
 //   bias gradients, the 1x1 head, the loss and Adam.
 #include <cuda.h>
@@ -45,28 +47,6 @@ using bf16 = __nv_bfloat16;
 // PTX helpers
 __device__ __forceinline__ uint32_t smem_addr(const void *p) {
   return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool valid) {
-  const int sz = valid ? 16 : 0;  // 0: fill the 16 bytes with zeros
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_addr(smem)), "l"(gmem), "r"(sz));
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
-}
-__device__ __forceinline__ void ldsm_x4_t(uint32_t &r0, uint32_t &r1, uint32_t &r2, uint32_t &r3, const void *p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
-               : "r"(smem_addr(p)));
-}
-// D = A (16x16, row) * B (16x8, col) + D, BF16 inputs, FP32 accumulators
-__device__ __forceinline__ void mma_bf16(float d[4], const uint32_t a[4], uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
 // ---------------------------------------------------------------------------
@@ -299,100 +279,127 @@ __global__ void __launch_bounds__(128) k_conv3x3_tc(const __grid_constant__ CUte
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TCOLS) : "memory");
 }
 
-// dW[tap*Cin + ci][co] += sum over a chunk of pixels of X(shifted)[ci] * G[co].
-template <int BN>
-__global__ void __launch_bounds__((BN / 16) * 32) k_conv3x3_wgrad(const bf16 *__restrict__ X, const bf16 *__restrict__ G,
-                                                                float *__restrict__ dW, int nimg, int H, int W, int Cin,
-                                                                int Cout, int chunk) {
-  constexpr int BMk = 32, BKp = 32, THREADS = (BN / 16) * 32;
-  constexpr int XS = BMk + 8, GS = BN + 8;
-  __shared__ __align__(16) bf16 sX[2][BKp * XS];
-  __shared__ __align__(16) bf16 sG[2][BKp * GS];
-  const int M = nimg * H * W;
-  const int kblk = blockIdx.x;  // (tap, 32-channel block)
-  const int tap = (kblk * BMk) / Cin, ci0 = (kblk * BMk) % Cin;
-  const int dy = tap / 3 - 1, dx = tap % 3 - 1;
-  const int n0 = blockIdx.y * BN;
+// MN-major operand (rows = K, 64 bytes = 32 elements along M or N per row,
+// 64-byte swizzled as the TMA writes it): a 64-byte column group of K_ROWS
+// rows is one TMA box; column groups lie box_bytes apart (leading-dimension
+// offset) and 8-row groups along K 512 bytes apart (stride-dimension offset).
+__device__ __forceinline__ uint64_t smem_desc_sw64_mn(uint32_t addr, uint32_t box_bytes) {
+  uint64_t d = (uint64_t)((addr >> 4) & 0x3FFFu);
+  d |= (uint64_t)((box_bytes >> 4) & 0x3FFFu) << 16;
+  d |= (uint64_t)(512 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)4 << 61;
+  return d;
+}
+
+// Weight gradient on the tensor cores: dW[k][co] += sum over pixels p of
+// X(p shifted by tap(k))[ci(k)] * G[p][co], k = tap * Cin + ci.  A CTA owns
+// 128 rows k (four 32-row groups, each one tap and 32 channels) x NC output
+// channels and a chunk of pixels; per stage of 64 pixels (a box of whole
+// image rows) the producer issues four 4D TMA loads of X (one per row group,
+// shifted by its tap, zero outside the image) and NC / 32 2D loads of G,
+// 64-byte swizzled; both operands are MN-major (K = pixels runs along the
+// rows of the boxes).  The issuer runs four 128 x NC x 16 MMAs per stage
+// into tensor memory; the epilogue adds the partial sums to dW with float4
+// reductions (rows k >= 9 Cin, the padding of the last tile, are dropped).
+template <int NC, int STAGES, int TCOLS>
+__global__ void __launch_bounds__(128) k_conv3x3_wgrad_tc(const __grid_constant__ CUtensorMap tmX,
+                                                          const __grid_constant__ CUtensorMap tmG,
+                                                          float *__restrict__ dW, int P, int H, int W, int Cin,
+                                                          int Cout, int chunk, int *err) {
+  constexpr int BOX = 64 * 64;                   // 64 pixels x 64 bytes
+  constexpr int A_BYTES = 4 * BOX, B_BYTES = (NC / 32) * BOX, STAGE = A_BYTES + B_BYTES;
+  static_assert(NC % 32 == 0 && NC >= 32 && NC <= 256, "UMMA N for M = 128");
+  static_assert(TCOLS >= NC && (TCOLS & (TCOLS - 1)) == 0, "tensor-memory allocation");
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], done;
+  __shared__ uint32_t tmem_base;
+  unsigned char *smem = smem_raw + ((1024u - (smem_addr(smem_raw) & 1023u)) & 1023u);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int K9 = 9 * Cin;
+  const int k_base = blockIdx.x * 128, n0 = blockIdx.y * NC;
   const int p_begin = blockIdx.z * chunk;
-  const int p_end = min(M, p_begin + chunk);
-  if (p_begin >= p_end) return;
-  const int nsteps = (p_end - p_begin + BKp - 1) / BKp;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nst = (min(P, p_begin + chunk) - p_begin + 63) / 64;
 
-  auto load_stage = [&](int s, int buf) {
-    const int p0 = p_begin + s * BKp;
-    for (int c = tid; c < BKp * 4; c += THREADS) {
-      const int r = c >> 2, part = c & 3;
-      const int m = p0 + r;
-      bool valid = false;
-      const bf16 *src = X;
-      if (m < p_end) {
-        const int x = m % W, y = (m / W) % H, n = m / (W * H);
-        const int ys = y + dy, xs = x + dx;
-        if (ys >= 0 && ys < H && xs >= 0 && xs < W) {
-          valid = true;
-          src = X + (((long long)n * H + ys) * W + xs) * Cin + ci0 + part * 8;
-        }
-      }
-      cp_async16(&sX[buf][r * XS + part * 8], src, valid);
+  if (tid == 0) {
+    for (int s2 = 0; s2 < STAGES; ++s2) {
+      tc::mbar_init(&full[s2], 1);
+      tc::mbar_init(&empty[s2], 1);
     }
-    for (int c = tid; c < BKp * (BN / 8); c += THREADS) {
-      const int r = c / (BN / 8), part = c % (BN / 8);
-      const int m = p0 + r;
-      const bool valid = m < p_end;
-      cp_async16(&sG[buf][r * GS + part * 8], valid ? G + (long long)m * Cout + n0 + part * 8 : G, valid);
-    }
-    cp_async_commit();
-  };
-
-  float acc[2][2][4];  // [m16 tile (channels)][n8 tile][4]
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 2; ++j)
-#pragma unroll
-      for (int e = 0; e < 4; ++e) acc[i][j][e] = 0.f;
-
-  load_stage(0, 0);
-  for (int s = 0; s < nsteps; ++s) {
-    if (s + 1 < nsteps) {
-      load_stage(s + 1, (s + 1) & 1);
-      cp_async_wait<1>();
-    } else {
-      cp_async_wait<0>();
-    }
-    __syncthreads();
-    const bf16 *xs_ = sX[s & 1];
-    const bf16 *gs_ = sG[s & 1];
-#pragma unroll
-    for (int ks = 0; ks < BKp; ks += 16) {
-      uint32_t af[2][4], bfr[2][2];
-      // A' = X^T (channels x pixels): transposed 8x8 loads of sX [pixel][ch]
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-        ldsm_x4_t(af[i][0], af[i][1], af[i][2], af[i][3],
-                  xs_ + (ks + (lane & 7) + ((lane >> 4) & 1) * 8) * XS + i * 16 + ((lane >> 3) & 1) * 8);
-      ldsm_x4_t(bfr[0][0], bfr[0][1], bfr[1][0], bfr[1][1],
-                gs_ + (ks + (lane & 7) + ((lane >> 3) & 1) * 8) * GS + warp * 16 + (lane >> 4) * 8);
-#pragma unroll
-      for (int i = 0; i < 2; ++i)
-#pragma unroll
-        for (int j = 0; j < 2; ++j) mma_bf16(acc[i][j], af[i], bfr[j][0], bfr[j][1]);
-    }
-    __syncthreads();
+    tc::mbar_init(&done, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
   }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(smem_addr(&tmem_base)),
+                 "r"(TCOLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n" ::: "memory");
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = tmem_base;
+  bool ok = true;
+
+  if (tid == 0) {  // producer
+    for (int st = 0; st < nst && ok; ++st) {
+      const int buf = st % STAGES;
+      if (st >= STAGES) ok = tc::mbar_wait(&empty[buf], (uint32_t)(st / STAGES - 1) & 1u);
+      if (!ok) break;
+      const int p0 = p_begin + 64 * st;
+      const int px = p0 % W, py = (p0 / W) % H, pn = p0 / (W * H);
+      unsigned char *sa = smem + buf * STAGE;
+      tc::mbar_expect_tx(&full[buf], (uint32_t)STAGE);
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+      for (int j = 0; j < 4; ++j) {
+        const int kj = k_base + 32 * j;
+        // rows past 9 Cin: a box entirely outside the image, i.e. zeros
+        const int tap = kj < K9 ? kj / Cin : 0, ci0 = kj < K9 ? kj - tap * Cin : 0;
+        const int xo = kj < K9 ? tap % 3 - 1 : 2 * W;
+        tc::tma_load_4d(sa + j * BOX, &tmX, ci0, px + xo, py + tap / 3 - 1, pn, &full[buf]);
+      }
 #pragma unroll
-    for (int j = 0; j < 2; ++j) {
-      const int c = n0 + warp * 16 + j * 8 + (lane & 3) * 2;
+      for (int j = 0; j < NC / 32; ++j) tc::tma_load_2d(sa + A_BYTES + j * BOX, &tmG, n0 + 32 * j, p0, &full[buf]);
+    }
+  } else if (tid == 32) {  // MMA issuer
+    // instruction descriptor: FP32 D, BF16 A and B, both MN-major
+    constexpr uint32_t IDESC = tc::instr_desc<128, NC>() | (1u << 15) | (1u << 16);
+    for (int st = 0; st < nst && ok; ++st) {
+      const int buf = st % STAGES;
+      ok = tc::mbar_wait(&full[buf], (uint32_t)(st / STAGES) & 1u);
+      if (!ok) break;
+      tc::fence_after();
+      const uint32_t a0 = smem_addr(smem + buf * STAGE), b0 = a0 + A_BYTES;
 #pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int r = tap * Cin + ci0 + i * 16 + (lane >> 2) + h * 8;
-        atomicAdd(dW + (long long)r * Cout + c, acc[i][j][2 * h]);
-        atomicAdd(dW + (long long)r * Cout + c + 1, acc[i][j][2 * h + 1]);
+      for (int ks = 0; ks < 4; ++ks)  // K = 16 pixels per MMA: two 8-row groups (1024 bytes)
+        tc::mma(tmem, smem_desc_sw64_mn(a0 + 1024 * ks, BOX), smem_desc_sw64_mn(b0 + 1024 * ks, BOX), IDESC,
+                (st > 0 || ks > 0) ? 1u : 0u);
+      tc::commit(&empty[buf]);
+    }
+    if (ok) tc::commit(&done);
+  }
+  if (ok) ok = tc::mbar_wait(&done, 0);
+  const bool failed = __syncthreads_or(!ok);
+  if (failed) {
+    if (tid == 0) atomicExch(err, 1);
+  } else if (nst > 0) {
+    tc::fence_after();
+    const int k = k_base + warp * 32 + lane;  // TMEM lane = row k
+#pragma unroll 1
+    for (int c0 = 0; c0 < NC; c0 += 16) {
+      float v[16];
+      tc::ld16(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+      if (k < K9) {
+        float4 *dst = reinterpret_cast<float4 *>(dW + (long long)k * Cout + n0 + c0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) atomicAdd(dst + q, make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
       }
     }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem), "r"(TCOLS) : "memory");
 }
 
 // ---------------------------------------------------------------------------
@@ -779,23 +786,64 @@ cudaError_t conv_fwd(const bf16 *X, const bf16 *Wk, const float *bias, bf16 *Y, 
   return conv_launch<32>(X, Wk, bias, Y, nimg, H, W, Cin, Cout, relu, err, s);
 }
 
-cudaError_t conv_wgrad(const bf16 *X, const bf16 *G, float *dW, int nimg, int H, int W, int Cin, int Cout,
-                       cudaStream_t s) {
-  const int M = nimg * H * W;
-  const int kblocks = 9 * Cin / 32;
-  const int nb = Cout % 64 == 0 ? Cout / 64 : Cout / 32;
-  // enough pixel chunks to give the GPU about 2048 CTAs
-  long long want = 2048 / std::max(1, kblocks * nb);
+template <int NC>
+cudaError_t wgrad_launch(const CUtensorMap &tmX, const CUtensorMap &tmG, float *dW, int P, int H, int W, int Cin,
+                         int Cout, int *err, cudaStream_t s) {
+  constexpr int S = NC <= 64 ? 4 : (NC <= 128 ? 3 : 2);
+  constexpr int TC = NC <= 32 ? 32 : (NC <= 64 ? 64 : (NC <= 128 ? 128 : 256));
+  constexpr int SMEM = S * (4 + NC / 32) * 4096 + 1024;
+  static bool ready = false;
+  if (!ready) {
+    const cudaError_t e =
+        cudaFuncSetAttribute(k_conv3x3_wgrad_tc<NC, S, TC>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    if (e != cudaSuccess) return e;
+    ready = true;
+  }
+  const int mt = (9 * Cin + 127) / 128, ny = Cout / NC;
+  // pixel chunks (multiples of 64) so that the grid gives every SM about
+  // four CTAs; each CTA adds its partial sums to dW
+  const long long stages = ((long long)P + 63) / 64;
+  long long want = (152LL * 4 + (long long)mt * ny - 1) / ((long long)mt * ny);
   if (want < 1) want = 1;
-  int chunk = (int)((M + want - 1) / want);
-  chunk = ((chunk + 31) / 32) * 32;
-  if (chunk < 256) chunk = 256;
-  dim3 grid(kblocks, nb, (M + chunk - 1) / chunk);
-  if (Cout % 64 == 0)
-    k_conv3x3_wgrad<64><<<grid, 128, 0, s>>>(X, G, dW, nimg, H, W, Cin, Cout, chunk);
-  else
-    k_conv3x3_wgrad<32><<<grid, 64, 0, s>>>(X, G, dW, nimg, H, W, Cin, Cout, chunk);
+  long long per = (stages + want - 1) / want;
+  if (per < 4) per = 4;
+  const int chunk = (int)(per * 64);
+  dim3 grid((unsigned)mt, (unsigned)ny, (unsigned)((P + chunk - 1) / chunk));
+  k_conv3x3_wgrad_tc<NC, S, TC><<<grid, 128, SMEM, s>>>(tmX, tmG, dW, P, H, W, Cin, Cout, chunk, err);
   return cudaGetLastError();
+}
+
+// dW (FP32, [9 Cin][Cout], accumulated into) += the weight gradient of a 3x3
+// 'same' convolution with input X [nimg][H][W][Cin] and output gradient
+// G [nimg][H][W][Cout] (BF16).
+cudaError_t conv_wgrad(const bf16 *X, const bf16 *G, float *dW, int nimg, int H, int W, int Cin, int Cout, int *err,
+                       cudaStream_t s) {
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return cudaErrorNotSupported;
+  const int P = nimg * H * W;
+  // 64-pixel boxes of whole image rows (W and H are powers of two)
+  const int wb = W < 64 ? W : 64;
+  const int hb = H < 64 / wb ? H : 64 / wb;
+  const int nb = 64 / (wb * hb);
+  if (wb * hb * nb != 64 || W % wb || H % hb) return cudaErrorInvalidValue;
+  CUtensorMap tmX, tmG;
+  const cuuint64_t gdX[4] = {(cuuint64_t)Cin, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)nimg};
+  const cuuint64_t gsX[3] = {(cuuint64_t)Cin * 2, (cuuint64_t)W * Cin * 2, (cuuint64_t)H * W * Cin * 2};
+  const cuuint32_t bxX[4] = {32, (cuuint32_t)wb, (cuuint32_t)hb, (cuuint32_t)nb}, es[4] = {1, 1, 1, 1};
+  const cuuint64_t gdG[2] = {(cuuint64_t)Cout, (cuuint64_t)P};
+  const cuuint64_t gsG[1] = {(cuuint64_t)Cout * 2};
+  const cuuint32_t bxG[2] = {32, 64};
+  if (enc(&tmX, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, (void *)X, gdX, gsX, bxX, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+          CUDA_SUCCESS ||
+      enc(&tmG, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, (void *)G, gdG, gsG, bxG, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) !=
+          CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  if (Cout % 256 == 0) return wgrad_launch<256>(tmX, tmG, dW, P, H, W, Cin, Cout, err, s);
+  if (Cout % 128 == 0) return wgrad_launch<128>(tmX, tmG, dW, P, H, W, Cin, Cout, err, s);
+  if (Cout % 64 == 0) return wgrad_launch<64>(tmX, tmG, dW, P, H, W, Cin, Cout, err, s);
+  return wgrad_launch<32>(tmX, tmG, dW, P, H, W, Cin, Cout, err, s);
 }
 
 cudaError_t bias_grad(const bf16 *G, float *db, long long P, int C, cudaStream_t s) {
@@ -916,7 +964,7 @@ tacchi_status backward(tacchi_nn *n, int batch, const float *target) {
       NCK(cudaGetLastError());
       const bf16 *xin = q == 0 ? n->act[k] : n->cat[l];
       bf16 *gin = q == 0 ? n->gact[k] : n->gcat[l];
-      NCK(conv_wgrad(xin, gcur, n->g + cl.w_off, batch, H, W, cl.cin, cl.cout, s));
+      NCK(conv_wgrad(xin, gcur, n->g + cl.w_off, batch, H, W, cl.cin, cl.cout, n->err, s));
       NCK(bias_grad(gcur, n->g + cl.b_off, P, cl.cout, s));
       NCK(conv_fwd(gcur, cl.wd, nullptr, gin, batch, H, W, cl.cout, cl.cin, 0, n->err, s));
       gcur = gin;
@@ -956,7 +1004,7 @@ tacchi_status backward(tacchi_nn *n, int batch, const float *target) {
       const bf16 *xin = (q == 1 && l > 0) ? n->pooled[l - 1] : n->act[k];
       float *dW = (k == 0) ? n->convs[0].dwpad : n->g + cl.w_off;
       if (k == 0) NCK(cudaMemsetAsync(dW, 0, sizeof(float) * cl.wpad_elems, s));
-      NCK(conv_wgrad(xin, gcur, dW, batch, H, W, cl.cin, cl.cout, s));
+      NCK(conv_wgrad(xin, gcur, dW, batch, H, W, cl.cin, cl.cout, n->err, s));
       NCK(bias_grad(gcur, n->g + cl.b_off, P, cl.cout, s));
       if (k == 0) {
         k_unpad_wgrad<<<grid_for(9LL * cl.cin_real * cl.cout), 256, 0, s>>>(dW, n->g + cl.w_off, cl.cin_real, cl.cin,
