@@ -541,8 +541,8 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["c2", "surrogate", "serving"], default="c1")
     ap.add_argument("--stream-s", type=float, default=0.5, help="seconds of the served query stream")
-    ap.add_argument("--samples", type=int, default=4096, help="surrogate training presses")
-    ap.add_argument("--train-steps", type=int, default=1500)
+    ap.add_argument("--samples", type=int, default=20000, help="surrogate training presses")
+    ap.add_argument("--train-steps", type=int, default=12000)
     ap.add_argument("--substeps", type=int, default=0, help="override substeps per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
