@@ -317,6 +317,17 @@ tacchi_status tacchi_batch_set_state(tacchi_handle h, int i, const float *u, con
 tacchi_status tacchi_batch_displacement_map(tacchi_handle h, int i, int w, int hgt, const double window_m[4],
                                             float *out_dev);
 
+/* Marker motion (the outlook of Sec. V: markers on the elastomer surface are
+ * particles that share the markers' positions, so recording the surface
+ * particles' motion gives the markers').  Marker k of instance i at rest at
+ * xy_dev[k] = (x, y) (world frame, m, on the top face) follows the top-layer
+ * particle whose rest sub-cell (the particle lattice at spacing dx/2 over the
+ * top face, clamped to it) contains (x, y): out_dev[k] = its displacement
+ * from rest (m, x/y/z).  The same selection as tacchi_batch_displacement_map.
+ * xy_dev: dev float [n][2]; out_dev: dev float [n][3].  Asynchronous.
+ * Errors: INVALID_ARG (i out of range, n < 1 or > 2^24, null pointers). */
+tacchi_status tacchi_batch_markers(tacchi_handle h, int i, int n, const float *xy_dev, float *out_dev);
+
 /* Penetration of instance i's indenter into the rest top face at its current
  * pose: per pixel centre (x, y) of window_m, max(0, z_top - z_b(x, y)) with
  * z_b the lowest point of the indenter over (x, y) (m).  Only rotations

@@ -235,6 +235,15 @@ class Tacchi:
         check(lib().tacchi_set_state(self._h, ptr(tu), ptr(tv), ptr(tC), ptr(tF)), "tacchi_set_state")
         check(lib().tacchi_sync(self._h), "tacchi_set_state")
 
+    def markers(self, xy, out=None):
+        """Marker displacement (m) at rest positions xy [n, 2] (see
+        TacchiBatch.markers)."""
+        torch = self._torch
+        xy = torch.as_tensor(xy, dtype=torch.float32, device=self.device).reshape(-1, 2).contiguous()
+        out = out if out is not None else torch.empty((xy.shape[0], 3), device=self.device, dtype=torch.float32)
+        check(lib().tacchi_batch_markers(self._h, 0, xy.shape[0], ptr(xy), ptr(out)), "tacchi_batch_markers")
+        return out
+
     def get_grid(self):
         """[n_nodes, 4] = (M, MG) of the last particle-to-grid transfer."""
         torch = self._torch
@@ -377,6 +386,17 @@ class TacchiBatch:
         out = out if out is not None else torch.empty((h, w, 3), device=self.device, dtype=torch.float32)
         check(lib().tacchi_batch_displacement_map(self._h, i, w, h, (C.c_double * 4)(*window), ptr(out)),
               "tacchi_batch_displacement_map")
+        return out
+
+    def markers(self, i, xy, out=None):
+        """Displacement (m) of the markers at rest positions xy [n, 2] (m,
+        world, on the top face): each follows the top-layer particle whose
+        rest sub-cell contains it."""
+        torch = self._torch
+        xy = torch.as_tensor(xy, dtype=torch.float32, device=self.device).reshape(-1, 2).contiguous()
+        n = xy.shape[0]
+        out = out if out is not None else torch.empty((n, 3), device=self.device, dtype=torch.float32)
+        check(lib().tacchi_batch_markers(self._h, i, n, ptr(xy), ptr(out)), "tacchi_batch_markers")
         return out
 
     def penetration_map(self, i, w, h, window, out=None):

@@ -1009,6 +1009,26 @@ tacchi_status tacchi_batch_displacement_map(tacchi_handle c, int i, int w, int h
   return TACCHI_OK;
 }
 
+tacchi_status tacchi_batch_markers(tacchi_handle c, int i, int n, const float *xy_dev, float *out_dev) {
+  if (check_index(c, i) != TACCHI_OK || n < 1 || n > (1 << 24) || !xy_dev || !out_dev) return TACCHI_ERR_INVALID_ARG;
+  const InstHost &I = c->in[i];
+  DispMapArgs a{};
+  a.ps = c->b.ps;
+  a.Ntot = c->Ntot;
+  a.surf = c->d_surf + I.surf_off;
+  a.rest = c->d_srest + I.surf_off;
+  a.rest_stride = c->Ns_tot;
+  a.nx = I.n[0];
+  a.ny = I.n[1];
+  a.xy = xy_dev;
+  a.dx = (float)I.dx;
+  a.w = n;
+  a.h = 1;
+  a.out = out_dev;
+  CK(launch_dispmap(a, c->stream));
+  return TACCHI_OK;
+}
+
 tacchi_status tacchi_batch_penetration_map(tacchi_handle c, int i, int w, int h, const double window_m[4],
                                            float *out_dev) {
   if (check_index(c, i) != TACCHI_OK || !out_dev) return TACCHI_ERR_INVALID_ARG;

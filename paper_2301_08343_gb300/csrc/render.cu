@@ -142,7 +142,8 @@ __global__ void __launch_bounds__(256) k_dispmap(DispMapArgs a) {
   if (e >= (long long)a.w * a.h) return;
   const int r = (int)(e / a.w), c = (int)(e % a.w);
   // rest lattice of the top particle layer: spacing dx/2 from the block corner
-  const float X = a.X0 + (float)c * a.PW, Y = a.Y0 + (float)r * a.PH;
+  const float X = a.xy ? a.xy[2 * e] : a.X0 + (float)c * a.PW;
+  const float Y = a.xy ? a.xy[2 * e + 1] : a.Y0 + (float)r * a.PH;
   int i = (int)floorf(X / (0.5f * a.dx)), j = (int)floorf(Y / (0.5f * a.dx));
   i = min(max(i, 0), 2 * a.nx - 1);
   j = min(max(j, 0), 2 * a.ny - 1);

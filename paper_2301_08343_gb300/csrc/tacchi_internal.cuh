@@ -206,6 +206,7 @@ struct DispMapArgs {
   long long rest_stride;   // Ns_tot
   int nx, ny;              // elastomer cells (the block's corner is world (0, 0))
   float X0, Y0, PW, PH;    // pixel (r, c) centre = (X0 + c PW, Y0 + r PH), metres
+  const float *xy;         // or, when set, point e = (xy[2e], xy[2e + 1]) (markers), h = 1
   float dx;
   int w, h;
   float *out;              // [h][w][3] metres
