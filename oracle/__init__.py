@@ -88,6 +88,7 @@ def lib():
             L.ora_set_indenter.argtypes = [C.c_void_p, C.c_int, dp, C.c_int, C.c_int,
                                            C.c_double, fp, dp, dp]
             L.ora_get_pose.argtypes = [C.c_void_p, dp]
+            L.ora_set_indenter_particles.argtypes = [C.c_void_p, C.c_longlong, dp, C.c_double]
             L.ora_node_inside.argtypes = [C.c_void_p, C.c_int, C.c_int, C.c_int]
             L.ora_p2g.argtypes = [C.c_void_p, C.c_double, dp, dp]
             L.ora_substep.argtypes = [C.c_void_p, C.c_double]
@@ -245,6 +246,15 @@ class Sim:
                                       _p(pose, C.c_double), _p(vel, C.c_double))
         if rc != 0:
             raise ValueError("oracle rejected the indenter description")
+
+    def set_indenter_particles(self, pts, mass):
+        """Indenter represented by particles at local positions pts (m,
+        [n, 3]), each of the given mass (Eq. 10, p in I); an empty array
+        restores the grid-boundary indenter."""
+        a = np.ascontiguousarray(np.asarray(pts, np.float64).reshape(-1, 3))
+        rc = self._L.ora_set_indenter_particles(self._h, a.shape[0], _p(a, C.c_double), float(mass))
+        if rc != 0:
+            raise ValueError("oracle rejected the indenter particles")
 
     def pose(self):
         p = np.zeros(7)

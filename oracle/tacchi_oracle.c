@@ -68,6 +68,11 @@ struct ora_sim {
   double hm_pixel;
   float *hm;
   double pose[7], vel[6];
+  /* indenter represented by particles (Eq. 10, p in I): local positions (m)
+   * in the indenter frame and the mass of each; 0 points = grid boundary */
+  long long ind_np;
+  double *ind_pts;
+  double ind_mass;
 };
 
 static int g_threads = 1;
@@ -153,6 +158,7 @@ void ora_destroy(ora_sim *s) {
   if (!s) return;
   free(s->xi); free(s->v); free(s->C); free(s->F); free(s->flags);
   free(s->rest_z); free(s->gm); free(s->gp); free(s->gv); free(s->hm);
+  free(s->ind_pts);
   free(s);
 }
 
@@ -459,6 +465,24 @@ int ora_set_indenter(ora_sim *s, int kind, const double *params, int hm_w,
   return 0;
 }
 
+/* Represent the indenter by n particles at local positions pts (m, [n][3],
+ * in the frame the pose maps to the world), each of the given mass: Eq. 10
+ * gives them the indenter's velocity, and Sec. III-C initialises them from a
+ * point cloud of the object.  n = 0 restores the grid-boundary indenter. */
+int ora_set_indenter_particles(ora_sim *s, long long n, const double *pts, double mass) {
+  if (n < 0 || (n > 0 && (!pts || !(mass > 0.0)))) return -1;
+  free(s->ind_pts);
+  s->ind_pts = NULL;
+  s->ind_np = 0;
+  s->ind_mass = 0.0;
+  if (n == 0) return 0;
+  s->ind_pts = (double *)malloc(sizeof(double) * 3 * (size_t)n);
+  memcpy(s->ind_pts, pts, sizeof(double) * 3 * (size_t)n);
+  s->ind_np = n;
+  s->ind_mass = mass;
+  return 0;
+}
+
 void ora_get_pose(const ora_sim *s, double pose[7]) {
   for (int e = 0; e < 7; ++e) pose[e] = s->pose[e];
 }
@@ -537,6 +561,46 @@ static void p2g_into(ora_sim *s, double dt, double *mass, double *mom) {
           }
     }
   }
+  /* Indenter particles (Eq. 10, p in I), at the pose of the start of the
+   * substep: world position x = c + R l, the rigid velocity v = v_c +
+   * w x (x - c), whose gradient C = skew(w) is the affine velocity of Eq. 4;
+   * they carry no elastic stress (rigid), so Eq. 5 adds nothing for them. */
+  if (s->ind_np > 0) {
+    double Rm[9];
+    quat_to_mat(s->pose + 3, Rm);
+    const double *w = s->vel + 3;
+    const double Cw[9] = {0.0, -w[2], w[1], w[2], 0.0, -w[0], -w[1], w[0], 0.0};
+    double *pm = priv; /* serial: the first thread's private grid */
+    for (long long q = 0; q < s->ind_np; ++q) {
+      const double *l = s->ind_pts + 3 * q;
+      double x[3], r[3], v[3], xi[3];
+      for (int a = 0; a < 3; ++a) {
+        r[a] = Rm[a * 3 + 0] * l[0] + Rm[a * 3 + 1] * l[1] + Rm[a * 3 + 2] * l[2];
+        x[a] = s->pose[a] + r[a];
+        xi[a] = (x[a] - s->origin[a]) / dx;
+      }
+      v[0] = s->vel[0] + (w[1] * r[2] - w[2] * r[1]);
+      v[1] = s->vel[1] + (w[2] * r[0] - w[0] * r[2]);
+      v[2] = s->vel[2] + (w[0] * r[1] - w[1] * r[0]);
+      int base[3];
+      double wt[27];
+      ora_weights(xi, base, wt);
+      for (int k = 0; k < 3; ++k)
+        for (int j = 0; j < 3; ++j)
+          for (int i = 0; i < 3; ++i) {
+            int I = base[0] + i, J = base[1] + j, K = base[2] + k;
+            if (I < 0 || J < 0 || K < 0 || I >= s->G[0] || J >= s->G[1] || K >= s->G[2]) continue;
+            double wip = wt[(k * 3 + j) * 3 + i];
+            double dpos[3] = {((double)I - xi[0]) * dx, ((double)J - xi[1]) * dx, ((double)K - xi[2]) * dx};
+            long long n = node_index(s, I, J, K);
+            pm[4 * n + 0] += wip * s->ind_mass; /* Eq. 2 */
+            for (int a = 0; a < 3; ++a) {
+              double Cd = Cw[a * 3 + 0] * dpos[0] + Cw[a * 3 + 1] * dpos[1] + Cw[a * 3 + 2] * dpos[2];
+              pm[4 * n + 1 + a] += wip * s->ind_mass * (v[a] + Cd); /* Eqs. 3-4 */
+            }
+          }
+    }
+  }
   for (long long n = 0; n < nodes; ++n) {
     double acc[4] = {0, 0, 0, 0};
     for (int t = 0; t < nt; ++t)
@@ -566,7 +630,7 @@ static void grid_update(ora_sim *s, double dt) {
     double M = s->gm[n];
     if (M > 0.0)
       for (int a = 0; a < 3; ++a) V[a] = s->gp[a * nodes + n] / M + dt * s->p.gravity[a];
-    if (inside32(s, &f, i, j, k)) {
+    if (s->ind_np == 0 && inside32(s, &f, i, j, k)) {
       double X[3] = {s->origin[0] + i * dx, s->origin[1] + j * dx, s->origin[2] + k * dx};
       double r[3] = {X[0] - s->pose[0], X[1] - s->pose[1], X[2] - s->pose[2]};
       const double *w = s->vel + 3;

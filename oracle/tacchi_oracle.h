@@ -75,6 +75,12 @@ void ora_get_state_f32(const ora_sim *s, float *u, float *v, float *C, float *Fm
 int ora_set_indenter(ora_sim *s, int kind, const double *params, int hm_w,
                      int hm_h, double hm_pixel_m, const float *hm,
                      const double pose[7], const double vel[6]);
+/* Indenter represented by n particles (Eq. 10, p in I): local positions
+ * pts (m, [n][3]) in the indenter frame, each of the given mass; they add
+ * mass and momentum to the grid at the rigid velocity, and grid nodes are no
+ * longer overridden by the shape.  n = 0 restores the grid boundary.
+ * Returns 0, or -1 on bad arguments. */
+int ora_set_indenter_particles(ora_sim *s, long long n, const double *pts, double mass);
 void ora_get_pose(const ora_sim *s, double pose[7]);
 int ora_node_inside(const ora_sim *s, int i, int j, int k);
 

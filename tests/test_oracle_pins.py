@@ -519,3 +519,73 @@ def test_shading_slope_toward_light_brightens_that_channel():
     up = oracle.shade(3e-3 - 0.2 * XX, pix, pix, 3e-3, rp)[5, 5, 0]
     down = oracle.shade(3e-3 + 0.2 * XX, pix, pix, 3e-3, rp)[5, 5, 0]
     assert up > flat > down
+
+
+# ---------------------------------------------------------------------------
+# Indenter represented by particles (Eq. 10, p in I)
+
+def _particle_indenter_sim(w):
+    s = oracle.Sim(6, 6, 2, 0.5e-3, 3.0e5, 0.45, 1000.0)
+    u, fl = oracle.lattice(6, 6, 2, 4, 3, 5, True)
+    s.set_state(u)
+    pts = W.indenter_points("sphere", (1.2e-3,), 400, seed=3, reach=0.6e-3)
+    pose = (1.5e-3, 1.4e-3, 1.0e-3 + 1.2e-3 - 0.2e-3, math.cos(0.2), 0.0, math.sin(0.2) * 0.6, math.sin(0.2) * 0.8)
+    vel = (0.05, -0.02, -0.3) + tuple(w)
+    s.set_indenter(oracle.IND_SPHERE, (1.2e-3,), pose, vel)
+    return s, pts, pose, vel
+
+
+def test_particle_indenter_adds_its_mass_momentum_and_angular_momentum():
+    # Indenter particles add m_I per particle (partition of unity), m_I v_p
+    # in total (sum_i w (X_i - x) = 0) and, about the indenter centre c,
+    # m_I (r_p x v_p + dX^2 / 2 w) each: sum_i w d x (w x d) = (tr D - D) w
+    # with D = sum_i w d d^T = dX^2 / 4 I for the quadratic B-spline.
+    w = (40.0, -25.0, 60.0)
+    s, pts, pose, vel = _particle_indenter_sim(w)
+    dt, mI, dx = 1e-5, 2.5e-8, 0.5e-3
+    m0, g0 = s.p2g(dt)
+    s.set_indenter_particles(pts, mI)
+    m1, g1 = s.p2g(dt)
+    dm, dg = m1 - m0, g1 - g0
+    qw, qx, qy, qz = pose[3:]
+    Rm = np.array([[1 - 2 * (qy * qy + qz * qz), 2 * (qx * qy - qw * qz), 2 * (qx * qz + qw * qy)],
+                   [2 * (qx * qy + qw * qz), 1 - 2 * (qx * qx + qz * qz), 2 * (qy * qz - qw * qx)],
+                   [2 * (qx * qz - qw * qy), 2 * (qy * qz + qw * qx), 1 - 2 * (qx * qx + qy * qy)]])
+    r = pts @ Rm.T
+    v = np.array(vel[:3]) + np.cross(np.array(w), r)
+    assert dm.sum() == pytest.approx(len(pts) * mI, rel=1e-12)
+    assert np.allclose(dg.sum(axis=1), mI * v.sum(axis=0), rtol=1e-10, atol=1e-20)
+    X = s.node_positions().T
+    L = np.cross(X - np.array(pose[:3]), dg.T).sum(axis=0)
+    Lp = mI * (np.cross(r, v).sum(axis=0) + len(pts) * dx * dx / 2 * np.array(w))
+    assert np.allclose(L, Lp, rtol=1e-9, atol=1e-24)
+
+
+def test_particle_indenter_leaves_grid_nodes_to_the_momentum():
+    # with particles, nodes inside the shape take MG / M like any other node
+    s, pts, pose, vel = _particle_indenter_sim((0.0, 0.0, 0.0))
+    s.set_indenter_particles(pts, 2.5e-8)
+    s.substep(1e-5)
+    m, g = s.last_grid()
+    V = s.last_grid_velocity()
+    G = s.G
+
+    def ijk(n):
+        return n % G[0], (n // G[0]) % G[1], n // (G[0] * G[1])
+
+    def interior(n):  # clear of the padding band and of the fixed base
+        i, j, k = ijk(n)
+        return min(i, j) >= 2 and k > 3 and i <= G[0] - 3 and j <= G[1] - 3 and k <= G[2] - 3
+
+    inside = [n for n in range(s.nodes) if m[n] > 0 and interior(n) and s.node_inside(*ijk(n))]
+    assert len(inside) > 5
+    for n in inside:
+        assert np.allclose(V[:, n], g[:, n] / m[n], rtol=1e-12, atol=0)
+    # nodes the elastomer's mass also reaches move slower than the indenter
+    assert any(not np.allclose(V[:, n], vel[:3]) for n in inside)
+    # back to the grid boundary: the nodes inside take the rigid velocity
+    s.set_indenter_particles(np.zeros((0, 3)), 1.0)
+    s.substep(1e-5)
+    V = s.last_grid_velocity()
+    n = [q for q in range(s.nodes) if interior(q) and s.node_inside(*ijk(q))][0]
+    assert np.allclose(V[:, n], vel[:3], rtol=1e-12, atol=1e-15)

@@ -317,3 +317,40 @@ def c4_queries(rate_hz=4096.0, duration_s=1.0, seed=4, out_of_range=0.10):
         out.append(spec)
         i += 1
     return out
+
+
+def indenter_points(kind, params, n, seed=0, reach=1.0e-3):
+    """n points sampled uniformly (numpy PCG64, seed) inside an analytic
+    indenter, in its local frame (m), restricted to the part within `reach`
+    of its lowest point (the part that can touch the elastomer): the point
+    cloud of a particle-represented indenter.  Shapes and frames as in the
+    C ABI: sphere (radius; centre at the origin), cylinder (radius, half
+    length along local x; axis through the origin), cone (half angle,
+    height; apex at the origin, opening to +z), prism (half angle, half
+    length along local y, height; edge at the origin, opening to +z)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    while sum(len(o) for o in out) < n:
+        m = 4 * n
+        if kind == "sphere":
+            R = params[0]
+            p = rng.uniform([-R, -R, -R], [R, R, -R + reach], (m, 3))
+            p = p[(p ** 2).sum(1) <= R * R]
+        elif kind == "cylinder":
+            R, L = params[0], params[1]
+            p = rng.uniform([-L, -R, -R], [L, R, -R + reach], (m, 3))
+            p = p[p[:, 1] ** 2 + p[:, 2] ** 2 <= R * R]
+        elif kind == "cone":
+            t = math.tan(params[0])
+            h = min(params[1], reach)
+            p = rng.uniform([-h * t, -h * t, 0.0], [h * t, h * t, h], (m, 3))
+            p = p[np.hypot(p[:, 0], p[:, 1]) <= t * p[:, 2]]
+        elif kind == "prism":
+            t, L = math.tan(params[0]), params[1]
+            h = min(params[2], reach)
+            p = rng.uniform([-h * t, -L, 0.0], [h * t, L, h], (m, 3))
+            p = p[np.abs(p[:, 0]) <= t * p[:, 2]]
+        else:
+            raise ValueError(kind)
+        out.append(p)
+    return np.concatenate(out)[:n]
