@@ -317,6 +317,23 @@ tacchi_status tacchi_batch_set_state(tacchi_handle h, int i, const float *u, con
 tacchi_status tacchi_batch_displacement_map(tacchi_handle h, int i, int w, int hgt, const double window_m[4],
                                             float *out_dev);
 
+/* Indenter represented by particles, the paper's own contact model (Eq. 10:
+ * the particles of set I share the rigid indenter's velocity; Sec. III-C:
+ * they are initialised from a point cloud of the object, and a sparse cloud
+ * gives the surface "defects" of Sec. IV-B).  local_m: host float [n][3],
+ * positions (m) in the indenter's local frame (the frame its pose maps to
+ * the world); mass_kg: the mass of each.  At the pose of the start of every
+ * substep each particle adds w m and w m (v + C (X_i - x)) to its grid nodes
+ * (Eqs. 2-4), with v the rigid velocity at its position and C = skew of the
+ * angular velocity, and no elastic term; grid nodes are then no longer
+ * overridden by the shape, which keeps serving the penetration map.  n = 0
+ * returns instance i to the grid-boundary indenter.  Synchronises; drops
+ * cached step graphs.  Errors: INVALID_ARG (n < 0 or > 2^26, non-finite
+ * positions, mass <= 0), OOM, CUDA. */
+tacchi_status tacchi_batch_set_indenter_particles(tacchi_handle h, int i, int n, const float *local_m,
+                                                  double mass_kg);
+tacchi_status tacchi_set_indenter_particles(tacchi_handle h, int n, const float *local_m, double mass_kg);
+
 /* Marker motion (the outlook of Sec. V: markers on the elastomer surface are
  * particles that share the markers' positions, so recording the surface
  * particles' motion gives the markers').  Marker k of instance i at rest at

@@ -235,6 +235,12 @@ class Tacchi:
         check(lib().tacchi_set_state(self._h, ptr(tu), ptr(tv), ptr(tC), ptr(tF)), "tacchi_set_state")
         check(lib().tacchi_sync(self._h), "tacchi_set_state")
 
+    def set_indenter_particles(self, pts, mass):
+        """Indenter represented by particles (see TacchiBatch)."""
+        a = np.ascontiguousarray(np.asarray(pts, np.float32).reshape(-1, 3))
+        check(lib().tacchi_set_indenter_particles(self._h, a.shape[0], a.ctypes.data_as(C.POINTER(C.c_float)),
+                                                  float(mass)), "tacchi_set_indenter_particles")
+
     def markers(self, xy, out=None):
         """Marker displacement (m) at rest positions xy [n, 2] (see
         TacchiBatch.markers)."""
@@ -387,6 +393,14 @@ class TacchiBatch:
         check(lib().tacchi_batch_displacement_map(self._h, i, w, h, (C.c_double * 4)(*window), ptr(out)),
               "tacchi_batch_displacement_map")
         return out
+
+    def set_indenter_particles(self, i, pts, mass):
+        """Represent instance i's indenter by particles at local positions
+        pts (m, [n, 3]) of the given mass each (the paper's Eq. 10 model); an
+        empty array returns it to the grid-boundary indenter."""
+        a = np.ascontiguousarray(np.asarray(pts, np.float32).reshape(-1, 3))
+        check(lib().tacchi_batch_set_indenter_particles(self._h, i, a.shape[0], a.ctypes.data_as(C.POINTER(C.c_float)),
+                                                        float(mass)), "tacchi_batch_set_indenter_particles")
 
     def markers(self, i, xy, out=None):
         """Displacement (m) of the markers at rest positions xy [n, 2] (m,

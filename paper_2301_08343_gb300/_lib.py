@@ -97,6 +97,8 @@ EXTRA_SIGNATURES = {
     "tacchi_batch_reset": (C.c_int, [_vp]),
     "tacchi_batch_displacement_map": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _dp, _vp]),
     "tacchi_batch_markers": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp]),
+    "tacchi_batch_set_indenter_particles": (C.c_int, [_vp, C.c_int, C.c_int, _fp, C.c_double]),
+    "tacchi_set_indenter_particles": (C.c_int, [_vp, C.c_int, _fp, C.c_double]),
     "tacchi_batch_penetration_map": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _dp, _vp]),
     "tacchi_autotune": (C.c_int, [_vp, C.c_int, C.c_double, C.POINTER(C.c_int), _dp]),
     "tacchi_nn_create": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,

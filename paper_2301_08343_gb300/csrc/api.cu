@@ -148,6 +148,8 @@ struct InstHost {
   float *d_hm = nullptr;
   double pose[7] = {0, 0, 0, 1, 0, 0, 0};
   double vel[6] = {0, 0, 0, 0, 0, 0};
+  std::vector<float> ind_pts;  // indenter particles, local positions (cells), [n][3]
+  double ind_mass = 0;
 };
 
 struct tacchi_ctx {
@@ -167,6 +169,8 @@ struct tacchi_ctx {
   uint32_t *d_block_inst = nullptr;
   IndenterFrame *d_frames = nullptr;  // [n_inst][kMaxChunk]
   uint32_t *d_surf = nullptr;
+  float *d_ind_pts = nullptr;      // indenter particles of all instances [Np][3]
+  uint32_t *d_ind_inst = nullptr;  // [Np]
   float *d_z0 = nullptr;
   float *d_srest = nullptr;  // [3][Ns_tot] rest positions of the surface particles (cells)
   float *d_u0 = nullptr;     // [3][Ntot] initial positions (for tacchi_batch_reset)
@@ -334,9 +338,11 @@ cudaError_t build_graph(tacchi_ctx *c, int n, float dt, GraphEntry *ge) {
   cudaStream_t s = c->cap;
   cudaError_t le = cudaMemsetAsync(b.gmm, 0, sizeof(float4) * c->Nnodes, s);
   if (le == cudaSuccess) le = timed(c, pe, 2, [&] { return launch_transfer(b, blk, XFER_P2G, dt, s); });
+  if (le == cudaSuccess && b.Np > 0) le = timed(c, pe, 2, [&] { return launch_indenter_p2g(b, 0, s); });
   for (int k = 0; k + 1 < n && le == cudaSuccess; ++k) {
     le = timed(c, pe, 0, [&] { return launch_grid_update(b, k, dt, 1, s); });
     if (le == cudaSuccess) le = timed(c, pe, 1, [&] { return launch_transfer(b, blk, XFER_FUSED, dt, s); });
+    if (le == cudaSuccess && b.Np > 0) le = timed(c, pe, 1, [&] { return launch_indenter_p2g(b, k + 1, s); });
     if (le == cudaSuccess) le = timed(c, pe, 3, [&] { return launch_sort(b, blk, 0, s); });
   }
   if (le == cudaSuccess) le = timed(c, pe, 0, [&] { return launch_grid_update(b, n - 1, dt, 0, s); });
@@ -534,6 +540,8 @@ void release(tacchi_ctx *c) {
   drop_graphs(c);
   for (auto &h : c->in)
     if (h.d_hm) cudaFree(h.d_hm);
+  cudaFree(c->d_ind_pts);
+  cudaFree(c->d_ind_inst);
   void *bufs[] = {c->b.ps, c->b.v, c->b.C, (void *)c->b.flags, c->b.idx, c->b.key, c->b.bstart,
                   c->b.bcount, c->b.cursor, c->b.gmm, c->b.gv, c->b.err, c->b.movers, c->d_inst,
                   c->d_node_offs, c->d_part_offs, c->d_block_inst, c->d_frames, c->d_surf, c->d_z0, c->d_srest,
@@ -869,6 +877,60 @@ tacchi_status tacchi_batch_set_indenter(tacchi_handle c, int i, const tacchi_ind
 tacchi_status tacchi_set_indenter(tacchi_handle c, const tacchi_indenter_desc *d, const double pose[7],
                                   const double vel[6]) {
   return tacchi_batch_set_indenter(c, 0, d, pose, vel);
+}
+
+tacchi_status tacchi_batch_set_indenter_particles(tacchi_handle c, int i, int n, const float *local_m,
+                                                  double mass_kg) {
+  if (check_index(c, i) != TACCHI_OK || n < 0 || n > (1 << 26)) return TACCHI_ERR_INVALID_ARG;
+  if (n > 0 && (!local_m || !(mass_kg > 0) || !std::isfinite(mass_kg))) return TACCHI_ERR_INVALID_ARG;
+  InstHost &h = c->in[i];
+  std::vector<float> pts((size_t)3 * n);
+  for (long long e = 0; e < 3LL * n; ++e) {
+    if (!std::isfinite(local_m[e])) return TACCHI_ERR_INVALID_ARG;
+    pts[e] = (float)((double)local_m[e] / h.dx);
+  }
+  // rebuild the concatenated arrays of all instances; queued work may still
+  // read the old ones, and captured graphs hold their pointers
+  CK(cudaStreamSynchronize(c->stream));
+  drop_graphs(c);
+  h.ind_pts.swap(pts);
+  h.ind_mass = n > 0 ? mass_kg : 0.0;
+  h.dev.ind_np = n;
+  h.dev.ind_m = (float)h.ind_mass;
+  long long total = 0;
+  for (auto &q : c->in) total += (long long)(q.ind_pts.size() / 3);
+  cudaFree(c->d_ind_pts);
+  cudaFree(c->d_ind_inst);
+  c->d_ind_pts = nullptr;
+  c->d_ind_inst = nullptr;
+  c->b.Np = 0;
+  c->b.ind_pts = nullptr;
+  c->b.ind_inst = nullptr;
+  if (total > 0) {
+    std::vector<float> all;
+    std::vector<uint32_t> inst;
+    all.reserve((size_t)3 * total);
+    inst.reserve((size_t)total);
+    for (int k = 0; k < c->n_inst(); ++k) {
+      all.insert(all.end(), c->in[k].ind_pts.begin(), c->in[k].ind_pts.end());
+      inst.insert(inst.end(), c->in[k].ind_pts.size() / 3, (uint32_t)k);
+    }
+    if (cudaMalloc((void **)&c->d_ind_pts, sizeof(float) * all.size()) != cudaSuccess ||
+        cudaMalloc((void **)&c->d_ind_inst, sizeof(uint32_t) * inst.size()) != cudaSuccess) {
+      cudaGetLastError();
+      return TACCHI_ERR_OOM;
+    }
+    CK(cudaMemcpy(c->d_ind_pts, all.data(), sizeof(float) * all.size(), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(c->d_ind_inst, inst.data(), sizeof(uint32_t) * inst.size(), cudaMemcpyHostToDevice));
+    c->b.Np = total;
+    c->b.ind_pts = c->d_ind_pts;
+    c->b.ind_inst = c->d_ind_inst;
+  }
+  return TACCHI_OK;
+}
+
+tacchi_status tacchi_set_indenter_particles(tacchi_handle c, int n, const float *local_m, double mass_kg) {
+  return tacchi_batch_set_indenter_particles(c, 0, n, local_m, mass_kg);
 }
 
 tacchi_status tacchi_batch_get_indenter_pose(tacchi_handle c, int i, double pose[7]) {

@@ -52,7 +52,8 @@ __device__ __forceinline__ void polar_rotation_delta(const float H[9], float Y[9
     const float m2 = c[0] + c[4] + c[8];
     const float dY = Y[0] * c[0] + Y[1] * c[1] + Y[2] * c[2];
     const float d = (Y[0] + Y[4] + Y[8]) + m2 + dY;
-    const float inv = 1.0f / (1.0f + d);
+    // approximate reciprocal: the iteration corrects its own rounding
+    const float inv = __fdividef(1.0f, 1.0f + d);
     const float s = -(m2 + dY);
     float Yn[9];
     float diff = 0.f;
@@ -129,7 +130,7 @@ __global__ void __launch_bounds__(256) k_grid_update(Batch b, int substep, float
     V1 = mm.z / mm.x + I.gdt[1] * dt;
     V2 = mm.w / mm.x + I.gdt[2] * dt;
   }
-  if (I.shape.kind != IND_NONE) {
+  if (I.shape.kind != IND_NONE && I.ind_np == 0) {  // grid-boundary indenter
     const IndenterFrame f = I.frames[substep];
     if (inside_indenter(I.shape, f, i, j, k)) {  // rigid indenter velocity
       const float r0 = ((float)i - f.c[0]) * I.dx;
@@ -808,6 +809,62 @@ __global__ void __launch_bounds__(256) k_sort_scatter(Batch b, int force) {
     base_slot = __shfl_sync(0xFFFFFFFFu, base_slot, leader);
     if (valid) b.idx[base_slot + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)p;
   }
+}
+
+// ---------------------------------------------------------------------------
+// Indenter represented by particles (Eq. 10, p in I; Sec. III-C: initialised
+// from a point cloud of the object): each particle sits at x = c + R l on
+// the rigid indenter and moves with it, v = v_c + w x (x - c), so its affine
+// velocity (Eq. 4) is C = skew(w); a rigid particle carries no elastic
+// stress (Eq. 5 adds nothing).  It adds its mass and momentum to the grid
+// nodes of its stencil inside the grid (Eqs. 2-4) with vector reductions.
+__global__ void __launch_bounds__(256) k_indenter_p2g(Batch b, int substep) {
+  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= b.Np) return;
+  const Instance &I = b.inst[b.ind_inst[q]];
+  const IndenterFrame f = I.frames[substep];
+  const float l0 = b.ind_pts[3 * q], l1 = b.ind_pts[3 * q + 1], l2 = b.ind_pts[3 * q + 2];
+  float r[3], x[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    r[a] = f.r[a * 3 + 0] * l0 + f.r[a * 3 + 1] * l1 + f.r[a * 3 + 2] * l2;  // cells
+    x[a] = f.c[a] + r[a];
+  }
+  const float dx = I.dx, m = I.ind_m;
+  const float v0 = f.vlin[0] + (f.w[1] * r[2] - f.w[2] * r[1]) * dx;
+  const float v1 = f.vlin[1] + (f.w[2] * r[0] - f.w[0] * r[2]) * dx;
+  const float v2 = f.vlin[2] + (f.w[0] * r[1] - f.w[1] * r[0]) * dx;
+  int bs[3];
+  float wt[3][3], dp[3][3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    bs[a] = (int)floorf(x[a] - 0.5f);
+    bspline3(x[a] - (float)bs[a], wt[a], dp[a]);
+  }
+  float4 *gmm = b.gmm + I.node_off;
+  const int G0 = I.G[0], G1 = I.G[1], G2 = I.G[2];
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int j = 0; j < 3; ++j)
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const int X = bs[0] + i, Y = bs[1] + j, Z = bs[2] + k;
+        if (X < 0 || Y < 0 || Z < 0 || X >= G0 || Y >= G1 || Z >= G2) continue;
+        const float w = wt[0][i] * wt[1][j] * wt[2][k];
+        // node offset from the particle (m) and its rigid velocity w x d
+        const float d0 = dp[0][i] * dx, d1 = dp[1][j] * dx, d2 = dp[2][k] * dx;
+        const float mw = m * w;
+        atomicAdd(gmm + ((long long)Z * G1 + Y) * G0 + X,
+                  make_float4(mw, mw * (v0 + (f.w[1] * d2 - f.w[2] * d1)), mw * (v1 + (f.w[2] * d0 - f.w[0] * d2)),
+                              mw * (v2 + (f.w[0] * d1 - f.w[1] * d0))));
+      }
+}
+
+cudaError_t launch_indenter_p2g(const Batch &b, int substep, cudaStream_t st) {
+  if (b.Np <= 0) return cudaSuccess;
+  k_indenter_p2g<<<(unsigned)((b.Np + 255) / 256), 256, 0, st>>>(b, substep);
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------

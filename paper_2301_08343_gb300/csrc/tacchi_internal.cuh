@@ -68,6 +68,8 @@ struct Instance {
   float gdt[3];      // gravity (m/s^2), multiplied by dt on use
   IndenterShape shape;
   const IndenterFrame *frames;  // [substep] for the running step chunk
+  int ind_np;        // indenter particles (Eq. 10, p in I); 0: the grid boundary
+  float ind_m;       // mass of each indenter particle (kg)
 };
 
 struct Batch {
@@ -82,6 +84,11 @@ struct Batch {
   const uint8_t *flags;
   uint32_t *idx, *key, *bstart, *bcount, *cursor;
   float4 *gmm, *gv;
+  // indenter particles of all instances: local positions (cells) and the
+  // instance of each
+  const float *ind_pts;         // [Np][3]
+  const uint32_t *ind_inst;     // [Np]
+  long long Np;
   int *err;
   int *movers;  // [0] a particle left its block in the last transfer; [1] sorts that did work
 };
@@ -172,6 +179,8 @@ cudaError_t launch_grid_update(const Batch &b, int substep, float dt, int clear,
 cudaError_t launch_transfer(const Batch &b, SortBlock blk, int mode, float dt, cudaStream_t st);
 cudaError_t launch_sort(const Batch &b, SortBlock blk, int force, cudaStream_t st);
 cudaError_t prepare_transfer(SortBlock blk);
+// P2G of the indenter particles of every instance at the frame of `substep`.
+cudaError_t launch_indenter_p2g(const Batch &b, int substep, cudaStream_t st);
 // Particles [o, o + n) of the records from / to structure-of-arrays u [3][n]
 // and Fm [9][n] (F - I); a null Fm packs F = I, a null output is skipped.
 cudaError_t launch_pack_state(float4 *ps, long long o, long long n, const float *u, const float *Fm,
