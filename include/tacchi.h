@@ -354,6 +354,26 @@ tacchi_status tacchi_batch_markers(tacchi_handle h, int i, int n, const float *x
 tacchi_status tacchi_batch_penetration_map(tacchi_handle h, int i, int w, int hgt, const double window_m[4],
                                            float *out_dev);
 
+/* Comparison renderer: the depth-smoothing simulators Tacchi is compared
+ * with in Sec. II build a pseudo elastomer surface by smoothing the
+ * indenter's depth map with a Gaussian kernel, with no physics; the image is
+ * then shaded like Tacchi's (Eqs. 12-14).  For instance i at its current
+ * pose: p = the penetration map of tacchi_batch_penetration_map, extended
+ * beyond the window (evaluated from the shape); s = p convolved with the
+ * normalised discrete Gaussian of standard deviation sigma_m (m) on the
+ * pixel lattice, truncated at R = ceil(3 sigma_m / pitch) pixels per axis
+ * (sigma_m = 0: s = p); out_height = z_top - s; out_rgb = its shading with
+ * rp (required).  out_rgb [hgt][w][3], out_height [hgt][w] or NULL;
+ * each a device or a host pointer (host: the call synchronises).  Only
+ * rotations about the vertical axis.  Errors: INVALID_ARG (a tilted pose,
+ * sigma_m < 0 or not finite, R > 256 pixels, hgt + 2 R > 65535, a bad
+ * window, rp NULL), OOM, CUDA. */
+tacchi_status tacchi_batch_render_smoothed(tacchi_handle h, int i, const tacchi_render_params *rp, int w, int hgt,
+                                           const double window_m[4], double sigma_m, float *out_rgb,
+                                           float *out_height);
+tacchi_status tacchi_render_smoothed(tacchi_handle h, const tacchi_render_params *rp, int w, int hgt,
+                                     const double window_m[4], double sigma_m, float *out_rgb, float *out_height);
+
 /* Put every instance back to its initial particle lattice (v = 0, C = 0,
  * F = I), clear the device error and re-sort; indenters are kept.  Lets a
  * caller reuse one handle (and its cached step graphs) for new presses.

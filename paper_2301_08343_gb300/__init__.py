@@ -217,6 +217,16 @@ class Tacchi:
                                   ptr(out), ptr(out_height)), "tacchi_render")
         return out
 
+    def render_smoothed(self, w, h, sigma_m, window=None, rp=None, out=None, out_height=None):
+        """Comparison renderer: the indenter's depth map smoothed by a
+        Gaussian of standard deviation sigma_m, shaded (see TacchiBatch)."""
+        torch = self._torch
+        rp = rp or default_render_params()
+        out = out if out is not None else torch.empty((h, w, 3), device=self.device, dtype=torch.float32)
+        check(lib().tacchi_render_smoothed(self._h, C.byref(rp), w, h, self._window(window), float(sigma_m),
+                                           ptr(out), ptr(out_height)), "tacchi_render_smoothed")
+        return out
+
     # -- state ----------------------------------------------------------------
     def get_state(self):
         torch = self._torch
@@ -385,6 +395,19 @@ class TacchiBatch:
         out = out if out is not None else torch.empty((h, w, 3), device=self.device, dtype=torch.float32)
         check(lib().tacchi_batch_render(self._h, i, C.byref(rp), w, h, (C.c_double * 4)(*window),
                                         fill_radius, ptr(out), ptr(out_height)), "tacchi_batch_render")
+        return out
+
+    def render_smoothed(self, i, w, h, window, sigma_m, rp=None, out=None, out_height=None):
+        """The depth-smoothing renderers of Sec. II, for comparison: the
+        indenter's penetration map convolved with a Gaussian of standard
+        deviation sigma_m (m, truncated at 3 sigma), H = z_top - that, shaded
+        by Eqs. 12-14.  No physics."""
+        torch = self._torch
+        rp = rp or default_render_params()
+        out = out if out is not None else torch.empty((h, w, 3), device=self.device, dtype=torch.float32)
+        check(lib().tacchi_batch_render_smoothed(self._h, i, C.byref(rp), w, h, (C.c_double * 4)(*window),
+                                                 float(sigma_m), ptr(out), ptr(out_height)),
+              "tacchi_batch_render_smoothed")
         return out
 
     def displacement_map(self, i, w, h, window, out=None):

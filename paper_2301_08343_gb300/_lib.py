@@ -100,6 +100,10 @@ EXTRA_SIGNATURES = {
     "tacchi_batch_set_indenter_particles": (C.c_int, [_vp, C.c_int, C.c_int, _fp, C.c_double]),
     "tacchi_set_indenter_particles": (C.c_int, [_vp, C.c_int, _fp, C.c_double]),
     "tacchi_batch_penetration_map": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _dp, _vp]),
+    "tacchi_batch_render_smoothed": (C.c_int, [_vp, C.c_int, C.POINTER(RenderParams), C.c_int, C.c_int, _dp,
+                                               C.c_double, _vp, _vp]),
+    "tacchi_render_smoothed": (C.c_int, [_vp, C.POINTER(RenderParams), C.c_int, C.c_int, _dp, C.c_double, _vp,
+                                         _vp]),
     "tacchi_autotune": (C.c_int, [_vp, C.c_int, C.c_double, C.POINTER(C.c_int), _dp]),
     "tacchi_nn_create": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.c_int, C.c_int, C.c_int, C.c_int, C.c_int,
                                    C.c_uint64, _vp, C.POINTER(_vp)]),

@@ -1091,12 +1091,9 @@ tacchi_status tacchi_batch_markers(tacchi_handle c, int i, int n, const float *x
   return TACCHI_OK;
 }
 
-tacchi_status tacchi_batch_penetration_map(tacchi_handle c, int i, int w, int h, const double window_m[4],
-                                           float *out_dev) {
-  if (check_index(c, i) != TACCHI_OK || !out_dev) return TACCHI_ERR_INVALID_ARG;
-  tacchi_status s = validate_window(w, h, window_m, 0);
-  if (s != TACCHI_OK) return s;
-  const InstHost &I = c->in[i];
+// Penetration-map arguments of instance i over the window's pixel centres;
+// INVALID_ARG for a pose tilted out of the horizontal plane.
+tacchi_status fill_penmap_args(const InstHost &I, int w, int h, const double *window_m, PenMapArgs *out) {
   const double *q = I.pose + 3;
   const double qn = std::sqrt(q[0] * q[0] + q[1] * q[1] + q[2] * q[2] + q[3] * q[3]);
   if (std::fabs(q[1]) > 1e-9 * qn || std::fabs(q[2]) > 1e-9 * qn) return TACCHI_ERR_INVALID_ARG;  // yaw only
@@ -1123,9 +1120,86 @@ tacchi_status tacchi_batch_penetration_map(tacchi_handle c, int i, int w, int h,
   a.PH = (float)((window_m[3] - window_m[1]) / h);
   a.w = w;
   a.h = h;
+  *out = a;
+  return TACCHI_OK;
+}
+
+tacchi_status tacchi_batch_penetration_map(tacchi_handle c, int i, int w, int h, const double window_m[4],
+                                           float *out_dev) {
+  if (check_index(c, i) != TACCHI_OK || !out_dev) return TACCHI_ERR_INVALID_ARG;
+  tacchi_status s = validate_window(w, h, window_m, 0);
+  if (s != TACCHI_OK) return s;
+  PenMapArgs a;
+  s = fill_penmap_args(c->in[i], w, h, window_m, &a);
+  if (s != TACCHI_OK) return s;
   a.out = out_dev;
   CK(launch_penmap(a, c->stream));
   return TACCHI_OK;
+}
+
+// Normalised discrete Gaussian g(0..R) of standard deviation sigma on a
+// lattice of pitch P, R = ceil(3 sigma / P) (R = 0: the identity).
+static int gaussian_half(double sigma, double pitch, float *g) {
+  const int R = sigma > 0.0 ? (int)std::ceil(3.0 * sigma / pitch) : 0;
+  if (R > kMaxSmoothRadius) return -1;
+  double v[kMaxSmoothRadius + 1], sum = 0.0;
+  for (int k = 0; k <= R; ++k) {
+    v[k] = R ? std::exp(-(k * pitch) * (k * pitch) / (2.0 * sigma * sigma)) : 1.0;
+    sum += k ? 2.0 * v[k] : v[k];
+  }
+  for (int k = 0; k <= R; ++k) g[k] = (float)(v[k] / sum);
+  return R;
+}
+
+tacchi_status tacchi_batch_render_smoothed(tacchi_handle c, int i, const tacchi_render_params *rp, int w, int h,
+                                           const double window_m[4], double sigma_m, float *out_rgb,
+                                           float *out_height) {
+  if (check_index(c, i) != TACCHI_OK || !out_rgb || !(sigma_m >= 0.0) || !std::isfinite(sigma_m))
+    return TACCHI_ERR_INVALID_ARG;
+  tacchi_status s = validate_window(w, h, window_m, 0);
+  if (s != TACCHI_OK) return s;
+  const double PW = (window_m[2] - window_m[0]) / w, PH = (window_m[3] - window_m[1]) / h;
+  SmoothArgs a{};
+  s = fill_penmap_args(c->in[i], w, h, window_m, &a.pen);
+  if (s != TACCHI_OK) return s;
+  a.rx = gaussian_half(sigma_m, PW, a.gx);
+  a.ry = gaussian_half(sigma_m, PH, a.gy);
+  if (a.rx < 0 || a.ry < 0 || h + 2 * a.ry > 65535) return TACCHI_ERR_INVALID_ARG;
+  ShadeArgs sa;
+  s = fill_shade_args(rp, w, h, PW, PH, c->in[i].z_top, &sa);
+  if (s != TACCHI_OK) return s;
+  const bool rgb_dev = is_device_ptr(out_rgb);
+  const bool h_dev = out_height && is_device_ptr(out_height);
+  float *H = h_dev ? out_height : nullptr;
+  if (!H) {
+    CK(ensure(c, &c->d_hbuf, &c->hbuf_cap, (size_t)w * h));
+    H = c->d_hbuf;
+  }
+  // the rows pass writes [h + 2 ry][w] into the image buffer, which the
+  // shading overwrites afterwards; a handle buffer when it does not fit
+  const size_t need = (size_t)w * (h + 2 * a.ry), img = (size_t)w * h * 3;
+  float *rgb = out_rgb;
+  if (!rgb_dev || need > img) CK(ensure(c, &c->d_rgb, &c->rgb_cap, std::max(need, img)));
+  if (!rgb_dev) rgb = c->d_rgb;
+  a.tmp = need > img ? c->d_rgb : rgb;
+  a.H = H;
+  CK(launch_smoothed(a, c->stream));
+  CK(launch_shade(sa, H, rgb, c->stream));
+  bool need_sync = false;
+  if (!rgb_dev) {
+    CK(cudaMemcpyAsync(out_rgb, rgb, sizeof(float) * 3 * w * h, cudaMemcpyDeviceToHost, c->stream));
+    need_sync = true;
+  }
+  if (out_height && !h_dev) {
+    CK(cudaMemcpyAsync(out_height, H, sizeof(float) * w * h, cudaMemcpyDeviceToHost, c->stream));
+    need_sync = true;
+  }
+  return need_sync ? sync_and_check(c) : TACCHI_OK;
+}
+
+tacchi_status tacchi_render_smoothed(tacchi_handle c, const tacchi_render_params *rp, int w, int h,
+                                     const double window_m[4], double sigma_m, float *out_rgb, float *out_height) {
+  return tacchi_batch_render_smoothed(c, 0, rp, w, h, window_m, sigma_m, out_rgb, out_height);
 }
 
 tacchi_status tacchi_shade(const tacchi_render_params *rp, const float *H_dev, int w, int h, double pixel_x_m,

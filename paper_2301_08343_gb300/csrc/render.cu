@@ -213,4 +213,55 @@ cudaError_t launch_penmap(const PenMapArgs &a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+// Rows pass: one CTA per 256 pixels of an (extended) row.  The row's
+// penetration over the segment and its rx-pixel margins is evaluated once
+// into shared memory, then each thread sums its 2 rx + 1 taps.
+constexpr int kSmoothTile = 256;
+__global__ void __launch_bounds__(kSmoothTile) k_smooth_rows(SmoothArgs a) {
+  __shared__ float sp[kSmoothTile + 2 * kMaxSmoothRadius];
+  __shared__ float sg[kMaxSmoothRadius + 1];
+  const PenMapArgs &p = a.pen;
+  const int t = threadIdx.x, rx = a.rx;
+  const int r = (int)blockIdx.y - a.ry;  // window row; outside [0, h) in the margins
+  const int c0 = (int)blockIdx.x * kSmoothTile;
+  const float y = p.Y0 + (float)r * p.PH;
+  for (int e = t; e < kSmoothTile + 2 * rx; e += kSmoothTile) {
+    const int c = c0 - rx + e;
+    sp[e] = fmaxf(p.z_top - indenter_bottom(p, p.X0 + (float)c * p.PW, y), 0.f);
+  }
+  for (int e = t; e <= rx; e += kSmoothTile) sg[e] = a.gx[e];
+  __syncthreads();
+  const int c = c0 + t;
+  if (c >= p.w) return;
+  const float *q = sp + t + rx;
+  float s = sg[0] * q[0];
+  for (int k = 1; k <= rx; ++k) s = fmaf(sg[k], q[-k] + q[k], s);
+  a.tmp[(size_t)blockIdx.y * p.w + c] = s;
+}
+
+// Columns pass: thread per pixel; the 2 ry + 1 taps of a column are
+// consecutive rows of tmp, so a warp's loads are coalesced.
+__global__ void __launch_bounds__(kSmoothTile) k_smooth_cols(SmoothArgs a) {
+  __shared__ float sg[kMaxSmoothRadius + 1];
+  const int t = threadIdx.x, ry = a.ry, w = a.pen.w;
+  for (int e = t; e <= ry; e += kSmoothTile) sg[e] = a.gy[e];
+  __syncthreads();
+  const int c = (int)blockIdx.x * kSmoothTile + t;
+  if (c >= w) return;
+  const int r = (int)blockIdx.y;
+  const float *q = a.tmp + (size_t)(r + ry) * w + c;
+  float s = sg[0] * q[0];
+  for (int l = 1; l <= ry; ++l) s = fmaf(sg[l], q[-(ptrdiff_t)l * w] + q[(ptrdiff_t)l * w], s);
+  a.H[(size_t)r * w + c] = a.pen.z_top - s;
+}
+
+cudaError_t launch_smoothed(const SmoothArgs &a, cudaStream_t st) {
+  const unsigned gx = (unsigned)((a.pen.w + kSmoothTile - 1) / kSmoothTile);
+  k_smooth_rows<<<dim3(gx, (unsigned)(a.pen.h + 2 * a.ry)), kSmoothTile, 0, st>>>(a);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_smooth_cols<<<dim3(gx, (unsigned)a.pen.h), kSmoothTile, 0, st>>>(a);
+  return cudaGetLastError();
+}
+
 }  // namespace tacchi

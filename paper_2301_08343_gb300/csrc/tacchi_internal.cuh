@@ -238,6 +238,20 @@ struct PenMapArgs {
 };
 cudaError_t launch_penmap(const PenMapArgs &a, cudaStream_t st);
 
+// Gaussian-smoothed penetration map (the depth-smoothing renderers of
+// Sec. II): rows pass over the window extended by ry rows above and below
+// (penetration evaluated from the shape, also beyond the window) into tmp
+// [h + 2 ry][w], then the columns pass into H = z_top - s [h][w].
+constexpr int kMaxSmoothRadius = 256;
+struct SmoothArgs {
+  PenMapArgs pen;          // pen.out unused
+  int rx, ry;              // kernel half widths (pixels)
+  float gx[kMaxSmoothRadius + 1], gy[kMaxSmoothRadius + 1];  // g(0..R), symmetric
+  float *tmp;              // [h + 2 ry][w]
+  float *H;                // [h][w] metres
+};
+cudaError_t launch_smoothed(const SmoothArgs &a, cudaStream_t st);
+
 struct ShadeArgs {
   int n_lights;
   float dir[8][3], dif[8][3], spe[8][3], amb[3];
