@@ -457,8 +457,32 @@ __global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer(Batch 
   // round r gives thread t the cell at position r * THREADS + t, mirrored on
   // odd rounds, so the warp that took the heaviest cells of one round takes
   // the lightest of the next
+  auto work_of = [&](uint32_t r0) -> uint32_t {
+    return r0 + (((r0 / P::THREADS) & 1u) ? (uint32_t)(P::THREADS - 1 - tid) : (uint32_t)tid);
+  };
+  // first particle of work item wk
+  auto first_of = [&](uint32_t wk) -> uint32_t {
+    return grouped ? s_list[s_start[s_order[wk]]] : b.idx[start + wk];
+  };
+  // The record of the next particle -- the next of the cell, or the first of
+  // the thread's next cell -- is copied into this thread's other staging
+  // slot while the current one computes.
+  float4 *stage = reinterpret_cast<float4 *>(smem + P::OFF_STAGE) + tid;
+  auto fetch = [&](uint32_t pp, int slot) {
+    const float4 *src = gps + 3 * (long long)pp;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) cp_async16(stage + (slot * 3 + j) * P::THREADS, src + j);
+    cp_async_commit();
+  };
+  int slot = 0;
+  uint32_t pn = 0, fln = 0;
+  if (work_of(0) < nwork) {
+    pn = first_of(work_of(0));
+    fetch(pn, 0);
+    if (DO_G2P) fln = gfl[pn];
+  }
   for (uint32_t r0 = 0; r0 < nwork; r0 += P::THREADS) {
-    const uint32_t wk = r0 + (((r0 / P::THREADS) & 1u) ? (uint32_t)(P::THREADS - 1 - tid) : (uint32_t)tid);
+    const uint32_t wk = work_of(r0);
     if (wk >= nwork) continue;
     uint32_t q0, q1;
     int cx, cy, cz;
@@ -481,25 +505,24 @@ __global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer(Batch 
 #pragma unroll
       for (int e = 0; e < 27; ++e) acc01[e] = acc2w[e] = make_float2(0.f, 0.f);
     }
-    // the record of particle q+1 is copied into this thread's staging slot
-    // while particle q computes
-    float4 *stage = reinterpret_cast<float4 *>(smem + P::OFF_STAGE) + tid;
-    auto fetch = [&](uint32_t pp, int slot) {
-      const float4 *src = gps + 3 * (long long)pp;
-#pragma unroll
-      for (int j = 0; j < 3; ++j) cp_async16(stage + (slot * 3 + j) * P::THREADS, src + j);
-      cp_async_commit();
-    };
-    uint32_t pn = grouped ? s_list[q0] : b.idx[start + q0];
-    fetch(pn, 0);
-    uint32_t fln = DO_G2P ? gfl[pn] : 0u;
     for (uint32_t q = q0; q < q1; ++q) {
       const uint32_t p = pn;
       const uint32_t fl = fln;
-      const int slot = (int)((q - q0) & 1u);
+      const int cur = slot;
+      bool ahead = false;
       if (q + 1 < q1) {
         pn = grouped ? s_list[q + 1] : b.idx[start + q + 1];
-        fetch(pn, slot ^ 1);
+        ahead = true;
+      } else {
+        const uint32_t nk = work_of(r0 + P::THREADS);
+        if (nk < nwork) {
+          pn = first_of(nk);
+          ahead = true;
+        }
+      }
+      if (ahead) {
+        slot ^= 1;
+        fetch(pn, slot);
         if (DO_G2P) fln = gfl[pn];
         cp_async_wait<1>();
       } else {
@@ -507,8 +530,8 @@ __global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer(Batch 
       }
       float u[3], H[9];
       {
-        const float4 a = stage[(slot * 3 + 0) * P::THREADS], bq = stage[(slot * 3 + 1) * P::THREADS],
-                     cq = stage[(slot * 3 + 2) * P::THREADS];
+        const float4 a = stage[(cur * 3 + 0) * P::THREADS], bq = stage[(cur * 3 + 1) * P::THREADS],
+                     cq = stage[(cur * 3 + 2) * P::THREADS];
         u[0] = a.x; u[1] = a.y; u[2] = a.z;
         H[0] = a.w; H[1] = bq.x; H[2] = bq.y; H[3] = bq.z; H[4] = bq.w;
         H[5] = cq.x; H[6] = cq.y; H[7] = cq.z; H[8] = cq.w;
