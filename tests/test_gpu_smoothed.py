@@ -106,3 +106,38 @@ def test_host_buffers_zero_sigma_is_the_penetration_map_and_checks():
     with pytest.raises(RuntimeError):
         bt.render_smoothed(0, 48, 48, win, -1e-4, out_height=Hd)
     assert bt.status() == 0
+
+
+def test_full_frame_sampled_pixels():
+    """The 640 x 480 frame of the A/B benchmark (the 12 x 12 mm top face,
+    sigma 0.7 mm: kernels of 112 x 84 pixels half width): sampled pixels
+    against the oracle's direct sum over each pixel's own kernel footprint."""
+    from oracle import smoothed as S
+    P = T()
+    b = W.C3_BLOCK
+    bt = P.TacchiBatch([b])
+    z_top = b.nz * b.dx
+    R, d, yaw = 3e-3, 0.8e-3, 0.4
+    pose = (6.4e-3, 5.7e-3, z_top + R - d, math.cos(yaw / 2), 0.0, 0.0, math.sin(yaw / 2))
+    bt.set_indenter(0, P.IndenterKind.CYLINDER, (R, 4e-3), pose, (0,) * 6)
+    win = W.top_window(b)
+    w, h, sigma = 640, 480, 0.7e-3
+    Hd = torch.empty((h, w), device="cuda")
+    bt.render_smoothed(0, w, h, win, sigma, out_height=Hd)
+    Hg = Hd.cpu().numpy().astype(np.float64)
+    gx = S.gaussian_weights(sigma, (win[2] - win[0]) / w)
+    gy = S.gaussian_weights(sigma, (win[3] - win[1]) / h)
+    rx, ry = len(gx) // 2, len(gy) // 2
+    assert (rx, ry) == (112, 84)
+    xs, ys, _, _ = S.pixel_lattice(win, w, h, rx, ry)
+    rng = np.random.default_rng(2)
+    pix = [(h // 2, w // 2), (0, 0), (h - 1, w - 1)] + [tuple(q) for q in
+                                                        rng.integers((0, 0), (h, w), size=(150, 2))]
+    worst = 0.0
+    for r, c in pix:
+        X, Y = np.meshgrid(xs[c:c + 2 * rx + 1], ys[r:r + 2 * ry + 1], indexing="xy")
+        p = S.penetration(S.CYLINDER, (R, 4e-3), pose, X, Y, z_top)
+        s = S.smooth(p, gx, gy)[0, 0]
+        worst = max(worst, abs(Hg[r, c] - (z_top - s)))
+    assert float((z_top - Hd).max()) > 0.3e-3
+    assert worst <= 5e-9, worst

@@ -119,6 +119,25 @@ def test_four_levels_match_oracle():
         assert cos >= 0.995, (k, cos)
 
 
+def test_full_size_matches_oracle():
+    # the configuration the benchmark trains: 64 x 64 maps, widths up to 256
+    # (levels 64, 32, 16 and 8 pixels wide: the pixel boxes of the 3x3
+    # convolution kernels are 2, 4, 8 and 16 image rows)
+    widths = (32, 64, 128, 256)
+    net, P, x, t = make(seed=11, size=64, batch=2, widths=widths)
+    y = net.forward(x).cpu().numpy()
+    yo, _ = S.forward(P, x, widths)
+    assert rel(y, yo) <= 3e-2
+    net.gradients(x, t)
+    _, Go = S.loss_and_grad(P, x, t, widths)
+    G = unflatten(net.get_params(grads=True).astype(np.float64), widths, 2, 3)
+    for k in Go:
+        a, b = G[k].ravel(), Go[k].ravel()
+        cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-30))
+        assert rel(a, b) <= 6e-2, (k, rel(a, b))
+        assert cos >= 0.995, (k, cos)
+
+
 def test_adam_steps_reduce_the_loss_and_match_the_oracle_step():
     net, P, x, t = make(seed=5)
     l0 = net.train_step(x, t, lr=1e-3)
