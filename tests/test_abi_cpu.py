@@ -101,3 +101,17 @@ def test_null_arguments_are_rejected(L):
     rp = _lib.RenderParams()
     rp.n_lights = 9
     assert L.tacchi_shade(C.byref(rp), C.c_void_p(16), 4, 4, 1e-4, 1e-4, 0.0, C.c_void_p(16), None) == -1
+
+
+def test_null_handles_of_the_later_entry_points_are_rejected(L):
+    # the particle indenter, markers, penetration map and comparison renderer
+    # check their handle and arguments before any CUDA call
+    from paper_2301_08343_gb300 import _lib
+    rp = _lib.RenderParams()
+    win = (C.c_double * 4)(0.0, 0.0, 1e-3, 1e-3)
+    buf = C.c_void_p(16)
+    assert L.tacchi_batch_render_smoothed(None, 0, C.byref(rp), 8, 8, win, 1e-4, buf, buf) == -1
+    assert L.tacchi_render_smoothed(None, C.byref(rp), 8, 8, win, 1e-4, buf, buf) == -1
+    assert L.tacchi_batch_penetration_map(None, 0, 8, 8, win, buf) == -1
+    assert L.tacchi_batch_markers(None, 0, 4, buf, buf) == -1
+    assert L.tacchi_set_indenter_particles(None, 4, None, 1e-6) == -1
