@@ -944,6 +944,7 @@ tacchi_status tacchi_get_indenter_pose(tacchi_handle c, double pose[7]) {
 }
 
 tacchi_status tacchi_step(tacchi_handle c, int n_substeps, double dt) {
+  NvtxRange range("tacchi_step");
   if (!c || n_substeps < 1 || !(dt > 0) || !std::isfinite(dt)) return TACCHI_ERR_INVALID_ARG;
   const float fdt = (float)dt;
   const int ni = c->n_inst();
@@ -981,6 +982,7 @@ tacchi_status tacchi_step(tacchi_handle c, int n_substeps, double dt) {
 
 tacchi_status tacchi_batch_heightmap(tacchi_handle c, int i, int w, int h, const double window_m[4],
                                      int fill_radius, float *out) {
+  NvtxRange range("tacchi_heightmap");
   if (check_index(c, i) != TACCHI_OK || !out) return TACCHI_ERR_INVALID_ARG;
   tacchi_status s = validate_window(w, h, window_m, fill_radius);
   if (s != TACCHI_OK) return s;
@@ -1006,6 +1008,7 @@ tacchi_status tacchi_heightmap(tacchi_handle c, int w, int h, const double windo
 
 tacchi_status tacchi_batch_render(tacchi_handle c, int i, const tacchi_render_params *rp, int w, int h,
                                   const double window_m[4], int fill_radius, float *out_rgb, float *out_height) {
+  NvtxRange range("tacchi_render");
   if (check_index(c, i) != TACCHI_OK || !out_rgb) return TACCHI_ERR_INVALID_ARG;
   tacchi_status s = validate_window(w, h, window_m, fill_radius);
   if (s != TACCHI_OK) return s;
@@ -1154,6 +1157,7 @@ static int gaussian_half(double sigma, double pitch, float *g) {
 tacchi_status tacchi_batch_render_smoothed(tacchi_handle c, int i, const tacchi_render_params *rp, int w, int h,
                                            const double window_m[4], double sigma_m, float *out_rgb,
                                            float *out_height) {
+  NvtxRange range("tacchi_render_smoothed");
   if (check_index(c, i) != TACCHI_OK || !out_rgb || !(sigma_m >= 0.0) || !std::isfinite(sigma_m))
     return TACCHI_ERR_INVALID_ARG;
   tacchi_status s = validate_window(w, h, window_m, 0);
@@ -1286,6 +1290,7 @@ tacchi_status tacchi_set_block(tacchi_handle c, int bx, int by, int bz) {
 }
 
 tacchi_status tacchi_autotune(tacchi_handle c, int n_substeps, double dt, int best[3], double ms_per_substep[4]) {
+  NvtxRange range("tacchi_autotune");
   if (!c || !best || n_substeps < 1 || n_substeps > kMaxChunk || !(dt > 0) || !std::isfinite(dt))
     return TACCHI_ERR_INVALID_ARG;
   // save the particle state and the indenter poses

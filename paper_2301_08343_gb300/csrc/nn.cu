@@ -30,6 +30,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cmath>
 #include <cstring>
@@ -1193,6 +1194,10 @@ tacchi_status tacchi_nn_set_params(tacchi_nn_handle n, const float *host) {
 }
 
 tacchi_status tacchi_nn_forward(tacchi_nn_handle n, int batch, const float *x_dev, float *y_dev) {
+  nvtxRangePushA("tacchi_nn_forward");
+  struct Pop {
+    ~Pop() { nvtxRangePop(); }
+  } pop;
   if (!n || !x_dev || !y_dev || batch < 1 || batch > n->max_batch) return TACCHI_ERR_INVALID_ARG;
   tacchi_status s = forward(n, batch, x_dev);
   if (s != TACCHI_OK) return s;
@@ -1218,6 +1223,10 @@ tacchi_status tacchi_nn_gradients(tacchi_nn_handle n, int batch, const float *x_
 
 tacchi_status tacchi_nn_train_step(tacchi_nn_handle n, int batch, const float *x_dev, const float *target_dev,
                                    float lr, float *loss_host) {
+  nvtxRangePushA("tacchi_nn_train_step");
+  struct Pop {
+    ~Pop() { nvtxRangePop(); }
+  } pop;
   if (!n || !(lr > 0) || !std::isfinite(lr)) return TACCHI_ERR_INVALID_ARG;
   tacchi_status s = tacchi_nn_gradients(n, batch, x_dev, target_dev, nullptr);
   if (s != TACCHI_OK) return s;

@@ -18,9 +18,21 @@
 //     gv float4 (Vx, Vy, Vz, 0)
 #pragma once
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 #include <stdint.h>
 
 namespace tacchi {
+
+// NVTX range over a host API call, shown on profiler timelines (a no-op
+// unless a tool is attached).  The substep kernels run inside CUDA graphs,
+// which profilers already list kernel by kernel.
+struct NvtxRange {
+  explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange &) = delete;
+  NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 
 enum : int {
   ERRBIT_OUT_OF_GRID = 1,
