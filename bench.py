@@ -305,15 +305,17 @@ def run_batch_bench(args, rank, world, local_rank):
         for i, (b, ind) in enumerate(specs):
             bt.set_indenter(i, vel=(0, 0, -ind["depth"] / (substeps * dt), 0, 0, 0))
         tuned = bt.autotune(min(32, substeps), dt)
-    hm = torch.empty((64, 64), device=dev)
+    hms = torch.empty((len(specs), 64, 64), device=dev)
 
-    def one_step(s):
+    def one_step(s, host=None):
         sign = -1.0 if s % 2 == 0 else 1.0
         for i, (b, ind) in enumerate(specs):
             bt.set_indenter(i, vel=(0, 0, sign * ind["depth"] / (substeps * dt), 0, 0, 0))
         bt.step(substeps, dt)
         for i, (b, ind) in enumerate(specs):
-            bt.heightmap(i, 64, 64, W.top_window(b), out=hm)
+            bt.heightmap(i, 64, 64, W.top_window(b), out=hms[i])
+        if host is not None:
+            host.copy_(hms, non_blocking=True)
         st = bt.status()
         if st != 0:
             raise RuntimeError(f"batched step {s} failed with status {st}")
@@ -340,10 +342,26 @@ def run_batch_bench(args, rank, world, local_rank):
     bt.set_profiling(False)
     ms = e0.elapsed_time(e1)
     prof = bt.profile(reset=True)
-    (ms,), units_all = reduce_over_ranks([ms], bt.N_total * substeps, world, dev)
+    # end to end: per step the indenter frames go in from host memory and the
+    # 256 height maps come back to pinned host memory
+    host = torch.empty((len(specs), 64, 64)).pin_memory()
+    e_steps = max(1, min(args.steps, 2))
+    barrier()
+    t0 = time.perf_counter()
+    for s in range(e_steps):
+        one_step(args.warmup + args.steps + s, host)
+    barrier()
+    e2e_s = time.perf_counter() - t0
+    (ms, e2e_s), units_all = reduce_over_ranks([ms, e2e_s], bt.N_total * substeps, world, dev)
     value = whole_job_rate(units_all * args.steps, ms * 1e-3)
+    e2e_value = whole_job_rate(units_all * e_steps, e2e_s)
     sizes = [b.n_particles for b, _ in specs]
     fused_avg = prof["fused_ms"] / max(prof["fused_launches"], 1)
+    peaks, src = measured_peaks()
+    nodes = sum((b.nx + 2 * b.pad_side + 1) * (b.ny + 2 * b.pad_side + 1) * (b.nz + b.pad_bottom + b.pad_top + 1)
+                for b, _ in specs)
+    tfl = FLOPS_PER_PARTICLE * bt.N_total / (fused_avg * 1e-3) / 1e12
+    gbs = (BYTES_PER_PARTICLE * bt.N_total + BYTES_PER_NODE * nodes) / (fused_avg * 1e-3) / 1e9
     return {
         "metric": METRIC + " (batched sensors)", "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
@@ -358,6 +376,15 @@ def run_batch_bench(args, rank, world, local_rank):
         "kernel_share_of_step": {k: round(prof[k + "_ms"] / max(ms, 1e-9), 4)
                                  for k in ("grid", "fused", "edge", "sort")},
         "fused_avg_launch_ms": fused_avg,
+        "roofline": {"kernel": "k_transfer (fused G2P+P2G)", "bound": "alu", "achieved": round(tfl, 3),
+                     "peak": round(FP32_PEAK_TFLOPS, 1), "unit": "TFLOP/s", "frac": round(tfl / FP32_PEAK_TFLOPS, 4),
+                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz", "traffic": None,
+                     "hbm": {"achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                             "frac": round(gbs / peaks["hbm_gbs"], 4),
+                             "peak_source": f"{src} (MEASURED_PEAKS hbm_gbs)"},
+                     "avg_launch_ms": round(fused_avg, 4)},
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 72 * substeps * len(specs) + 256 * len(specs),
+                "d2h_bytes_per_step": host.numel() * 4, "steps": e_steps},
         "gpu_launches": args.steps * (5 * substeps + 1 + 3 * len(specs)),
         "clocks": clk,
     }
@@ -690,6 +717,11 @@ def main():
     if args.workload == "c2":
         result = run_batch_bench(args, rank, world, local_rank)
         if rank == 0:
+            if not args.no_cpu_baseline:
+                b0 = W.c2_instances(1, seed_base=1000)[0][0]
+                v, desc = oracle_sample(b0, W.C2_DT, args.cpu_seconds, os.cpu_count() or 1)
+                result["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                          "sample": desc.replace("of the workload", "of the first sensor")}
             print(json.dumps(result))
         if world > 1:
             torch.distributed.barrier()
