@@ -732,8 +732,10 @@ def main():
         if not args.no_cpu_baseline:
             block, dt, _, _ = WORKLOADS[args.workload]
             v, desc = oracle_sample(block, dt, args.cpu_seconds, os.cpu_count() or 1)
+            v1, desc1 = oracle_sample(block, dt, 3.0, 1)
             result["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": os.cpu_count(),
-                                      "kind": "oracle", "sample": desc}
+                                      "kind": "oracle", "sample": desc,
+                                      "single_thread": {"value": v1, "unit": UNIT, "cores": 1, "sample": desc1}}
         print(json.dumps(result))
     if world > 1:
         torch.distributed.barrier()
