@@ -412,8 +412,9 @@ tacchi_status tacchi_autotune(tacchi_handle h, int n_substeps, double dt, int be
 typedef struct tacchi_nn *tacchi_nn_handle;
 
 /* Create a network for height x width images (multiples of 2^(levels-1)),
- * in_channels <= 32, out_channels <= 16, widths multiples of 32, at most
- * max_batch images per call; weights He-normal from splitmix64(seed).
+ * in_channels <= 32, out_channels in {1, 2, 3, 4, 8, 16}, widths multiples
+ * of 32, at most max_batch images per call; weights He-normal from
+ * splitmix64(seed).
  * stream: cudaStream_t for all its work.  Errors: INVALID_ARG, OOM, CUDA. */
 tacchi_status tacchi_nn_create(int levels, const int *widths, int in_channels, int out_channels, int height,
                                int width, int max_batch, uint64_t seed, void *stream, tacchi_nn_handle *out);

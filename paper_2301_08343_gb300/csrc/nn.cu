@@ -519,28 +519,39 @@ __global__ void k_upsample_concat_bwd(const bf16 *g, bf16 *ga, bf16 *gs, int nim
 }
 // db[c] += sum over pixels of g[p][c]
 __global__ void k_bias_grad(const bf16 *g, float *db, long long P, int C) {
-  extern __shared__ float red[];
-  const int c = threadIdx.x % C, lanes = blockDim.x / C;
-  const int r = threadIdx.x / C;
-  float s = 0.f;
-  if (r < lanes)
-    for (long long p = blockIdx.x * (long long)lanes + r; p < P; p += (long long)gridDim.x * lanes)
-      s += __bfloat162float(g[p * C + c]);
-  red[threadIdx.x] = s;
+  // a thread reads one 8-channel chunk (16 bytes) per pixel; the grid's
+  // thread count is a multiple of the C / 8 chunks, so it always sums the
+  // same chunk, in registers, then per block in shared memory
+  extern __shared__ float red[];  // [C]
+  for (int t = threadIdx.x; t < C; t += blockDim.x) red[t] = 0.f;
   __syncthreads();
-  if (threadIdx.x < C) {
-    float t = 0.f;
-    for (int q = 0; q < lanes; ++q) t += red[q * C + threadIdx.x];
-    atomicAdd(db + threadIdx.x, t);
+  const int nch = C / 8;
+  const int c = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) % nch);
+  float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  GRID_STRIDE(e, P * nch) {
+    float v[8];
+    unpack8(reinterpret_cast<const uint4 *>(g)[e], v);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) acc[k] += v[k];
   }
+#pragma unroll
+  for (int k = 0; k < 8; ++k) atomicAdd(&red[c * 8 + k], acc[k]);
+  __syncthreads();
+  for (int t = threadIdx.x; t < C; t += blockDim.x) atomicAdd(db + t, red[t]);
 }
 // head: y[p][o] = b[o] + sum_i W[i][o] x[p][i] (FP32 out); one pixel per
-// thread, Ci a multiple of 8, Co <= 16
-__global__ void k_head_fwd(const bf16 *x, const float *Wh, const float *bh, float *y, unsigned P, int Ci, int Co) {
+// thread, W and b staged in shared memory (dynamic, Ci * CO + CO floats), Ci
+// a multiple of 8
+template <int CO>
+__global__ void __launch_bounds__(256) k_head_fwd(const bf16 *x, const float *Wh, const float *bh, float *y,
+                                                  unsigned P, int Ci) {
+  extern __shared__ float sw[];
+  for (int t = threadIdx.x; t < Ci * CO + CO; t += blockDim.x) sw[t] = t < Ci * CO ? Wh[t] : bh[t - Ci * CO];
+  __syncthreads();
   GRID_STRIDE_U(p, P) {
-    float acc[16];
+    float acc[CO];
 #pragma unroll
-    for (int o = 0; o < 16; ++o) acc[o] = o < Co ? bh[o] : 0.f;
+    for (int o = 0; o < CO; ++o) acc[o] = sw[Ci * CO + o];
     const uint4 *xp = reinterpret_cast<const uint4 *>(x + (long long)p * Ci);
     for (int c = 0; c < Ci / 8; ++c) {
       float xv[8];
@@ -548,14 +559,16 @@ __global__ void k_head_fwd(const bf16 *x, const float *Wh, const float *bh, floa
 #pragma unroll
       for (int k = 0; k < 8; ++k)
 #pragma unroll
-        for (int o = 0; o < 16; ++o)
-          if (o < Co) acc[o] += Wh[(c * 8 + k) * Co + o] * xv[k];
+        for (int o = 0; o < CO; ++o) acc[o] = fmaf(sw[(c * 8 + k) * CO + o], xv[k], acc[o]);
     }
-    for (int o = 0; o < Co; ++o) y[(long long)p * Co + o] = acc[o];
+#pragma unroll
+    for (int o = 0; o < CO; ++o) y[(long long)p * CO + o] = acc[o];
   }
 }
-// loss: sum of squared errors (atomic) and gy = 2 (y - t) / count
-__global__ void k_mse(const float *y, const float *t, float *gy, long long n, float *loss_sum) {
+// loss: sum of squared errors (one atomic per block) and gy = 2 (y - t) / count
+__global__ void __launch_bounds__(256) k_mse(const float *y, const float *t, float *gy, long long n,
+                                             float *loss_sum) {
+  __shared__ float red[8];
   float s = 0.f;
   const float sc = 2.0f / (float)n;
   GRID_STRIDE(e, n) {
@@ -564,45 +577,68 @@ __global__ void k_mse(const float *y, const float *t, float *gy, long long n, fl
     gy[e] = sc * d;
   }
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(loss_sum, s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float b = 0.f;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) b += red[w];
+    atomicAdd(loss_sum, b);
+  }
 }
-// head backward: gx[p][i] = sum_o W[i][o] gy[p][o] (bf16); dW, db summed in
-// registers (every thread keeps one input channel i, since the total thread
-// count is a multiple of Ci), then per block, then atomically.
-__global__ void k_head_bwd(const bf16 *x, const float *gy, const float *Wh, bf16 *gx, float *dWh, float *dbh,
-                           long long P, int Ci, int Co) {
-  extern __shared__ float part[];  // [Ci * Co + Co]
-  for (int t = threadIdx.x; t < Ci * Co + Co; t += blockDim.x) part[t] = 0.f;
+// head backward: gx[p][i] = sum_o W[i][o] gy[p][o] (bf16); dW, db.  A thread
+// takes one 8-channel chunk of a pixel (16-byte loads and stores, a warp
+// covering consecutive chunks); the grid's thread count is a multiple of the
+// Ci / 8 chunks, so every thread keeps one chunk and sums its dW in registers,
+// then per block in shared memory, then atomically.  Shared memory (dynamic):
+// W [Ci * CO], partial sums [Ci * CO + CO].
+template <int CO>
+__global__ void __launch_bounds__(256) k_head_bwd(const bf16 *x, const float *gy, const float *Wh, bf16 *gx,
+                                                  float *dWh, float *dbh, long long P, int Ci) {
+  extern __shared__ float sm[];
+  float *sw = sm, *part = sm + Ci * CO;
+  for (int t = threadIdx.x; t < Ci * CO; t += blockDim.x) sw[t] = Wh[t];
+  for (int t = threadIdx.x; t < Ci * CO + CO; t += blockDim.x) part[t] = 0.f;
   __syncthreads();
-  float aw[16], ab[16];
+  const int nch = Ci / 8;
+  const int c = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) % nch);
+  float aw[8][CO], ab[CO];
 #pragma unroll
-  for (int o = 0; o < 16; ++o) aw[o] = ab[o] = 0.f;
-  const int i = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) % Ci);
-  GRID_STRIDE(e, P * Ci) {
-    const long long p = e / Ci;
-    const float xv = __bfloat162float(x[e]);
-    float s = 0.f;
+  for (int o = 0; o < CO; ++o) {
+    ab[o] = 0.f;
 #pragma unroll
-    for (int o = 0; o < 16; ++o) {
-      if (o < Co) {
-        const float g = gy[p * Co + o];
-        s += Wh[i * Co + o] * g;
-        aw[o] += xv * g;
-        ab[o] += g;
+    for (int k = 0; k < 8; ++k) aw[k][o] = 0.f;
+  }
+  GRID_STRIDE(e, P * nch) {
+    const long long p = e / nch;
+    float g[CO];
+#pragma unroll
+    for (int o = 0; o < CO; ++o) g[o] = gy[p * CO + o];
+    float xv[8], gv[8];
+    unpack8(reinterpret_cast<const uint4 *>(x)[e], xv);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      float sk = 0.f;
+#pragma unroll
+      for (int o = 0; o < CO; ++o) {
+        sk = fmaf(sw[(c * 8 + k) * CO + o], g[o], sk);
+        aw[k][o] = fmaf(xv[k], g[o], aw[k][o]);
       }
+      gv[k] = sk;
     }
-    gx[e] = __float2bfloat16_rn(s);
+#pragma unroll
+    for (int o = 0; o < CO; ++o) ab[o] += g[o];
+    reinterpret_cast<uint4 *>(gx)[e] = pack8(gv);
   }
 #pragma unroll
-  for (int o = 0; o < 16; ++o) {
-    if (o < Co) {
-      atomicAdd(&part[i * Co + o], aw[o]);
-      if (i == 0) atomicAdd(&part[Ci * Co + o], ab[o]);
-    }
-  }
+  for (int k = 0; k < 8; ++k)
+#pragma unroll
+    for (int o = 0; o < CO; ++o) atomicAdd(&part[(c * 8 + k) * CO + o], aw[k][o]);
+  if (c == 0)
+#pragma unroll
+    for (int o = 0; o < CO; ++o) atomicAdd(&part[Ci * CO + o], ab[o]);
   __syncthreads();
-  for (int t = threadIdx.x; t < Ci * Co; t += blockDim.x) atomicAdd(dWh + t, part[t]);
-  for (int t = threadIdx.x; t < Co; t += blockDim.x) atomicAdd(dbh + t, part[Ci * Co + t]);
+  for (int t = threadIdx.x; t < Ci * CO; t += blockDim.x) atomicAdd(dWh + t, part[t]);
+  for (int t = threadIdx.x; t < CO; t += blockDim.x) atomicAdd(dbh + t, part[Ci * CO + t]);
 }
 // Adam (Kingma & Ba) on FP32 parameters; bias corrections c1 = 1 - b1^t,
 // c2 = 1 - b2^t passed in
@@ -645,6 +681,42 @@ __global__ void k_unpad_wgrad(const float *gpad, float *g, int Cin_real, int Cin
 unsigned grid_for(long long n, int threads = 256) {
   long long b = (n + threads - 1) / threads;
   return (unsigned)(b < 1 ? 1 : (b > 65535 * 8 ? 65535 * 8 : b));
+}
+
+// The head for CO output channels (compile time: its sums stay in registers).
+template <int CO>
+cudaError_t head_launch(const bf16 *x, const float *Wh, const float *bh, float *y, const bf16 *xb, const float *gy,
+                        bf16 *gx, float *dWh, float *dbh, long long P, int Ci, bool backward, cudaStream_t s) {
+  if (!backward) {
+    k_head_fwd<CO><<<grid_for(P), 256, (Ci * CO + CO) * sizeof(float), s>>>(x, Wh, bh, y, (unsigned)P, Ci);
+  } else {
+    // a bounded grid: each thread loops over many pixels with its sums in
+    // registers before the per-block reduction
+    k_head_bwd<CO><<<std::min<unsigned>(grid_for(P * (Ci / 8)), 1216u), 256, (2 * Ci * CO + CO) * sizeof(float),
+                     s>>>(xb, gy, Wh, gx, dWh, dbh, P, Ci);
+  }
+  return cudaGetLastError();
+}
+cudaError_t head_dispatch(int Co, const bf16 *x, const float *Wh, const float *bh, float *y, const bf16 *xb,
+                          const float *gy, bf16 *gx, float *dWh, float *dbh, long long P, int Ci, bool backward,
+                          cudaStream_t s) {
+  switch (Co) {
+    case 1: return head_launch<1>(x, Wh, bh, y, xb, gy, gx, dWh, dbh, P, Ci, backward, s);
+    case 2: return head_launch<2>(x, Wh, bh, y, xb, gy, gx, dWh, dbh, P, Ci, backward, s);
+    case 3: return head_launch<3>(x, Wh, bh, y, xb, gy, gx, dWh, dbh, P, Ci, backward, s);
+    case 4: return head_launch<4>(x, Wh, bh, y, xb, gy, gx, dWh, dbh, P, Ci, backward, s);
+    case 8: return head_launch<8>(x, Wh, bh, y, xb, gy, gx, dWh, dbh, P, Ci, backward, s);
+    case 16: return head_launch<16>(x, Wh, bh, y, xb, gy, gx, dWh, dbh, P, Ci, backward, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+cudaError_t head_fwd(const bf16 *x, const float *Wh, const float *bh, float *y, long long P, int Ci, int Co,
+                     cudaStream_t s) {
+  return head_dispatch(Co, x, Wh, bh, y, nullptr, nullptr, nullptr, nullptr, nullptr, P, Ci, false, s);
+}
+cudaError_t head_bwd(const bf16 *x, const float *gy, const float *Wh, bf16 *gx, float *dWh, float *dbh, long long P,
+                     int Ci, int Co, cudaStream_t s) {
+  return head_dispatch(Co, nullptr, Wh, nullptr, nullptr, x, gy, gx, dWh, dbh, P, Ci, true, s);
 }
 
 }  // namespace
@@ -848,9 +920,10 @@ cudaError_t conv_wgrad(const bf16 *X, const bf16 *G, float *dW, int nimg, int H,
 }
 
 cudaError_t bias_grad(const bf16 *G, float *db, long long P, int C, cudaStream_t s) {
-  const int lanes = 256 / C > 0 ? 256 / C : 1;
-  const int threads = lanes * C;
-  k_bias_grad<<<512, threads, threads * sizeof(float), s>>>(G, db, P, C);
+  const int nch = C / 8;
+  if (C % 8 || nch < 1 || nch > 1024) return cudaErrorInvalidValue;
+  const int threads = nch * (256 / nch > 0 ? 256 / nch : 1);  // a multiple of the chunks
+  k_bias_grad<<<512, threads, C * sizeof(float), s>>>(G, db, P, C);
   return cudaGetLastError();
 }
 
@@ -930,9 +1003,7 @@ tacchi_status forward(tacchi_nn *n, int batch, const float *x) {
       in = n->act[k + 1];
     }
   }
-  k_head_fwd<<<grid_for(P0), 256, 0, s>>>(in, n->p + n->head_w, n->p + n->head_b, n->out, (unsigned)P0,
-                                                     n->widths[0], n->cout);
-  NCK(cudaGetLastError());
+  NCK(head_fwd(in, n->p + n->head_w, n->p + n->head_b, n->out, P0, n->widths[0], n->cout, s));
   return TACCHI_OK;
 }
 
@@ -942,15 +1013,13 @@ tacchi_status backward(tacchi_nn *n, int batch, const float *target) {
   const long long P0 = (long long)batch * n->H * n->W;
   NCK(cudaMemsetAsync(n->g, 0, sizeof(float) * n->nparams, s));
   NCK(cudaMemsetAsync(n->loss, 0, sizeof(float), s));
-  k_mse<<<grid_for(P0 * n->cout), 256, 0, s>>>(n->out, target, n->gout, P0 * n->cout, n->loss);
+  k_mse<<<std::min<unsigned>(grid_for(P0 * n->cout), 1216u), 256, 0, s>>>(n->out, target, n->gout, P0 * n->cout,
+                                                                          n->loss);
   NCK(cudaGetLastError());
   const int nk = (int)n->convs.size();
   const int C0 = n->widths[0];
-  // a bounded grid: each thread loops over many pixels with its sums in
-  // registers before the per-block reduction
-  k_head_bwd<<<std::min<unsigned>(grid_for(P0 * C0), 1216u), 256, (C0 * n->cout + n->cout) * sizeof(float), s>>>(
-      n->act[nk], n->gout, n->p + n->head_w, n->gact[nk], n->g + n->head_w, n->g + n->head_b, P0, C0, n->cout);
-  NCK(cudaGetLastError());
+  NCK(head_bwd(n->act[nk], n->gout, n->p + n->head_w, n->gact[nk], n->g + n->head_w, n->g + n->head_b, P0, C0,
+               n->cout, s));
 
   // layer k's input activation and the gradient buffer of that input
   int H = n->H, W = n->W;
@@ -1032,7 +1101,8 @@ extern "C" {
 tacchi_status tacchi_nn_create(int levels, const int *widths, int in_channels, int out_channels, int height,
                                int width, int max_batch, uint64_t seed, void *stream, tacchi_nn_handle *out) {
   if (!out || !widths || levels < 1 || levels > 6 || in_channels < 1 || in_channels > 32 || out_channels < 1 ||
-      out_channels > 16 || max_batch < 1 || height < 1 || width < 1)
+      out_channels > 16 || (out_channels > 4 && out_channels != 8 && out_channels != 16) || max_batch < 1 ||
+      height < 1 || width < 1)
     return TACCHI_ERR_INVALID_ARG;
   *out = nullptr;
   if (height % (1 << (levels - 1)) || width % (1 << (levels - 1))) return TACCHI_ERR_INVALID_ARG;
