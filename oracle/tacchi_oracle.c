@@ -17,7 +17,7 @@
  *   - height map of the deformed top surface (Sec. III-B, "2D interpolation");
  *   - Phong shading, Eqs. 12-14.
  *
- * Readings where the paper is silent or garbled (each listed in the design doc):
+ * Readings where the paper is silent or garbled:
  *   - S_p of Eq. 5 is the fixed-corotated Kirchhoff stress
  *       tau = 2 mu (F - R) F^T + lambda J (J - 1) I,  R = polar factor of F;
  *   - Eq. 4 carries m_p on the affine term: w m_p (v_p + C_p (X_i - x_p));
