@@ -88,3 +88,49 @@ def test_switching_back_to_the_grid_boundary():
     g.step(20, 1e-5)
     assert o.run(20, 1e-5) == 0
     assert np.abs(g.get_state()["u"].cpu().numpy() - o.state()[0]).max() <= 1e-3
+
+
+def test_point_cloud_density_against_the_grid_boundary():
+    """The same 0.5 mm sphere press (R 3 mm, 12 x 12 x 3 mm gel at dx 0.5 mm)
+    with the grid-boundary indenter and with heavy indenter particles (Eq. 10)
+    sampled at two densities, as in the paper's point-cloud study (Sec. IV-B:
+    sparse clouds leave surface defects).  A dense cloud (16 points per cell
+    volume) carries the surface down to most of the press depth, deeper than
+    the grid boundary (whose node-by-node decision holds the surface back by
+    a fraction of a cell and leaves a stepped contact, rough at the node
+    spacing); a sparse cloud (0.2 per cell volume, 13 points) lets the gel
+    slip between its points and stops far short."""
+    import paper_2301_08343_gb300 as T
+    b = W.Block(24, 24, 6, 0.5e-3, seed=3)
+    Rs, depth, n, dt = 3e-3, 0.5e-3, 500, 1e-5
+    z_top = b.nz * b.dx
+    pose = (b.nx * b.dx / 2, b.ny * b.dx / 2, z_top + Rs, 1, 0, 0, 0)
+    vel = (0, 0, -depth / (n * dt), 0, 0, 0)
+    win = W.top_window(b)
+    cap = math.pi * 1.0e-3 ** 2 * (3 * Rs - 1.0e-3) / 3  # the sampled 1 mm cap
+
+    def press(per_cell=None):
+        g = T.Tacchi(b.extent_m, b.dx, b.E, b.nu, b.rho, seed=b.seed)
+        g.set_indenter(T.IndenterKind.SPHERE, (Rs,), pose, vel)
+        if per_cell:
+            pts = W.indenter_points("sphere", (Rs,), max(8, int(per_cell * cap / b.dx ** 3)), seed=1,
+                                    reach=1.0e-3).astype(np.float32)
+            g.set_indenter_particles(pts, 1e-5)  # about 640 gel particles' mass each
+        g.step(n, dt)
+        assert g.status() == 0
+        return g.heightmap(64, 64, win).cpu().numpy().astype(np.float64)
+
+    xs = (np.arange(64) + 0.5) * (win[2] - win[0]) / 64
+    X, Y = np.meshgrid(xs, xs)
+    inside = np.hypot(X - pose[0], Y - pose[1]) < 0.8 * math.sqrt(2 * Rs * depth)
+
+    def rough(H):  # RMS of the 5-point Laplacian over the contact
+        L = 4 * H[1:-1, 1:-1] - H[:-2, 1:-1] - H[2:, 1:-1] - H[1:-1, :-2] - H[1:-1, 2:]
+        return float(np.sqrt((L[inside[1:-1, 1:-1]] ** 2).mean()))
+
+    Hg, Hd, Hs = press(), press(16.0), press(0.2)
+    dg, dd, ds = (z_top - Hg).max(), (z_top - Hd).max(), (z_top - Hs).max()
+    assert dd >= 0.85 * depth, dd
+    assert dg <= dd - 60e-6, (dg, dd)
+    assert ds <= 0.75 * dd, (ds, dd)
+    assert rough(Hd) <= 0.6 * rough(Hg), (rough(Hd), rough(Hg))
