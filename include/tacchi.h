@@ -63,9 +63,9 @@ typedef struct {
   double density;      /* kg/m^3, > 0 */
   uint64_t seed;       /* seed of the jittered particle lattice */
   int jitter;          /* 1: jitter each particle in its sub-cell; 0: centres */
-  int pad_side;        /* grid cells around the block in x and y (0 -> 4; >= 3) */
-  int pad_bottom;      /* grid cells below the base (0 -> 3; >= 3) */
-  int pad_top;         /* grid cells above the top face (0 -> 4; >= 3) */
+  int pad_side;        /* grid cells around the block in x and y (0 -> 4; 3..1024) */
+  int pad_bottom;      /* grid cells below the base (0 -> 3; 3..1024) */
+  int pad_top;         /* grid cells above the top face (0 -> 4; 3..1024) */
   double gravity[3];   /* m/s^2, applied on the grid; the paper uses none */
   int free_base;       /* 0: base held fixed (Eq. 10); 1: no base condition */
   int block[3];        /* particle-sort block in cells (0 -> library default) */
@@ -127,7 +127,8 @@ typedef struct {
  * stream: a cudaStream_t (NULL = the legacy default stream); the library
  * does not take ownership.  *out receives the handle.
  * Errors: INVALID_ARG (bad sizes/material, extents not multiples of dx_m,
- * padding < 3), OOM, CUDA. */
+ * padding outside 3..1024, more than 2e9 particles or 2^31 - 1 grid nodes),
+ * OOM, CUDA. */
 tacchi_status tacchi_create(const tacchi_elastomer_desc *desc, void *stream,
                             tacchi_handle *out);
 

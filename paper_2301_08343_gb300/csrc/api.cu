@@ -106,8 +106,12 @@ tacchi_status validate_desc(const tacchi_elastomer_desc *d, Geometry *g) {
   g->ps = d->pad_side ? d->pad_side : 4;
   g->pb = d->pad_bottom ? d->pad_bottom : 3;
   g->pt = d->pad_top ? d->pad_top : 4;
-  if (g->ps < 3 || g->pb < 3 || g->pt < 3) return TACCHI_ERR_INVALID_ARG;
+  if (g->ps < 3 || g->pb < 3 || g->pt < 3 || g->ps > 1024 || g->pb > 1024 || g->pt > 1024)
+    return TACCHI_ERR_INVALID_ARG;
   if (8.0 * g->n[0] * g->n[1] * g->n[2] > 2.0e9) return TACCHI_ERR_INVALID_ARG;
+  // the kernels index an instance's grid nodes with 32-bit arithmetic
+  const double nodes = (g->n[0] + 2.0 * g->ps + 1) * (g->n[1] + 2.0 * g->ps + 1) * (g->n[2] + g->pb + g->pt + 1.0);
+  if (nodes > 2147483647.0) return TACCHI_ERR_INVALID_ARG;
   const bool user_block = d->block[0] != 0 || d->block[1] != 0 || d->block[2] != 0;
   if (user_block && !block_supported(SortBlock{d->block[0], d->block[1], d->block[2]}))
     return TACCHI_ERR_INVALID_ARG;

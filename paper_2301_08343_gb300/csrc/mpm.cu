@@ -118,11 +118,13 @@ __global__ void __launch_bounds__(256) k_grid_update(Batch b, int substep, float
   if (n >= b.Nnodes) return;
   const int ii = find_instance(b.node_offs, b.n_inst, n);
   const Instance &I = b.inst[ii];
-  const long long loc = n - I.node_off;
+  // an instance has fewer than 2^31 nodes: 32-bit index arithmetic
+  const unsigned loc = (unsigned)(n - I.node_off);
   const int G0 = I.G[0], G1 = I.G[1], G2 = I.G[2];
-  const int i = (int)(loc % G0);
-  const int j = (int)((loc / G0) % G1);
-  const int k = (int)(loc / ((long long)G0 * G1));
+  const unsigned row = loc / (unsigned)G0;
+  const int i = (int)(loc - row * (unsigned)G0);
+  const int k = (int)(row / (unsigned)G1);
+  const int j = (int)(row - (unsigned)k * (unsigned)G1);
   const float4 mm = b.gmm[n];
   float V0 = 0.f, V1 = 0.f, V2 = 0.f;
   if (mm.x > 0.f) {  // Eq. 6; empty nodes keep V = 0

@@ -83,6 +83,7 @@ def _desc(**kw):
     dict(dx=0.0), dict(dx=-1.0), dict(E=0.0), dict(nu=0.5), dict(nu=-1.0), dict(rho=0.0),
     dict(extent=(6.1e-3, 6e-3, 2e-3)), dict(extent=(0.0, 6e-3, 2e-3)), dict(pad_side=2),
     dict(pad_top=1), dict(block=(3, 3, 3)), dict(extent=(float("nan"), 6e-3, 2e-3)),
+    dict(pad_side=1025), dict(extent=(0.725, 0.725, 0.5e-3), pad_top=1024),  # 2.19e9 grid nodes
 ])
 def test_create_rejects_invalid_descriptions_before_touching_cuda(L, bad):
     d = _desc(**bad)
