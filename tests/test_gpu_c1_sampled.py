@@ -18,7 +18,8 @@ after the closing G2P: positions to 1e-4 cells (FP32 spacing at 300 cells is
 G2P sums, about 2e-7 per substep).  The nodes are those with the largest
 momentum whose whole box is clear of the indenter, the fixed base and the
 padding band, so that no boundary condition acts inside it.  Also checked at every node: the total
-grid mass equals N m."""
+grid mass equals N m; and the 640 x 480 frame of the final state against the
+oracle's height map and shading."""
 import math
 
 import numpy as np
@@ -135,3 +136,24 @@ def test_c1_two_substeps_at_sampled_nodes_and_particles():
     assert dM / sM <= 1e-5, (dM, sM)
     assert du <= 1e-4, du
     assert sF > 1e-3 and dF <= 1e-4 * sF, (dF, sF)
+
+    # the benchmark's frame of that state, 640 x 480 over the top face: the
+    # height map against the oracle's from the same positions (Sec. III-B),
+    # and the image against the oracle's shading of the same height map
+    # (Eqs. 12-14)
+    win = W.top_window(b)
+    Lt = W.default_lights()
+    Hd = torch.empty((480, 640), device="cuda")
+    img = g.render(640, 480, win, rp=T.render_params_from(Lt), out_height=Hd)
+    o = oracle.Sim(b.nx, b.ny, b.nz, dx, b.E, b.nu, b.rho, b.pad_side, b.pad_bottom, b.pad_top)
+    u0, fl = oracle.lattice(b.nx, b.ny, b.nz, b.pad_side, b.pad_bottom, b.seed)
+    o.set_rest(u0)
+    o.set_state(S2["u"].cpu().numpy(), flags=S2["flags"].cpu().numpy())
+    Hg = Hd.cpu().numpy().astype(np.float64)
+    Ho = o.heightmap(win, 640, 480)
+    assert Ho.min() < g.z_top - 0.3e-3  # the press shows
+    assert np.abs(Hg - Ho).max() <= 1e-3 * dx
+    rpo = oracle.render_params(Lt["n_lights"], Lt["dirs"], Lt["diffuse"], Lt["specular"], Lt["ambient"],
+                               Lt["ka"], Lt["kd"], Lt["ks"], Lt["alpha"])
+    Io = oracle.shade(Hg, (win[2] - win[0]) / 640, (win[3] - win[1]) / 480, g.z_top, rpo)
+    assert np.abs(img.cpu().numpy() - Io).max() <= 2e-5
