@@ -533,7 +533,7 @@ def run_smoothed_bench(args):
     sg = sigmas[best]
     for _ in range(max(args.warmup, 3)):
         bt.render_smoothed(0, w, h, win, sg, out=out, out_height=Hf)
-    K = max(args.steps, 1) * 100
+    K = max(args.steps, 1) * 2000  # about a second at 0.05 ms a frame: the clock sampler needs that
     clocks = ClockSampler(0)
     clocks.start()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
