@@ -777,11 +777,14 @@ tacchi_status nn_sync(tacchi_nn *n) {
     if (e_ != cudaSuccess) return st_of(e_);   \
   } while (0)
 
-// Ring depth per tile width: about 80-100 KB of shared memory, so that two
-// CTAs share an SM and their tensor-memory columns fit its 512.
+// Ring depth per tile width.  A tile is a few small loads re-read from L2
+// (nine taps of 8 KB for C_in = 32), so the layer is bound by the loads in
+// flight per SM: a shallow ring lets more CTAs share an SM (N <= 64: 31-38 KB
+// of shared memory, five to seven CTAs; N = 128: four), as long as their
+// tensor-memory columns fit its 512 (N >= 192: two CTAs of 256 columns).
 template <int N>
 constexpr int conv_stages() {
-  return N <= 64 ? 8 : (N <= 128 ? 6 : 4);
+  return N <= 64 ? 3 : (N == 128 ? 3 : 4);
 }
 template <int N>
 constexpr int conv_tcols() {
@@ -862,7 +865,7 @@ cudaError_t conv_fwd(const bf16 *X, const bf16 *Wk, const float *bias, bf16 *Y, 
 template <int NC>
 cudaError_t wgrad_launch(const CUtensorMap &tmX, const CUtensorMap &tmG, float *dW, int P, int H, int W, int Cin,
                          int Cout, int *err, cudaStream_t s) {
-  constexpr int S = NC <= 64 ? 4 : (NC <= 128 ? 3 : 2);
+  constexpr int S = 2;  // a shallow ring: more CTAs per SM hide the load latency better
   constexpr int TC = NC <= 32 ? 32 : (NC <= 64 ? 64 : (NC <= 128 ? 128 : 256));
   constexpr int SMEM = S * (4 + NC / 32) * 4096 + 1024;
   static bool ready = false;
