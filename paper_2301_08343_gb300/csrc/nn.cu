@@ -25,8 +25,8 @@
 //                  rows = (tap, C_in), columns = C_out, K = pixels, both
 //                  operands MN-major from TMA boxes, split over pixel chunks
 //                  whose partial sums meet in dW through float4 reductions.
-//   elementwise kernels for ReLU masks, pooling, upsampling, concatenation,
-//   bias gradients, the 1x1 head, the loss and Adam.
+//   elementwise kernels for pooling, upsampling, concatenation, the ReLU
+//   mask fused with the bias gradients, the 1x1 head, the loss and Adam.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -440,18 +440,6 @@ __global__ void k_pack_input(const float *x, bf16 *y, unsigned P, int cin, int c
     reinterpret_cast<uint4 *>(y)[e] = pack8(f);
   }
 }
-// g = g * (y > 0), n8 = elements / 8
-__global__ void k_relu_mask(bf16 *g, const bf16 *y, unsigned n8) {
-  GRID_STRIDE_U(e, n8) {
-    float gv[8], yv[8];
-    unpack8(reinterpret_cast<const uint4 *>(g)[e], gv);
-    unpack8(reinterpret_cast<const uint4 *>(y)[e], yv);
-#pragma unroll
-    for (int k = 0; k < 8; ++k)
-      if (!(yv[k] > 0.f)) gv[k] = 0.f;
-    reinterpret_cast<uint4 *>(g)[e] = pack8(gv);
-  }
-}
 // y[n][H/2][W/2][C] = mean of the 2 x 2 block
 __global__ void k_avgpool(const bf16 *x, bf16 *y, int nimg, int H, int W, int C) {
   const unsigned Ho = H / 2, Wo = W / 2, cc = C / 8;
@@ -518,7 +506,9 @@ __global__ void k_upsample_concat_bwd(const bf16 *g, bf16 *ga, bf16 *gs, int nim
   }
 }
 // db[c] += sum over pixels of g[p][c]
-__global__ void k_bias_grad(const bf16 *g, float *db, long long P, int C) {
+// With y given, the ReLU mask is applied on the way: g[p][c] = 0 where
+// y[p][c] <= 0, written back, and the sums taken of the masked gradient.
+__global__ void k_bias_grad(bf16 *g, const bf16 *y, float *db, long long P, int C) {
   // a thread reads one 8-channel chunk (16 bytes) per pixel; the grid's
   // thread count is a multiple of the C / 8 chunks, so it always sums the
   // same chunk, in registers, then per block in shared memory
@@ -531,6 +521,14 @@ __global__ void k_bias_grad(const bf16 *g, float *db, long long P, int C) {
   GRID_STRIDE(e, P * nch) {
     float v[8];
     unpack8(reinterpret_cast<const uint4 *>(g)[e], v);
+    if (y) {
+      float yv[8];
+      unpack8(reinterpret_cast<const uint4 *>(y)[e], yv);
+#pragma unroll
+      for (int k = 0; k < 8; ++k)
+        if (!(yv[k] > 0.f)) v[k] = 0.f;
+      reinterpret_cast<uint4 *>(g)[e] = pack8(v);
+    }
 #pragma unroll
     for (int k = 0; k < 8; ++k) acc[k] += v[k];
   }
@@ -922,11 +920,12 @@ cudaError_t conv_wgrad(const bf16 *X, const bf16 *G, float *dW, int nimg, int H,
   return wgrad_launch<32>(tmX, tmG, dW, P, H, W, Cin, Cout, err, s);
 }
 
-cudaError_t bias_grad(const bf16 *G, float *db, long long P, int C, cudaStream_t s) {
+// db += sum over pixels of G; with Y, G is first masked by ReLU'(Y) in place
+cudaError_t mask_bias_grad(bf16 *G, const bf16 *Y, float *db, long long P, int C, cudaStream_t s) {
   const int nch = C / 8;
   if (C % 8 || nch < 1 || nch > 1024) return cudaErrorInvalidValue;
   const int threads = nch * (256 / nch > 0 ? 256 / nch : 1);  // a multiple of the chunks
-  k_bias_grad<<<512, threads, C * sizeof(float), s>>>(G, db, P, C);
+  k_bias_grad<<<512, threads, C * sizeof(float), s>>>(G, Y, db, P, C);
   return cudaGetLastError();
 }
 
@@ -1033,12 +1032,11 @@ tacchi_status backward(tacchi_nn *n, int batch, const float *target) {
     for (int q = 0; q < 2; ++q, --k) {
       ConvLayer &cl = n->convs[k];
       const long long P = (long long)batch * H * W;
-      k_relu_mask<<<grid_for(P * cl.cout / 8), 256, 0, s>>>(gcur, n->act[k + 1], (unsigned)(P * cl.cout / 8));
-      NCK(cudaGetLastError());
+      // ReLU mask and bias gradient in one pass over the output gradient
+      NCK(mask_bias_grad(gcur, n->act[k + 1], n->g + cl.b_off, P, cl.cout, s));
       const bf16 *xin = q == 0 ? n->act[k] : n->cat[l];
       bf16 *gin = q == 0 ? n->gact[k] : n->gcat[l];
       NCK(conv_wgrad(xin, gcur, n->g + cl.w_off, batch, H, W, cl.cin, cl.cout, n->err, s));
-      NCK(bias_grad(gcur, n->g + cl.b_off, P, cl.cout, s));
       NCK(conv_fwd(gcur, cl.wd, nullptr, gin, batch, H, W, cl.cout, cl.cin, 0, n->err, s));
       gcur = gin;
     }
@@ -1072,13 +1070,11 @@ tacchi_status backward(tacchi_nn *n, int batch, const float *target) {
     for (int q = 0; q < 2; ++q, --k) {
       ConvLayer &cl = n->convs[k];
       const long long P = (long long)batch * H * W;
-      k_relu_mask<<<grid_for(P * cl.cout / 8), 256, 0, s>>>(gcur, n->act[k + 1], (unsigned)(P * cl.cout / 8));
-      NCK(cudaGetLastError());
+      NCK(mask_bias_grad(gcur, n->act[k + 1], n->g + cl.b_off, P, cl.cout, s));
       const bf16 *xin = (q == 1 && l > 0) ? n->pooled[l - 1] : n->act[k];
       float *dW = (k == 0) ? n->convs[0].dwpad : n->g + cl.w_off;
       if (k == 0) NCK(cudaMemsetAsync(dW, 0, sizeof(float) * cl.wpad_elems, s));
       NCK(conv_wgrad(xin, gcur, dW, batch, H, W, cl.cin, cl.cout, n->err, s));
-      NCK(bias_grad(gcur, n->g + cl.b_off, P, cl.cout, s));
       if (k == 0) {
         k_unpad_wgrad<<<grid_for(9LL * cl.cin_real * cl.cout), 256, 0, s>>>(dW, n->g + cl.w_off, cl.cin_real, cl.cin,
                                                                             cl.cout);
