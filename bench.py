@@ -139,7 +139,12 @@ def whole_job_rate(units, seconds):
 def indenter_for_step(block, s, substeps, dt):
     """Indenter s (cycled over the nine shapes and four depths): its tip
     starts at the rest top face over the block centre and moves straight
-    down to the step's depth over the step's substeps."""
+    down to the step's depth over the step's substeps.  The small 12 x 12 x 3
+    mm block keeps its own press: the 3 mm sphere, 1 mm deep."""
+    if block is W.C0:
+        z_top = block.nz * block.dx
+        pose = (block.nx * block.dx / 2, block.ny * block.dx / 2, z_top + W.C0_SPHERE_R, 1.0, 0.0, 0.0, 0.0)
+        return "sphere", (W.C0_SPHERE_R,), None, pose, (0.0, 0.0, -1.0e-3 / (substeps * dt), 0.0, 0.0, 0.0), 1.0e-3
     ind = W.c1_indenters()
     name, params, hm, tip = ind[s % len(ind)]
     depth = W.C1_DEPTHS[s % len(W.C1_DEPTHS)]
@@ -268,7 +273,8 @@ def run_ours(args, rank, world, local_rank):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": f"{args.workload}: {block.nx}x{block.ny}x{block.nz} cells dx={block.dx*1e3:g} mm, "
                                f"{sim.N} particles, {substeps} substeps dt={dt:g} s + {w}x{h} frame per step, "
-                               "nine procedural indenters cycled, depths 0.2-1.5 mm",
+                               + ("3 mm sphere pressed 1 mm" if block is W.C0 else
+                                  "nine procedural indenters cycled, depths 0.2-1.5 mm"),
                    "particles": sim.N, "grid_nodes": sim.n_nodes, "substeps_per_step": substeps,
                    "image": [w, h], "sort_block": list(sim.block), "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (particle state %.2f GB)" % (sim.N * 96 / 1e9)},
