@@ -13,6 +13,14 @@ the particle state (2.7 GB) is far larger than L2.
 
 --impl reference times the FP64 CPU oracle on the host cores on bounded
 samples of the same workload (the paper's method has no GPU reference code).
+
+Other lines (--workload): c0 (the 12 x 12 x 3 mm block, 3 mm sphere),
+c1-quarter (a quarter of the default, for profiling), c2 (256 uneven sensors
+stepped in one graph), surrogate (training data, training and inference of the
+learned surrogate, with its error against the MPM), serving (a Poisson query
+stream served by the surrogate with MPM fallback), smoothed (the Gaussian
+depth-smoothing renderer the paper compares against, with its height error
+against the MPM surface).
 """
 from __future__ import annotations
 
