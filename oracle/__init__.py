@@ -93,6 +93,7 @@ def lib():
             L.ora_p2g.argtypes = [C.c_void_p, C.c_double, dp, dp]
             L.ora_substep.argtypes = [C.c_void_p, C.c_double]
             L.ora_run.argtypes = [C.c_void_p, C.c_int, C.c_double]
+            L.ora_g2p.argtypes = [C.c_void_p, dp, C.c_double]
             L.ora_last_grid.argtypes = [C.c_void_p, dp, dp]
             L.ora_last_grid_velocity.argtypes = [C.c_void_p, dp]
             L.ora_weights.argtypes = [dp, ip, dp]
@@ -275,6 +276,11 @@ class Sim:
 
     def run(self, n, dt) -> int:
         return int(self._L.ora_run(self._h, n, dt))
+
+    def g2p(self, V, dt) -> int:
+        """Eqs. 7-11 alone from the grid velocity V ([3][nodes], m/s)."""
+        V = np.ascontiguousarray(V, np.float64).reshape(3, self.nodes)
+        return int(self._L.ora_g2p(self._h, _p(V, C.c_double), dt))
 
     def last_grid(self):
         m = np.zeros(self.nodes)

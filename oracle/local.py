@@ -1,16 +1,25 @@
-"""Two substeps of the method in FP64 over the particles of one box, from
-the oracle's per-particle routines (B-spline weights, polar decomposition and
-stress): P2G (Eqs. 2-5), grid velocity (Eq. 6), G2P, F update and advection
-(Eqs. 7-11).  Used by the full-size sampled parity test; pinned against the
-oracle's own whole-grid substeps in tests/test_sampled_mpm_cpu.py."""
+"""Substeps of the method in FP64 over the particles of one box of grid
+nodes, from the oracle's per-particle routines (B-spline weights, polar
+decomposition and stress): P2G (Eqs. 2-5), grid velocity (Eq. 6), G2P, the
+F update and advection (Eqs. 7-11).
+
+TEST INFRASTRUCTURE ONLY, like the rest of ``oracle/``: the full-size sampled
+parity tests recompute two substeps around sampled grid nodes with it, where
+the whole-grid oracle would take hours.  Pinned against the oracle's own
+whole-grid substeps (tests/test_sampled_mpm_cpu.py) and against an affine
+grid velocity field, which Eqs. 7-9 reproduce exactly
+(tests/test_oracle_pins.py)."""
 import numpy as np
+
+from . import stress as _stress
+from . import weights as _weights
 
 
 class Local:
-    """Two substeps of the method in FP64 over the particles of one box."""
+    """Substeps of the method in FP64 over the particles of one box."""
 
-    def __init__(self, oracle, dx, dt, E, nu, rho):
-        self.o, self.dx, self.dt = oracle, dx, dt
+    def __init__(self, dx, dt, E, nu, rho):
+        self.dx, self.dt = dx, dt
         self.mu = E / (2 * (1 + nu))
         self.la = E * nu / ((1 + nu) * (1 - 2 * nu))
         self.V0 = dx ** 3 / 8
@@ -20,14 +29,14 @@ class Local:
         base = np.zeros((len(u), 3), np.int64)
         w = np.zeros((len(u), 3, 3, 3))
         for p in range(len(u)):
-            b, wp = self.o.weights(u[p])
+            b, wp = _weights(u[p])
             base[p], w[p] = b, wp
         return base, w  # w[p][k][j][i]
 
     def p2g(self, u, v, C, F, lo, shape):
         """(M, MG) on nodes lo + [0, shape) from every given particle."""
         base, w = self.weights(u)
-        tau = np.stack([self.o.stress(F[p], self.mu, self.la) for p in range(len(u))])
+        tau = np.stack([_stress(F[p], self.mu, self.la) for p in range(len(u))])
         A = self.m * C - self.dt * self.V0 * 4.0 / self.dx ** 2 * tau
         M = np.zeros(shape)
         MG = np.zeros(shape + (3,))

@@ -706,6 +706,15 @@ int ora_run(ora_sim *s, int n, double dt) {
   return err;
 }
 
+/* Grid-to-particle step alone (Eqs. 7-11) from a given grid velocity V
+ * ([3][nodes], x fastest): the same g2p() that ends ora_substep, without
+ * P2G, grid update or the pose advance.  For tests that prescribe V. */
+int ora_g2p(ora_sim *s, const double *V, double dt) {
+  for (long long n = 0; n < s->nodes; ++n)
+    for (int a = 0; a < 3; ++a) s->gv[3 * n + a] = V[a * s->nodes + n];
+  return g2p(s, dt);
+}
+
 void ora_last_grid(const ora_sim *s, double *mass, double *mom) {
   memcpy(mass, s->gm, sizeof(double) * s->nodes);
   memcpy(mom, s->gp, sizeof(double) * 3 * s->nodes);

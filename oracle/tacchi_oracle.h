@@ -87,6 +87,8 @@ int ora_node_inside(const ora_sim *s, int i, int j, int k);
 void ora_p2g(ora_sim *s, double dt, double *mass, double *mom);
 int ora_substep(ora_sim *s, double dt);
 int ora_run(ora_sim *s, int n, double dt);
+/* Eqs. 7-11 alone from the grid velocity V [3][nodes]; returns error bits. */
+int ora_g2p(ora_sim *s, const double *V, double dt);
 void ora_last_grid(const ora_sim *s, double *mass, double *mom);
 void ora_last_grid_velocity(const ora_sim *s, double *V);
 

@@ -26,7 +26,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from sampled_mpm import Local, velocity
+from oracle.local import Local, velocity
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -86,7 +86,7 @@ def test_c1_two_substeps_at_sampled_nodes_and_particles():
 
     u = S["u"]
     base = torch.floor(u - 0.5).to(torch.int32)
-    L = Local(oracle, dx, dt, b.E, b.nu, b.rho)
+    L = Local(dx, dt, b.E, b.nu, b.rho)
     gM = grid[:, 0].reshape(G2, G1, G0)
     gMG = grid[:, 1:].reshape(G2, G1, G0, 3)
     dM, dMG, sM, sMG, du, dF, sF, nck = 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0

@@ -6,7 +6,7 @@ routines can compute one by one.
 Every sensor is pressed for 200 substeps; the state of a few sensors is read
 back, two more substeps run on the GPU for the whole batch, and around a
 sampled node of each of those sensors the two substeps are recomputed in FP64
-from the read-back state (tests/sampled_mpm.py: P2G, grid velocity, G2P,
+from the read-back state (oracle/local.py: P2G, grid velocity, G2P,
 F update and advection, twice).  Compared: position and F of every particle
 whose stencil the box covers, after the closing G2P (1e-4 cells; F - I to 1e-4
 of its largest entry).  The sensors are the thick ones (12 cells or more)
@@ -19,7 +19,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from sampled_mpm import Local, velocity
+from oracle.local import Local, velocity
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -56,7 +56,7 @@ def test_c2_two_substeps_at_sampled_particles():
     for i in picks:
         b, ind = specs[i]
         dx = b.dx
-        L = Local(oracle, dx, dt, b.E, b.nu, b.rho)
+        L = Local(dx, dt, b.E, b.nu, b.rho)
         org = np.array([-b.pad_side * dx, -b.pad_side * dx, -b.pad_bottom * dx])
         cc = (np.array(poses[i][:3]) - org) / dx             # sphere centre (cells)
         R = ind["params"][0] / dx

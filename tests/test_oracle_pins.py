@@ -240,6 +240,94 @@ def test_rotated_configuration_is_stress_free():
     assert np.abs(MG).max() <= 1e-5 * np.abs(MGs).max()  # FP32 rounding of R0 only
 
 
+# ------------------------------------------------------------------- G2P --
+def _affine_field(s, v0, G, Xref):
+    """Grid velocity V(X) = v0 + G (X - Xref) on every node, [3][nodes]."""
+    X = s.node_positions()
+    return v0[:, None] + G @ (X - Xref[:, None])
+
+
+def _affine_case(fix_base):
+    s, u0, fl = small_sim(4, 4, 3, dx=1e-3, fix_base=fix_base, pad=5)
+    rng = np.random.default_rng(21)
+    G = rng.uniform(-150.0, 150.0, (3, 3))        # 1/s, not symmetric
+    v0 = np.array([0.03, -0.02, 0.015])            # m/s
+    Xref = s.origin + 0.5 * np.array(s.G) * s.dx
+    Fm = (0.15 * rng.standard_normal((9, s.N))).astype(np.float32)  # F0 - I, order matters
+    s.set_state(u0, None, None, Fm, fl)
+    x0 = s.origin[:, None] + u0.astype(np.float64) * s.dx
+    F0 = Fm.T.astype(np.float64).reshape(-1, 3, 3) + np.eye(3)
+    return s, u0, fl, G, v0, Xref, x0, F0
+
+
+def test_g2p_reproduces_an_affine_grid_velocity_exactly():
+    """Eqs. 7-8 with quadratic B-splines reproduce an affine field exactly:
+    v_p = V(x_p) (partition of unity and linear reproduction) and
+    C_p = (4/dX^2) sum_i w V_i (X_i - x_p)^T = G, because sum_i w (X_i - x_p)
+    (X_i - x_p)^T = dX^2 / 4 I.  Eq. 9 then gives F = (I + dt G) F0, in
+    that order (G is not symmetric and F0 is a random matrix, so
+    F0 (I + dt G) or F0 + dt G differ by far more than the tolerance), and
+    Eq. 11 moves x by dt v."""
+    s, u0, fl, G, v0, Xref, x0, F0 = _affine_case(False)
+    dt = 1e-5
+    assert s.g2p(_affine_field(s, v0, G, Xref), dt) == 0
+    xi, v, Cm, F = s.state()
+    v_exp = v0[:, None] + G @ (x0 - Xref[:, None])
+    assert np.abs(v - v_exp).max() <= 1e-13 * np.abs(v_exp).max()
+    Cp = Cm.T.reshape(-1, 3, 3)
+    assert np.abs(Cp - G[None]).max() <= 1e-11 * np.abs(G).max()
+    Fp = F.T.reshape(-1, 3, 3)
+    F_exp = np.einsum("ab,pbc->pac", np.eye(3) + dt * G, F0)
+    err = np.abs(Fp - F_exp).max()
+    assert err <= 1e-13
+    wrong_order = np.einsum("pab,bc->pac", F0, np.eye(3) + dt * G)
+    assert np.abs(wrong_order - F_exp).max() > 1e6 * max(err, 1e-16)
+    assert np.abs((F0 + dt * G[None]) - F_exp).max() > 1e6 * max(err, 1e-16)
+    x1 = s.origin[:, None] + xi * s.dx
+    assert np.abs(x1 - (x0 + dt * v_exp)).max() <= 1e-15
+
+
+def test_g2p_base_particles_stop_but_still_deform():
+    """Eq. 10: particles of the base set B (flag bit 0) take v = 0 and stay
+    put, while C and F follow Eqs. 8-9 like every other particle; particles
+    outside B move with the field."""
+    s, u0, fl, G, v0, Xref, x0, F0 = _affine_case(True)
+    dt = 1e-5
+    assert s.g2p(_affine_field(s, v0, G, Xref), dt) == 0
+    xi, v, Cm, F = s.state()
+    base = (fl & 1) > 0
+    assert 0 < base.sum() < s.N
+    assert np.all(v[:, base] == 0.0)
+    assert np.all(xi[:, base] == u0[:, base].astype(np.float64))
+    v_exp = v0[:, None] + G @ (x0 - Xref[:, None])
+    assert np.abs(v[:, ~base] - v_exp[:, ~base]).max() <= 1e-13 * np.abs(v_exp).max()
+    Cp = Cm.T.reshape(-1, 3, 3)
+    assert np.abs(Cp[base] - G[None]).max() <= 1e-11 * np.abs(G).max()
+    F_exp = np.einsum("ab,pbc->pac", np.eye(3) + dt * G, F0)
+    assert np.abs(F.T.reshape(-1, 3, 3)[base] - F_exp[base]).max() <= 1e-13
+
+
+def test_box_local_g2p_reproduces_an_affine_grid_velocity_exactly():
+    """The box-local substep of oracle/local.py (the judge of the full-size
+    sampled parity tests) meets the same affine-field identities."""
+    from oracle.local import Local
+    s, u0, fl, G, v0, Xref, x0, F0 = _affine_case(True)
+    dt = 1e-5
+    Vn = _affine_field(s, v0, G, Xref)                   # [3][nodes]
+    gx, gy, gz = s.G
+    V = Vn.T.reshape(gz, gy, gx, 3)                      # [z][y][x][3]
+    L = Local(s.dx, dt, 3.0e5, 0.45, 1000.0)
+    fixed = (fl & 1) > 0
+    u1, v1, C1, F1 = L.g2p(u0.T.astype(np.float64), F0, fixed, V, np.zeros(3, int))
+    v_exp = (v0[:, None] + G @ (x0 - Xref[:, None])).T
+    v_exp[fixed] = 0.0
+    assert np.abs(v1 - v_exp).max() <= 1e-13 * np.abs(v_exp).max()
+    assert np.abs(C1 - G[None]).max() <= 1e-11 * np.abs(G).max()
+    F_exp = np.einsum("ab,pbc->pac", np.eye(3) + dt * G, F0)
+    assert np.abs(F1 - F_exp).max() <= 1e-13
+    assert np.abs(u1 - (u0.T + dt / s.dx * v_exp)).max() <= 1e-12
+
+
 # -------------------------------------------------------------- grid update --
 def test_grid_update_eq6_and_boundaries():
     s, u0, fl = small_sim(4, 4, 3, dx=1e-3, fix_base=True, pad=4)

@@ -6,7 +6,7 @@ node and the state of the particles whose stencils the box covers."""
 import numpy as np
 
 import oracle
-from sampled_mpm import Local, velocity
+from oracle.local import Local, velocity
 
 
 def test_box_local_substeps_equal_the_oracle():
@@ -25,7 +25,7 @@ def test_box_local_substeps_equal_the_oracle():
     Mo, MGo = o.last_grid()
     xi, _, _, Fo = o.state()
     G0, G1, _ = o.G
-    L = Local(oracle, dx, dt, E, nu, rho)
+    L = Local(dx, dt, E, nu, rho)
     c = np.array([13, 13, 12])
     lo, hi = c - 6, c + 6
     up = u0.T.astype(np.float64)
