@@ -53,8 +53,6 @@ BYTES_PER_NODE = 32
 # the kernel source with three Newton polar iterations: G2P 641, stress 420,
 # P2G 385.
 FLOPS_PER_PARTICLE = 1446
-# FP32 ALU peak: 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz.
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 WORKLOADS = {
     # name: (block, dt, substeps per step, image)
@@ -62,6 +60,21 @@ WORKLOADS = {
     "c1-quarter": (W.Block(160, 120, 40, 0.1e-3, pad_side=10, pad_top=20), W.C1_DT, 200, (320, 240)),
     "c0": (W.C0, W.C0_DT, 500, W.C0_IMAGE),
 }
+
+
+def fp32_peak():
+    """FP32 ALU roof measured on this GPU by the library's FMA
+    microbenchmark, with the SM count and clock the driver reports and the
+    nominal figure they give (128 FP32 lanes per SM, 2 flop per FMA)."""
+    import ctypes as C
+    import paper_2301_08343_gb300 as T
+    t, n, k = C.c_double(), C.c_int(), C.c_int()
+    T._lib.check(T.lib().tacchi_measure_fp32_peak(C.byref(t), C.byref(n), C.byref(k)), "tacchi_measure_fp32_peak")
+    nominal = n.value * 128 * 2 * k.value * 1e3 / 1e12 if k.value > 0 else None
+    return {"tflops": t.value, "sm_count": n.value, "sm_clock_khz": k.value,
+            "nominal_tflops": nominal,
+            "source": f"measured: FMA chains over every SM ({n.value} SMs, "
+                      f"driver max SM clock {k.value / 1e3:g} MHz)"}
 
 
 def measured_peaks():
@@ -144,6 +157,28 @@ def whole_job_rate(units, seconds):
     return units / seconds
 
 
+def shard_sensors(sizes, world):
+    """Sensor indices per rank and particle loads: greedy bin packing,
+    longest first, so that ranks differ by at most one sensor's particles."""
+    from paper_2301_08343_gb300.sharding import bin_pack
+    return bin_pack(sizes, world)
+
+
+def relaunch_under_torchrun(n):
+    """`bench.py --gpus N` started without ranks: run it again as N ranks on
+    this node (torch.distributed.run on 127.0.0.1), with NCCL's log on so
+    that every rank reports its communicator.  Returns the exit status."""
+    import socket
+    with socket.socket() as so:
+        so.bind(("127.0.0.1", 0))
+        port = so.getsockname()[1]
+    env = dict(os.environ)
+    env.setdefault("NCCL_DEBUG", "INFO")
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={n}",
+           "--master-addr", "127.0.0.1", f"--master-port={port}", os.path.abspath(__file__)] + sys.argv[1:]
+    return subprocess.call(cmd, env=env)
+
+
 def indenter_for_step(block, s, substeps, dt):
     """Indenter s (cycled over the nine shapes and four depths): its tip
     starts at the rest top face over the block centre and moves straight
@@ -180,6 +215,9 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
     sim = T.Tacchi(block.extent_m, block.dx, block.E, block.nu, block.rho, seed=block.seed + rank,
                    pad_side=block.pad_side, pad_bottom=block.pad_bottom, pad_top=block.pad_top)
+    if args.plan:
+        shape, tpc = args.plan.split("/")
+        sim.set_transfer(tuple(int(x) for x in shape.split("x")), int(tpc))
     rest = sim.get_state()
     assert rest["status"] == 0
     rest_u = rest["u"].clone()
@@ -251,6 +289,7 @@ def run_ours(args, rank, world, local_rank):
     e2e_value = whole_job_rate(units_all * e_steps, e2e_s)
 
     peaks, src = measured_peaks()
+    fp32 = fp32_peak()
     fused_avg_ms = prof["fused_ms"] / max(prof["fused_launches"], 1)
     bytes_fused = BYTES_PER_PARTICLE * sim.N + BYTES_PER_NODE * sim.n_nodes
     flops_fused = FLOPS_PER_PARTICLE * sim.N
@@ -260,9 +299,9 @@ def run_ours(args, rank, world, local_rank):
     roof = {
         "kernel": "k_transfer (fused G2P+P2G)",
         "bound": "alu",
-        "achieved": round(tfl, 3), "peak": round(FP32_PEAK_TFLOPS, 1), "unit": "TFLOP/s",
-        "frac": round(tfl / FP32_PEAK_TFLOPS, 4),
-        "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+        "achieved": round(tfl, 3), "peak": round(fp32["tflops"], 2), "unit": "TFLOP/s",
+        "frac": round(tfl / fp32["tflops"], 4),
+        "peak_source": fp32["source"], "peak_nominal": fp32["nominal_tflops"],
         "traffic": traffic,
         "hbm": {"achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": round(gbs / peaks["hbm_gbs"], 4), "peak_source": f"{src} (MEASURED_PEAKS hbm_gbs)"},
@@ -284,7 +323,7 @@ def run_ours(args, rank, world, local_rank):
                                + ("3 mm sphere pressed 1 mm" if block is W.C0 else
                                   "nine procedural indenters cycled, depths 0.2-1.5 mm"),
                    "particles": sim.N, "grid_nodes": sim.n_nodes, "substeps_per_step": substeps,
-                   "image": [w, h], "sort_block": list(sim.block), "parallelism": f"replicas x{world}",
+                   "image": [w, h], "sort_block": list(sim.block), "threads_per_cell": sim.threads_per_cell, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (particle state %.2f GB)" % (sim.N * 96 / 1e9)},
         "roofline": roof,
         "kernel_share_of_step": share,
@@ -306,7 +345,11 @@ def run_batch_bench(args, rank, world, local_rank):
     torch.cuda.set_device(local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
-    specs = W.c2_instances(args.instances, seed_base=1000 + 100000 * rank)
+    # one set of sensors for the whole job, split over the ranks by particle
+    # count (longest first); each rank steps only its own sensors
+    all_specs = W.c2_instances(args.instances, seed_base=1000)
+    owners, loads = shard_sensors([b.n_particles for b, _ in all_specs], world)
+    specs = [all_specs[i] for i in owners[rank]]
     substeps = args.substeps or 200
     dt = W.C2_DT
     bt = T.TacchiBatch([b for b, _ in specs])
@@ -369,30 +412,34 @@ def run_batch_bench(args, rank, world, local_rank):
     (ms, e2e_s), units_all = reduce_over_ranks([ms, e2e_s], bt.N_total * substeps, world, dev)
     value = whole_job_rate(units_all * args.steps, ms * 1e-3)
     e2e_value = whole_job_rate(units_all * e_steps, e2e_s)
-    sizes = [b.n_particles for b, _ in specs]
+    sizes = [b.n_particles for b, _ in all_specs]
     fused_avg = prof["fused_ms"] / max(prof["fused_launches"], 1)
     peaks, src = measured_peaks()
     nodes = sum((b.nx + 2 * b.pad_side + 1) * (b.ny + 2 * b.pad_side + 1) * (b.nz + b.pad_bottom + b.pad_top + 1)
                 for b, _ in specs)
     tfl = FLOPS_PER_PARTICLE * bt.N_total / (fused_avg * 1e-3) / 1e12
+    fp32 = fp32_peak()
     gbs = (BYTES_PER_PARTICLE * bt.N_total + BYTES_PER_NODE * nodes) / (fused_avg * 1e-3) / 1e9
     return {
         "metric": METRIC + " (batched sensors)", "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": f"c2: {len(specs)} sensors, sides U[8,16] mm x thickness U[2,4] mm, "
+        "config": {"workload": f"c2: {len(all_specs)} sensors, sides U[8,16] mm x thickness U[2,4] mm, "
                                f"dx=0.25 mm, {bt.N_total} particles ({min(sizes)}-{max(sizes)} each), "
                                f"{substeps} substeps dt={dt:g} s + 64x64 map per sensor per step",
-                   "instances": len(specs), "particles": bt.N_total,
+                   "instances": len(all_specs), "instances_rank0": len(specs), "particles": bt.N_total,
                    "particles_all_ranks": int(units_all // substeps), "autotune": tuned,
-                   "parallelism": f"replicas x{world}", "l2": "inputs larger than L2"},
+                   "rank_particle_loads": loads,
+                   "parallelism": f"sensors split over {world} rank(s) by particle count (longest first), "
+                                  "no collective in the step",
+                   "l2": "inputs larger than L2"},
         "kernel_share_of_step": {k: round(prof[k + "_ms"] / max(ms, 1e-9), 4)
                                  for k in ("grid", "fused", "edge", "sort")},
         "fused_avg_launch_ms": fused_avg,
         "roofline": {"kernel": "k_transfer (fused G2P+P2G)", "bound": "alu", "achieved": round(tfl, 3),
-                     "peak": round(FP32_PEAK_TFLOPS, 1), "unit": "TFLOP/s", "frac": round(tfl / FP32_PEAK_TFLOPS, 4),
-                     "peak_source": "152 SMs x 128 FP32 lanes x 2 x 2.07 GHz", "traffic": None,
+                     "peak": round(fp32["tflops"], 2), "unit": "TFLOP/s", "frac": round(tfl / fp32["tflops"], 4),
+                     "peak_source": fp32["source"], "peak_nominal": fp32["nominal_tflops"], "traffic": None,
                      "hbm": {"achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
                              "frac": round(gbs / peaks["hbm_gbs"], 4),
                              "peak_source": f"{src} (MEASURED_PEAKS hbm_gbs)"},
@@ -462,15 +509,20 @@ def run_surrogate_bench(args):
         "train_samples_per_s": 256 * args.train_steps / (train_ms * 1e-3),
         "loss_log": log,
         "roofline": {"kernel": "training step (3x3 conv fwd/dgrad/wgrad dominate)", "bound": "tensor",
-                     "achieved": round(tflops, 2), "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
-                     "frac": round(tflops / peaks["bf16_tflops"], 4),
-                     "peak_source": f"{src} (MEASURED_PEAKS bf16_tflops)", "traffic": None},
+                     "achieved": round(tflops, 2), "peak": peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]),
+                     "unit": "TFLOP/s",
+                     "frac": round(tflops / peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"]), 4),
+                     "peak_source": f"{src} (MEASURED_PEAKS bf16_tflops_sustained: a training run lasts "
+                                    f"seconds, under the power cap)", "traffic": None},
     }
 
 
-def run_serving_bench(args):
+def run_serving_bench(args, rank=0, world=1, local_rank=0):
     """Poisson press-query stream served by surrogate + MPM fallback, against
-    the same stream served by the batched MPM alone."""
+    the same stream served by the batched MPM alone.  With several ranks each
+    GPU runs its own server (network lane and MPM lane) on every world-th
+    query of the stream; frames/s = all answered queries / the slowest
+    rank's makespan."""
     import paper_2301_08343_gb300 as T
     from paper_2301_08343_gb300 import serving as SV
     from paper_2301_08343_gb300 import surrogate as SG
@@ -480,7 +532,9 @@ def run_serving_bench(args):
     net = T.SurrogateNet((32, 64, 128, 256), 2, 3, size=W.C3_SIZE, max_batch=1024, seed=0)
     SG.train(net, X, Y, steps=args.train_steps, batch=256, lr=2e-3)
     del X, Y
-    q = W.c4_queries(rate_hz=4096.0, duration_s=args.stream_s, seed=4)
+    from paper_2301_08343_gb300.sharding import round_robin
+    q_all = W.c4_queries(rate_hz=4096.0, duration_s=args.stream_s, seed=4)
+    q = [q_all[i] for i in round_robin(len(q_all), world, rank)]
     srv = SV.PressServer(net, W.C3_BLOCK, W.C3_SUBSTEPS, W.C3_DT, size=W.C3_SIZE)
     srv.serve(q[:64])  # warm-up: pooled MPM handles and their step graphs
     mixed = srv.serve(q)
@@ -488,9 +542,19 @@ def run_serving_bench(args):
                           mpm_batch=1024)
     base.serve(q[:64])
     plain = base.serve(q)
+    if world > 1:
+        import torch
+        dev = torch.device("cuda", local_rank)
+        for res in (mixed, plain):
+            (mk, p99), n_all = reduce_over_ranks([res["makespan_s"], res["latency_p99_ms"] or 0.0],
+                                                 res["queries"], world, dev)
+            res["rank0"] = {"queries": res["queries"], "makespan_s": res["makespan_s"],
+                            "frames_per_s": res["frames_per_s"]}
+            res.update(queries=int(n_all), makespan_s=mk, frames_per_s=n_all / mk if mk > 0 else 0.0,
+                       latency_p99_ms_max_over_ranks=p99)
     return {
         "metric": "served press frames/s (surrogate + MPM fallback) vs plain batched MPM", "value":
-        mixed["frames_per_s"], "unit": "frames/s", "n_gpus": 1, "steps": 1, "warmup": 0,
+        mixed["frames_per_s"], "unit": "frames/s", "n_gpus": world, "steps": 1, "warmup": 0,
         "ms_per_step": mixed["makespan_s"] * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16 + f32", "data": "synthetic",
         "config": {"workload": f"c4: Poisson stream of {len(q)} press queries at 4096/s over {args.stream_s} s, "
@@ -499,6 +563,7 @@ def run_serving_bench(args):
                                "every 64th in-range query checked against the MPM (5 um RMS gate)",
                    "train_samples": args.samples, "train_steps": args.train_steps},
         "mixed": mixed, "plain_mpm": plain, "speedup": mixed["frames_per_s"] / plain["frames_per_s"],
+        "parallelism": f"stream split over {world} rank(s), a server (network + MPM lane) per GPU",
     }
 
 
@@ -699,10 +764,14 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--instances", type=int, default=256, help="sensors of the batched workload")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--plan", default="", help="transfer plan bx x by x bz / threads per cell, e.g. 8x8x4/3 "
+                                               "(default: the library's)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours" and not args.substeps:
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
 
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        sys.exit(relaunch_under_torchrun(args.gpus))
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
@@ -717,8 +786,12 @@ def main():
         torch.cuda.set_device(local_rank)
         torch.distributed.init_process_group("nccl")
     if args.workload == "serving":
+        result = run_serving_bench(args, rank, world, local_rank)
         if rank == 0:
-            print(json.dumps(run_serving_bench(args)))
+            print(json.dumps(result))
+        if world > 1:
+            torch.distributed.barrier()
+            torch.distributed.destroy_process_group()
         return
     if args.workload == "surrogate":
         if rank == 0:

@@ -69,6 +69,8 @@ typedef struct {
   double gravity[3];   /* m/s^2, applied on the grid; the paper uses none */
   int free_base;       /* 0: base held fixed (Eq. 10); 1: no base condition */
   int block[3];        /* particle-sort block in cells (0 -> library default) */
+  int threads_per_cell; /* transfer threads sharing a cell: 1 or 3 (0 -> 1); 3
+                           needs an 8x8x4 or 4x4x4 block; see tacchi_set_transfer */
 } tacchi_elastomer_desc;
 
 typedef enum {
@@ -116,6 +118,7 @@ typedef struct {
   int block[3];           /* particle-sort block in cells */
   int64_t n_blocks;
   size_t device_bytes;    /* device memory held by the context */
+  int threads_per_cell;   /* transfer threads sharing a cell (1 or 3) */
 } tacchi_info_t;
 
 /* Create a simulator on the current CUDA device (Sec. III-A, Initialization;
@@ -203,14 +206,20 @@ tacchi_status tacchi_shade(const tacchi_render_params *rp, const float *H_dev, i
  * in cells from grid node 0, the layout of tacchi_get_state), surf_dev (dev,
  * uint32 [n_surface], ids of the top-layer particles, flag bit 1), z0_dev
  * (dev, float [n_surface], their rest z in cells), dx_m, origin_m (x and y of
- * grid node 0, m), z_top_m (rest height of the top face).  window_m, w, hgt,
- * fill_radius and out_dev (dev, float [hgt][w], metres) are as in
- * tacchi_heightmap; the work is queued on stream.
+ * grid node 0, m), z_top_m (rest height of the top face).  Every id in
+ * surf_dev must be below n_particles: the library cannot check device data
+ * from the host without a copy, and a larger id reads past u_dev.
+ * window_m, w, hgt, fill_radius and out_dev (dev, float [hgt][w], metres) are
+ * as in tacchi_heightmap; the work is queued on stream.
  * Scratch: a static device array of TACCHI_STATIC_HEIGHTMAP_MAX_PIXELS ints
  * (4 MiB) that every GPU loading the library holds until the process exits.
  * The first call on a device looks up that array's device address (with the
- * device current); make that first call before any stream capture.  Every
- * call clears and reuses the same array, so calls that overlap on the GPU
+ * device current).  That first call, like the first launch of any of the
+ * library's kernels on a device, may also load the library's GPU code, and
+ * loading can allocate device memory (the 4 MiB array included).  So make
+ * one warm-up call per device at initialisation, before any stream capture
+ * and before the real-time loop; later calls allocate nothing.  Every call
+ * clears and reuses the same array, so calls that overlap on the GPU
  * (unordered streams or threads) race and corrupt each other's output.
  * Errors: INVALID_ARG (null pointers, w * hgt above the maximum, bad window),
  * CUDA. */
@@ -260,6 +269,17 @@ tacchi_status tacchi_set_profiling(tacchi_handle h, int on);
  * reset != 0 zeroes them after reading.  Synchronises the stream (to read the
  * device count of sorts).  out: host.  Errors: INVALID_ARG, CUDA. */
 tacchi_status tacchi_get_profile(tacchi_handle h, tacchi_profile_t *out, int reset);
+
+/* Measured FP32 FMA throughput of the current device, the ALU roof of the
+ * fused transfer (which does about 15 FP32 operations per byte it moves; the
+ * paper gives no roofline, this is measurement support).  Runs independent
+ * FMA chains, scalar and packed two-lane, over four full waves of every SM
+ * and writes the best rate in TFLOP/s (2 flop per lane per FMA) to *tflops;
+ * *sm_count and *sm_clock_khz (optional) receive the SM count and the
+ * device's maximum SM clock attribute (0 when the driver does not report
+ * it).  Allocates 4 bytes of device memory and a stream for the duration of
+ * the call; synchronises.  Errors: INVALID_ARG (null tflops), CUDA, OOM. */
+tacchi_status tacchi_measure_fp32_peak(double *tflops, int *sm_count, int *sm_clock_khz);
 
 /* Wait for the context's queued work and report the sticky device error. */
 tacchi_status tacchi_sync(tacchi_handle h);
@@ -382,19 +402,36 @@ tacchi_status tacchi_render_smoothed(tacchi_handle h, const tacchi_render_params
 tacchi_status tacchi_batch_reset(tacchi_handle h);
 
 /* Sort-block shape (cells) used by the transfer kernel for every instance:
- * 4x4x4, 8x8x4, 8x8x8 or 16x8x4.  Re-sorts the particles and drops cached
- * graphs.  Errors: INVALID_ARG for other shapes. */
+ * 4x4x4, 8x8x4, 8x8x8 or 16x8x4, with one thread per cell (the same as
+ * tacchi_set_transfer(h, bx, by, bz, 1)).  Re-sorts the particles and drops
+ * cached graphs.  Errors: INVALID_ARG for other shapes. */
 tacchi_status tacchi_set_block(tacchi_handle h, int bx, int by, int bz);
 
-/* Autotuner: times n_substeps substeps of length dt with each supported
- * block shape on the handle's current state (which it saves and restores,
- * together with the indenter poses), keeps the fastest shape and writes it to
- * best[3] (host); ms_per_substep[4] (host, optional) receives the time per
- * substep of the four candidates in the order 4x4x4, 8x8x4, 8x8x8, 16x8x4.
- * Synchronises.  Errors: INVALID_ARG, CUDA, and any device error raised
- * while timing. */
-tacchi_status tacchi_autotune(tacchi_handle h, int n_substeps, double dt, int best[3],
-                              double ms_per_substep[4]);
+/* Transfer plan of the fused G2P+P2G kernel (Sec. III-A, Eqs. 2-11): the
+ * sort block (bx, by, bz) in cells and how many threads share a cell.
+ * threads_per_cell = 1: one thread runs every particle of its cell and holds
+ * the cell's 27 node sums; any of the four block shapes.  threads_per_cell =
+ * 3: three threads split a cell's particles for G2P and the stress and its
+ * node planes for P2G; blocks 8x8x4 or 4x4x4.  The library default is 8x8x4
+ * with one thread per cell.  Both
+ * compute the same substep up to FP32 rounding order.  Re-sorts the
+ * particles and drops cached graphs.  Errors: INVALID_ARG for other plans. */
+tacchi_status tacchi_set_transfer(tacchi_handle h, int bx, int by, int bz, int threads_per_cell);
+
+/* Number of transfer plans the autotuner tries, in this order:
+ * 4x4x4/1, 8x8x4/1, 8x8x8/1, 16x8x4/1, 8x8x4/3, 4x4x4/3
+ * (block shape / threads per cell). */
+#define TACCHI_NUM_TRANSFER_PLANS 6
+
+/* Autotuner: times n_substeps substeps of length dt with each transfer plan
+ * on the handle's current state (which it saves and restores, together with
+ * the indenter poses), keeps the fastest plan and writes it to best[4]
+ * (host: bx, by, bz, threads per cell); ms_per_substep (host, optional,
+ * TACCHI_NUM_TRANSFER_PLANS entries) receives the time per substep of each
+ * plan in the order above.  Synchronises.  Errors: INVALID_ARG, CUDA, and
+ * any device error raised while timing. */
+tacchi_status tacchi_autotune(tacchi_handle h, int n_substeps, double dt, int best[4],
+                              double ms_per_substep[TACCHI_NUM_TRANSFER_PLANS]);
 
 /* ---- Learned surrogate ------------------------------------------------------
  * A U-Net that maps per-pixel inputs (the indenter's penetration map over the

@@ -23,6 +23,10 @@ __all__ = ["Tacchi", "TacchiError", "IndenterKind", "default_render_params", "sh
            "init_lattice", "lib"]
 
 
+# Transfer plans in the autotuner's order: sort block / threads per cell.
+TRANSFER_PLANS = ("4x4x4/1", "8x8x4/1", "8x8x8/1", "16x8x4/1", "8x8x4/3", "4x4x4/3")
+
+
 class IndenterKind:
     NONE, SPHERE, CYLINDER, CONE, PRISM, HEIGHTMAP = range(6)
 
@@ -117,6 +121,8 @@ class Tacchi:
         if block is not None:
             for a in range(3):
                 d.block[a] = block[a]
+            if len(block) > 3:
+                d.threads_per_cell = block[3]
         self._stream = stream if stream is not None else torch.cuda.current_stream()
         h = C.c_void_p()
         self._h = None
@@ -133,6 +139,7 @@ class Tacchi:
         self.dx = float(info.dx_m)
         self.z_top = float(info.z_top_m)
         self.block = tuple(int(x) for x in info.block)
+        self.threads_per_cell = int(info.threads_per_cell)
         self.n_blocks = int(info.n_blocks)
         self.device_bytes = int(info.device_bytes)
         self.device = torch.device("cuda", torch.cuda.current_device())
@@ -184,6 +191,11 @@ class Tacchi:
     def status(self) -> int:
         """Synchronise and return the device status code (0 = OK)."""
         return int(lib().tacchi_sync(self._h))
+
+    def set_transfer(self, shape, threads_per_cell):
+        """Transfer plan: sort block (bx, by, bz) and threads sharing a cell (1 or 3)."""
+        check(lib().tacchi_set_transfer(self._h, *shape, int(threads_per_cell)), "tacchi_set_transfer")
+        self.block, self.threads_per_cell = tuple(int(x) for x in shape), int(threads_per_cell)
 
     def set_profiling(self, on=True):
         check(lib().tacchi_set_profiling(self._h, int(bool(on))), "tacchi_set_profiling")
@@ -285,6 +297,8 @@ def _desc_from(block, seed=None, fix_base=True, gravity=(0.0, 0.0, 0.0), sort_bl
     if sort_block is not None:
         for a in range(3):
             d.block[a] = sort_block[a]
+        if len(sort_block) > 3:
+            d.threads_per_cell = sort_block[3]
     return d
 
 
@@ -374,13 +388,25 @@ class TacchiBatch:
         check(lib().tacchi_batch_reset(self._h), "tacchi_batch_reset")
 
     def set_block(self, shape):
+        """Sort block (bx, by, bz) with one thread per cell."""
         check(lib().tacchi_set_block(self._h, *shape), "tacchi_set_block")
 
+    def set_transfer(self, shape, threads_per_cell):
+        """Transfer plan: sort block (bx, by, bz) and threads sharing a cell (1 or 3)."""
+        check(lib().tacchi_set_transfer(self._h, *shape, int(threads_per_cell)), "tacchi_set_transfer")
+
+    def transfer_plan(self):
+        info = _lib.Info()
+        check(lib().tacchi_info(self._h, C.byref(info)), "tacchi_info")
+        return tuple(int(x) for x in info.block), int(info.threads_per_cell)
+
     def autotune(self, n_substeps, dt):
-        best = (C.c_int * 3)()
-        ms = (C.c_double * 4)()
+        """Times every transfer plan; returns ((bx, by, bz, threads per
+        cell) of the fastest, {plan name: ms per substep})."""
+        best = (C.c_int * 4)()
+        ms = (C.c_double * len(TRANSFER_PLANS))()
         check(lib().tacchi_autotune(self._h, int(n_substeps), float(dt), best, ms), "tacchi_autotune")
-        return tuple(best), dict(zip(["4x4x4", "8x8x4", "8x8x8", "16x8x4"], list(ms)))
+        return tuple(best), dict(zip(TRANSFER_PLANS, list(ms)))
 
     def heightmap(self, i, w, h, window, fill_radius=8, out=None):
         torch = self._torch

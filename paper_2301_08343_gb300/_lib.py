@@ -26,7 +26,7 @@ class ElastomerDesc(C.Structure):
                 ("nu", C.c_double), ("density", C.c_double), ("seed", C.c_uint64),
                 ("jitter", C.c_int), ("pad_side", C.c_int), ("pad_bottom", C.c_int),
                 ("pad_top", C.c_int), ("gravity", C.c_double * 3), ("free_base", C.c_int),
-                ("block", C.c_int * 3)]
+                ("block", C.c_int * 3), ("threads_per_cell", C.c_int)]
 
 
 class IndenterDesc(C.Structure):
@@ -45,7 +45,7 @@ class Info(C.Structure):
     _fields_ = [("n_particles", C.c_int64), ("n_surface", C.c_int64), ("grid", C.c_int * 3),
                 ("n_nodes", C.c_int64), ("origin_m", C.c_double * 3), ("dx_m", C.c_double),
                 ("z_top_m", C.c_double), ("block", C.c_int * 3), ("n_blocks", C.c_int64),
-                ("device_bytes", C.c_size_t)]
+                ("device_bytes", C.c_size_t), ("threads_per_cell", C.c_int)]
 
 
 class Profile(C.Structure):
@@ -81,6 +81,7 @@ SIGNATURES = {
     "tacchi_init_lattice": (C.c_int, [C.c_int] * 5 + [C.c_uint64, C.c_int, _fp, _u8p]),
     "tacchi_status_string": (C.c_char_p, [C.c_int]),
     "tacchi_version": (C.c_int, []),
+    "tacchi_measure_fp32_peak": (C.c_int, [_dp, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
 }
 EXTRA_SIGNATURES = {
     "tacchi_batch_create": (C.c_int, [C.c_int, C.POINTER(ElastomerDesc), _vp, C.POINTER(_vp)]),
@@ -94,6 +95,7 @@ EXTRA_SIGNATURES = {
     "tacchi_batch_get_state": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp, _vp]),
     "tacchi_batch_set_state": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp]),
     "tacchi_set_block": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int]),
+    "tacchi_set_transfer": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.c_int]),
     "tacchi_batch_reset": (C.c_int, [_vp]),
     "tacchi_batch_displacement_map": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _dp, _vp]),
     "tacchi_batch_markers": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp]),

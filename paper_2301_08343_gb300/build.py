@@ -19,7 +19,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libtacchi.so")
 
-SOURCES = ["api.cu", "mpm.cu", "render.cu", "nn.cu", "noalloc.cu"]
+SOURCES = ["api.cu", "mpm.cu", "transfer3.cu", "render.cu", "nn.cu", "noalloc.cu", "peak.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr",
                 "-Xcompiler", "-fPIC,-ffp-contract=off,-fno-fast-math", "-I", INCLUDE, "-I", CSRC]

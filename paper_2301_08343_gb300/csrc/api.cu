@@ -28,9 +28,11 @@ namespace {
 
 constexpr int kMaxChunk = 512;  // substeps per captured graph
 constexpr int kMaxGraphs = 8;   // cached (n, dt) graphs per context
-constexpr int kMaxFillRadius = 64;
 constexpr int kMaxInstances = 65536;
 const SortBlock kShapes[4] = {{4, 4, 4}, {8, 8, 4}, {8, 8, 8}, {16, 8, 4}};
+// transfer plans in the autotuner's order: shape and threads per cell
+const SortBlock kPlans[TACCHI_NUM_TRANSFER_PLANS] = {{4, 4, 4, 1}, {8, 8, 4, 1}, {8, 8, 8, 1},
+                                                     {16, 8, 4, 1}, {8, 8, 4, 3}, {4, 4, 4, 3}};
 
 bool finite_all(const double *a, int n) {
   for (int i = 0; i < n; ++i)
@@ -72,9 +74,18 @@ void make_lattice(int nx, int ny, int nz, int pad_side, int pad_bottom, uint64_t
 }
 
 bool block_supported(SortBlock b) {
-  for (const SortBlock &s : kShapes)
-    if (s.x == b.x && s.y == b.y && s.z == b.z) return true;
+  for (const SortBlock &s : kPlans)
+    if (s.x == b.x && s.y == b.y && s.z == b.z && s.t == b.t) return true;
   return false;
+}
+
+// The plan of a creation descriptor: its block (default 8x8x4) and threads
+// per cell (default 1, the faster plan on the GelSight-scale press).
+SortBlock desc_plan(const tacchi_elastomer_desc *d) {
+  const bool user_block = d->block[0] != 0 || d->block[1] != 0 || d->block[2] != 0;
+  SortBlock b = user_block ? SortBlock{d->block[0], d->block[1], d->block[2], 1} : SortBlock{8, 8, 4, 1};
+  if (d->threads_per_cell != 0) b.t = d->threads_per_cell;
+  return b;
 }
 
 tacchi_status cuda_status(cudaError_t e) { return e == cudaSuccess ? TACCHI_OK : TACCHI_ERR_CUDA; }
@@ -112,9 +123,7 @@ tacchi_status validate_desc(const tacchi_elastomer_desc *d, Geometry *g) {
   // the kernels index an instance's grid nodes with 32-bit arithmetic
   const double nodes = (g->n[0] + 2.0 * g->ps + 1) * (g->n[1] + 2.0 * g->ps + 1) * (g->n[2] + g->pb + g->pt + 1.0);
   if (nodes > 2147483647.0) return TACCHI_ERR_INVALID_ARG;
-  const bool user_block = d->block[0] != 0 || d->block[1] != 0 || d->block[2] != 0;
-  if (user_block && !block_supported(SortBlock{d->block[0], d->block[1], d->block[2]}))
-    return TACCHI_ERR_INVALID_ARG;
+  if (!block_supported(desc_plan(d))) return TACCHI_ERR_INVALID_ARG;
   return TACCHI_OK;
 }
 
@@ -163,7 +172,7 @@ struct tacchi_ctx {
   cudaStream_t cap = nullptr;
 
   std::vector<InstHost> in;
-  SortBlock blk{8, 8, 4};
+  SortBlock blk{8, 8, 4, 1};
   long long Ntot = 0, Nnodes = 0, Nblk = 0, Nblk_cap = 0, Ns_tot = 0;
 
   Batch b{};  // device pointers of the whole batch
@@ -652,8 +661,7 @@ tacchi_status create_batch(int n, const tacchi_elastomer_desc *descs, void *stre
   c->Nnodes = node;
   c->Ns_tot = surf;
   c->Nblk_cap = blk_cap;
-  // one thread per home cell: 8x8x4 blocks keep the 128 threads of a CTA busy
-  SortBlock blk = user_block ? SortBlock{d0.block[0], d0.block[1], d0.block[2]} : SortBlock{8, 8, 4};
+  SortBlock blk = desc_plan(&d0);
   for (int i = 0; i < n; ++i) c->in[i].dev.frames = nullptr;
 
   const long long N = c->Ntot, Nn = c->Nnodes;
@@ -813,6 +821,7 @@ tacchi_status tacchi_batch_info(tacchi_handle c, int i, tacchi_info_t *o) {
   o->block[0] = c->blk.x;
   o->block[1] = c->blk.y;
   o->block[2] = c->blk.z;
+  o->threads_per_cell = c->blk.t;
   o->n_blocks = h.dev.nblocks;
   o->device_bytes = c->device_bytes;
   return TACCHI_OK;
@@ -1290,10 +1299,16 @@ tacchi_status tacchi_get_grid(tacchi_handle c, float *out) {
 
 tacchi_status tacchi_set_block(tacchi_handle c, int bx, int by, int bz) {
   if (!c) return TACCHI_ERR_INVALID_ARG;
-  return apply_blocks(c, SortBlock{bx, by, bz});
+  return apply_blocks(c, SortBlock{bx, by, bz, 1});
 }
 
-tacchi_status tacchi_autotune(tacchi_handle c, int n_substeps, double dt, int best[3], double ms_per_substep[4]) {
+tacchi_status tacchi_set_transfer(tacchi_handle c, int bx, int by, int bz, int threads_per_cell) {
+  if (!c) return TACCHI_ERR_INVALID_ARG;
+  return apply_blocks(c, SortBlock{bx, by, bz, threads_per_cell});
+}
+
+tacchi_status tacchi_autotune(tacchi_handle c, int n_substeps, double dt, int best[4],
+                              double ms_per_substep[TACCHI_NUM_TRANSFER_PLANS]) {
   NvtxRange range("tacchi_autotune");
   if (!c || !best || n_substeps < 1 || n_substeps > kMaxChunk || !(dt > 0) || !std::isfinite(dt))
     return TACCHI_ERR_INVALID_ARG;
@@ -1323,8 +1338,8 @@ tacchi_status tacchi_autotune(tacchi_handle c, int n_substeps, double dt, int be
   c->profiling = false;
   double best_ms = 1e300;
   int best_k = -1;
-  for (int k = 0; k < 4 && st == TACCHI_OK; ++k) {
-    st = apply_blocks(c, kShapes[k]);
+  for (int k = 0; k < TACCHI_NUM_TRANSFER_PLANS && st == TACCHI_OK; ++k) {
+    st = apply_blocks(c, kPlans[k]);
     if (st != TACCHI_OK) break;
     double ms = 0;
     for (int rep = 0; rep < 2 && st == TACCHI_OK; ++rep) {  // the first run builds the graph
@@ -1347,12 +1362,13 @@ tacchi_status tacchi_autotune(tacchi_handle c, int n_substeps, double dt, int be
   c->profiling = prof;
   if (st == TACCHI_OK) st = restore();
   for (int i = 0; i < c->n_inst(); ++i) std::copy(poses[i].begin(), poses[i].end(), c->in[i].pose);
-  if (st == TACCHI_OK && best_k >= 0) st = apply_blocks(c, kShapes[best_k]);
+  if (st == TACCHI_OK && best_k >= 0) st = apply_blocks(c, kPlans[best_k]);
   cudaFree(save);
   if (st == TACCHI_OK) {
     best[0] = c->blk.x;
     best[1] = c->blk.y;
     best[2] = c->blk.z;
+    best[3] = c->blk.t;
     c->stepped = false;
   }
   return st;

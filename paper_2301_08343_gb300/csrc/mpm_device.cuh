@@ -1,0 +1,254 @@
+// mpm_device.cuh -- device helpers shared by the MLS-MPM transfer kernels
+// (Tacchi, arXiv 2301.08343, Sec. III-A): 3x3 algebra, the polar rotation
+// and the fixed-corotated stress (Eq. 5's S_p), quadratic B-spline weights,
+// block-wide scans of the cell grouping, the single-particle scatter and the
+// asynchronous-copy wrappers.  Included only by the library's .cu files.
+#pragma once
+#include "tacchi_internal.cuh"
+
+namespace tacchi {
+
+// ---------------------------------------------------------------------------
+// 3x3 helpers (row-major).
+__device__ __forceinline__ void cofactor3(const float Y[9], float c[9]) {
+  c[0] = Y[4] * Y[8] - Y[5] * Y[7];
+  c[1] = Y[5] * Y[6] - Y[3] * Y[8];
+  c[2] = Y[3] * Y[7] - Y[4] * Y[6];
+  c[3] = Y[2] * Y[7] - Y[1] * Y[8];
+  c[4] = Y[0] * Y[8] - Y[2] * Y[6];
+  c[5] = Y[1] * Y[6] - Y[0] * Y[7];
+  c[6] = Y[1] * Y[5] - Y[2] * Y[4];
+  c[7] = Y[2] * Y[3] - Y[0] * Y[5];
+  c[8] = Y[0] * Y[4] - Y[1] * Y[3];
+}
+
+// Rotation R of the polar decomposition F = R S by Newton's iteration
+// X <- (X + X^{-T}) / 2 (Higham 1986), carried in the form Y = X - I so that
+// R - I keeps its relative precision near the rest state.  With
+// X = I + Y:  det X = 1 + tr Y + m2(Y) + det Y  and
+// cof X = (1 + tr Y) I - Y^T + cof Y, hence
+// X^{-T} - I = [ -(m2 + det Y) I - Y^T + cof Y ] / det X.
+// Input H = F - I; output Y = R - I.
+__device__ __forceinline__ void polar_rotation_delta(const float H[9], float Y[9]) {
+  float hmag = 0.f;
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    Y[e] = H[e];
+    hmag = fmaxf(hmag, fabsf(H[e]));
+  }
+  // Newton converges quadratically: with |Y_{k+1} - Y_k| = e the next error is
+  // about e^2 / 2, below 1e-7 of the strain scale once e^2 <= 2e-7 |H|.
+  const float tol2 = 2e-7f * hmag;
+#pragma unroll 1
+  for (int it = 0; it < 12; ++it) {
+    float c[9];
+    cofactor3(Y, c);
+    const float m2 = c[0] + c[4] + c[8];
+    const float dY = Y[0] * c[0] + Y[1] * c[1] + Y[2] * c[2];
+    const float d = (Y[0] + Y[4] + Y[8]) + m2 + dY;
+    // approximate reciprocal: the iteration corrects its own rounding
+    const float inv = __fdividef(1.0f, 1.0f + d);
+    const float s = -(m2 + dY);
+    float Yn[9];
+    float diff = 0.f;
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        const float Z = ((r == q ? s : 0.f) - Y[q * 3 + r] + c[r * 3 + q]) * inv;
+        Yn[r * 3 + q] = 0.5f * (Y[r * 3 + q] + Z);
+        diff = fmaxf(diff, fabsf(Yn[r * 3 + q] - Y[r * 3 + q]));
+      }
+#pragma unroll
+    for (int e = 0; e < 9; ++e) Y[e] = Yn[e];
+    if (!(diff * diff > tol2)) break;
+  }
+}
+
+// Elasticity term S_p of Eq. 5 as the fixed-corotated Kirchhoff stress
+// tau = 2 mu (F - R) F^T + lambda J (J - 1) I, from H = F - I.
+// Returns J - 1 (computed as tr H + m2(H) + det H).
+__device__ __forceinline__ float kirchhoff_stress(const float H[9], float mu, float la, float tau[9]) {
+  float Y[9];
+  polar_rotation_delta(H, Y);
+  float c[9];
+  cofactor3(H, c);
+  const float Jm1 = (H[0] + H[4] + H[8]) + (c[0] + c[4] + c[8]) + (H[0] * c[0] + H[1] * c[1] + H[2] * c[2]);
+  const float J = 1.0f + Jm1;
+  float D[9];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) D[e] = H[e] - Y[e];  // F - R
+  const float pr = la * J * Jm1;
+  const float tm = 2.0f * mu;
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      // (D (I + H)^T)_{rq} = D_rq + sum_k D_rk H_qk
+      float t = D[r * 3 + q] + D[r * 3 + 0] * H[q * 3 + 0] + D[r * 3 + 1] * H[q * 3 + 1] + D[r * 3 + 2] * H[q * 3 + 2];
+      tau[r * 3 + q] = tm * t + (r == q ? pr : 0.f);
+    }
+  return Jm1;
+}
+
+// Quadratic B-spline weights of one axis at fraction f in [1/2, 3/2) from
+// the stencil base, and node offsets (i - f) in cells.
+__device__ __forceinline__ void bspline3(float f, float w[3], float d[3]) {
+  const float a = 1.5f - f, b = f - 1.0f, c = f - 0.5f;
+  w[0] = 0.5f * a * a;
+  w[1] = 0.75f - b * b;
+  w[2] = 0.5f * c * c;
+  d[0] = -f;
+  d[1] = 1.0f - f;
+  d[2] = 2.0f - f;
+}
+
+__device__ __forceinline__ int clampi(int x, int lo, int hi) { return x < lo ? lo : (x > hi ? hi : x); }
+
+// Exclusive scan over n (<= THREADS * PER) entries of `a` into `out` (out[n] =
+// total); also compacts the indices with a[c] > 0 into `cells`, returning
+// their number.  All threads of the CTA call it.
+template <int THREADS, int PER>
+__device__ __forceinline__ uint32_t block_scan_compact(const uint32_t *a, uint32_t *out, uint16_t *cells,
+                                                       int n, uint32_t *warp_buf) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NWARP = THREADS / 32;
+  uint32_t v[PER], nz[PER];
+  uint32_t sum = 0, nzs = 0;
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int c = tid * PER + q;
+    v[q] = c < n ? a[c] : 0u;
+    nz[q] = v[q] > 0 ? 1u : 0u;
+    sum += v[q];
+    nzs += nz[q];
+  }
+  // pack both running sums: counts < 2^20 per CTA, non-empty cells < 2^12
+  uint32_t x = sum | (nzs << 20);
+  const uint32_t mine = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_buf[warp] = x;
+  __syncthreads();
+  uint32_t wpre = 0;
+  for (int w = 0; w < warp; ++w) wpre += warp_buf[w];
+  uint32_t run = x - mine + wpre;
+  uint32_t rs = run & 0xFFFFFu, rn = run >> 20;
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int c = tid * PER + q;
+    if (c < n) {
+      out[c] = rs;
+      if (nz[q]) cells[rn] = (uint16_t)c;
+    }
+    rs += v[q];
+    rn += nz[q];
+  }
+  uint32_t tot = 0;
+  for (int w = 0; w < NWARP; ++w) tot += warp_buf[w];
+  if (tid == 0) out[n] = tot & 0xFFFFFu;
+  __syncthreads();
+  return tot >> 20;
+}
+
+// Stable partition of the n non-empty cells (cells[0..n), index order) into
+// four classes by particle count, heaviest first: >= 11, 9-10, 7-8, <= 6.
+// The thread-per-cell loop then runs cells of similar count side by side in
+// a warp, so that lanes and warps finish together when the particles of a
+// strained block have spread unevenly over its cells (at rest every cell
+// holds 8).  Within a class the index order (and the locality of
+// neighbouring cells in a warp) is kept.  All threads of the CTA call it.
+template <int THREADS, int PER>
+__device__ __forceinline__ void order_cells_by_load(const uint16_t *cells, const uint32_t *start, int n,
+                                                    uint16_t *order, unsigned long long *warp_buf) {
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NWARP = THREADS / 32;
+  auto cls = [](uint32_t k) { return k >= 11 ? 0 : (k >= 9 ? 1 : (k >= 7 ? 2 : 3)); };
+  int myc[PER];
+  unsigned long long cnt = 0;  // four 16-bit class counts of this thread's chunk
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int i = tid * PER + q;
+    myc[q] = -1;
+    if (i < n) {
+      const uint32_t c = cells[i];
+      myc[q] = cls(start[c + 1] - start[c]);
+      cnt += 1ull << (16 * myc[q]);
+    }
+  }
+  unsigned long long x = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_buf[warp] = x;
+  __syncthreads();
+  unsigned long long pre = x - cnt, tot = 0;
+  for (int w = 0; w < NWARP; ++w) {
+    if (w < warp) pre += warp_buf[w];
+    tot += warp_buf[w];
+  }
+  // class base = sum of the totals of the heavier classes
+  uint32_t base[4];
+  base[0] = 0;
+#pragma unroll
+  for (int k = 1; k < 4; ++k) base[k] = base[k - 1] + (uint32_t)((tot >> (16 * (k - 1))) & 0xFFFFu);
+  uint32_t run[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) run[k] = base[k] + (uint32_t)((pre >> (16 * k)) & 0xFFFFu);
+#pragma unroll
+  for (int q = 0; q < PER; ++q) {
+    const int i = tid * PER + q;
+    if (i < n) order[run[myc[q]]++] = cells[i];
+  }
+  __syncthreads();
+}
+
+// P2G of one particle straight into the shared tile (particles that change
+// cell during the substep, and the capacity fallback).
+__device__ __forceinline__ void scatter_particle(float *tile, int TN, int TX, int TY, int lx, int ly, int lz,
+                                                 const float f[3], const float mv[3], const float A[9]) {
+  float wx[3], wy[3], wz[3], dpx[3], dpy[3], dpz[3];
+  bspline3(f[0], wx, dpx);
+  bspline3(f[1], wy, dpy);
+  bspline3(f[2], wz, dpz);
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const float wjk = wy[j] * wz[k];
+      float *t = tile + ((lz + k) * TY + (ly + j)) * TX + lx;
+#pragma unroll
+      for (int i = 0; i < 3; ++i) {
+        const float w = wx[i] * wjk;
+        atomicAdd(t + i, w);
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+          atomicAdd(t + (a + 1) * TN + i,
+                    w * (mv[a] + A[a * 3 + 0] * dpx[i] + A[a * 3 + 1] * dpy[j] + A[a * 3 + 2] * dpz[k]));
+      }
+    }
+}
+
+// 16-byte asynchronous copy global -> shared (L2 only), and its group fences.
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async16_zfill(void *smem, const void *gmem, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"((uint32_t)__cvta_generic_to_shared(smem)),
+               "l"(gmem), "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+}  // namespace tacchi

@@ -66,7 +66,8 @@ extern "C" tacchi_status tacchi_heightmap_static(const float *u_dev, int64_t n_p
     return TACCHI_ERR_INVALID_ARG;
   if (w < 1 || hgt < 1 || (long long)w * hgt > (long long)TACCHI_STATIC_HEIGHTMAP_MAX_PIXELS)
     return TACCHI_ERR_INVALID_ARG;
-  if (!(window_m[2] > window_m[0]) || !(window_m[3] > window_m[1]) || fill_radius < 0 || fill_radius > 64)
+  if (!(window_m[2] > window_m[0]) || !(window_m[3] > window_m[1]) || fill_radius < 0 ||
+      fill_radius > tacchi::kMaxFillRadius)
     return TACCHI_ERR_INVALID_ARG;
 
   int *scratch = nullptr;

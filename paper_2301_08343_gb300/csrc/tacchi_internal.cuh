@@ -186,11 +186,20 @@ __device__ __forceinline__ bool inside_indenter(const IndenterShape &s, const In
 }
 
 // Launchers implemented in mpm.cu / render.cu (host side).
-struct SortBlock { int x, y, z; };
+// Transfer plan: the sort block in cells and the threads that share a cell
+// in the transfer kernel (1: k_transfer, mpm.cu; 3: k_transfer3,
+// transfer3.cu).
+struct SortBlock {
+  int x, y, z;
+  int t = 1;
+};
 cudaError_t launch_grid_update(const Batch &b, int substep, float dt, int clear, cudaStream_t st);
 cudaError_t launch_transfer(const Batch &b, SortBlock blk, int mode, float dt, cudaStream_t st);
 cudaError_t launch_sort(const Batch &b, SortBlock blk, int force, cudaStream_t st);
 cudaError_t prepare_transfer(SortBlock blk);
+bool transfer3_supported(SortBlock blk);
+cudaError_t prepare_transfer3(SortBlock blk);
+cudaError_t launch_transfer3(const Batch &b, SortBlock blk, int mode, float dt, cudaStream_t st);
 // P2G of the indenter particles of every instance at the frame of `substep`.
 cudaError_t launch_indenter_p2g(const Batch &b, int substep, cudaStream_t st);
 // Particles [o, o + n) of the records from / to structure-of-arrays u [3][n]
@@ -200,6 +209,9 @@ cudaError_t launch_pack_state(float4 *ps, long long o, long long n, const float 
 cudaError_t launch_unpack_state(const float4 *ps, long long o, long long n, float *u, float *Fm, cudaStream_t st);
 
 enum : int { XFER_P2G = 1, XFER_G2P = 2, XFER_FUSED = 3 };
+
+// Largest hole-fill radius (pixels) of a height map, for every entry point.
+constexpr int kMaxFillRadius = 64;
 
 struct HeightmapArgs {
   const float4 *ps;       // particle records [Ntot][3], or null: then

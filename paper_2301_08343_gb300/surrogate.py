@@ -93,6 +93,72 @@ def errors_um(pred, Y):
             "rms_xyz_um": all_rms, "signal_rms_uz_um": float((Y[..., 2] * 1e3).pow(2).mean().sqrt().item())}
 
 
+def per_frame_rms_um(pred, Y):
+    """RMS of the vertical displacement error of every frame (um), numpy."""
+    import torch
+    dz = (pred[..., 2] - Y[..., 2]) * 1e3
+    return torch.sqrt((dz ** 2).mean(dim=(1, 2))).cpu().numpy()
+
+
+def depth_bin(depth_m, width_m=0.1e-3):
+    return int(depth_m / width_m + 1e-9)
+
+
+def calibrate_region(rms_um, specs, gate_um=5.0, width_m=0.1e-3, min_frames=8):
+    """The validity region of a trained surrogate: the (shape, depth bin)
+    cells whose held-out frames all meet the gate at the 99th percentile of
+    their per-frame RMS error (cells with fewer than min_frames frames are
+    left out).  Returns a sorted list of (kind, bin) pairs."""
+    groups = {}
+    for e, sp in zip(rms_um, specs):
+        groups.setdefault((sp["kind"], depth_bin(sp["depth"], width_m)), []).append(float(e))
+    return sorted(k for k, v in groups.items() if len(v) >= min_frames and np.percentile(v, 99) <= gate_um)
+
+
+def in_region(region, kind, depth_m, width_m=0.1e-3):
+    return (kind, depth_bin(depth_m, width_m)) in set(map(tuple, region))
+
+
+def errors_by_group(rms_um, specs, width_m=0.1e-3):
+    """Per shape and per depth bin: frames, mean and p99 of the per-frame RMS
+    error (um)."""
+    out = {}
+    for key_of in (lambda sp: sp["kind"], lambda sp: f"{depth_bin(sp['depth'], width_m) * width_m * 1e3:.1f}mm"):
+        groups = {}
+        for e, sp in zip(rms_um, specs):
+            groups.setdefault(key_of(sp), []).append(float(e))
+        for k, v in sorted(groups.items()):
+            out[k] = {"n": len(v), "mean": float(np.mean(v)), "p99": float(np.percentile(v, 99))}
+    return out
+
+
+def tactile_images(uz_mm, block, rp=None):
+    """Tactile images (Sec. III-B, Eqs. 12-14) of vertical top-surface
+    displacement maps uz_mm [n, h, w] (mm, over the block's top face): the
+    height map H = z_top + u_z shaded by the library's kernel.  Returns
+    [n, h, w, 3] on the device."""
+    import torch
+    from . import default_render_params, shade
+    rp = rp or default_render_params()
+    n, h, w = uz_mm.shape
+    z_top = block.nz * block.dx
+    out = torch.empty((n, h, w, 3), device=uz_mm.device)
+    H = (z_top + uz_mm * MM).float().contiguous()
+    for i in range(n):
+        shade(H[i], block.nx * block.dx / w, block.ny * block.dx / h, z_top, rp, out=out[i])
+    return out
+
+
+def image_errors(img, ref):
+    """Per-frame RMS difference of two tactile image stacks (intensity in
+    [0, 1], over pixels and channels): mean, p99, max, and the mean PSNR."""
+    import torch
+    rms = torch.sqrt(((img - ref) ** 2).mean(dim=(1, 2, 3))).cpu().numpy()
+    psnr = -20.0 * np.log10(np.maximum(rms, 1e-12))
+    return {"rms_mean": float(rms.mean()), "rms_p99": float(np.percentile(rms, 99)), "rms_max": float(rms.max()),
+            "psnr_db_mean": float(psnr.mean())}
+
+
 def inference_rate(net: SurrogateNet, X, batch, reps=5):
     """Frames per second of surrogate inference at a batch size."""
     import torch

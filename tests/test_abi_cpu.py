@@ -76,6 +76,8 @@ def _desc(**kw):
     if "block" in kw:
         for a in range(3):
             d.block[a] = kw["block"][a]
+    if "tpc" in kw:
+        d.threads_per_cell = kw["tpc"]
     return d
 
 
@@ -83,6 +85,7 @@ def _desc(**kw):
     dict(dx=0.0), dict(dx=-1.0), dict(E=0.0), dict(nu=0.5), dict(nu=-1.0), dict(rho=0.0),
     dict(extent=(6.1e-3, 6e-3, 2e-3)), dict(extent=(0.0, 6e-3, 2e-3)), dict(pad_side=2),
     dict(pad_top=1), dict(block=(3, 3, 3)), dict(extent=(float("nan"), 6e-3, 2e-3)),
+    dict(block=(8, 8, 8), tpc=3), dict(tpc=2), dict(block=(16, 8, 4), tpc=3),
     dict(pad_side=1025), dict(extent=(0.725, 0.725, 0.5e-3), pad_top=1024),  # 2.19e9 grid nodes
 ])
 def test_create_rejects_invalid_descriptions_before_touching_cuda(L, bad):

@@ -92,10 +92,15 @@ def test_batched_instances_match_single_instance_runs_and_oracle():
             assert np.abs(ub - o.state()[0]).max() <= 1e-3
 
 
-@pytest.mark.parametrize("shape", [(4, 4, 4), (8, 8, 4), (8, 8, 8), (16, 8, 4)])
-def test_every_block_shape_gives_the_same_batch(shape):
-    ref = run_batch(shape=(4, 4, 4))
+@pytest.mark.parametrize("shape", [(4, 4, 4, 1), (8, 8, 4, 1), (8, 8, 8, 1), (16, 8, 4, 1), (8, 8, 4, 3),
+                                   (4, 4, 4, 3)])
+def test_every_transfer_plan_gives_the_same_batch(shape):
+    """Every block shape, with one thread per cell or three, steps the batch
+    alike (FP32 summation order only)."""
+    ref = run_batch(shape=(4, 4, 4, 1))
+    assert ref.transfer_plan() == ((4, 4, 4), 1)
     got = run_batch(shape=shape)
+    assert got.transfer_plan() == (tuple(shape[:3]), shape[3])
     for i in range(len(BLOCKS)):
         a = ref.get_state(i)["u"].cpu().numpy()
         b = got.get_state(i)["u"].cpu().numpy()
@@ -111,8 +116,9 @@ def test_autotune_keeps_the_state_and_picks_a_supported_shape():
     before = [bt.get_state(i)["u"].clone() for i in range(len(BLOCKS))]
     poses = [bt.indenter_pose(i) for i in range(len(BLOCKS))]
     best, ms = bt.autotune(8, 1e-5)
-    assert best in [(4, 4, 4), (8, 8, 4), (8, 8, 8), (16, 8, 4)]
-    assert all(v > 0 for v in ms.values())
+    assert best in [(4, 4, 4, 1), (8, 8, 4, 1), (8, 8, 8, 1), (16, 8, 4, 1), (8, 8, 4, 3), (4, 4, 4, 3)]
+    assert bt.transfer_plan() == (best[:3], best[3])
+    assert len(ms) == 6 and all(v > 0 for v in ms.values())
     for i in range(len(BLOCKS)):
         assert torch.equal(bt.get_state(i)["u"], before[i])
         assert bt.indenter_pose(i) == poses[i]

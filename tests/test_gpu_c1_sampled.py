@@ -47,7 +47,7 @@ def test_c1_two_substeps_at_sampled_nodes_and_particles():
     dx = b.dx
     g = T.Tacchi(b.extent_m, dx, b.E, b.nu, b.rho, seed=0, pad_side=b.pad_side, pad_bottom=b.pad_bottom,
                  pad_top=b.pad_top)
-    assert g.block == (8, 8, 4) and g.N == 24_576_000
+    assert g.block == (8, 8, 4) and g.threads_per_cell == 1 and g.N == 24_576_000
     R, depth, n = 4e-3, 0.5e-3, 200
     g.set_indenter(T.IndenterKind.SPHERE, (R,), (b.nx * dx / 2, b.ny * dx / 2, g.z_top + R, 1, 0, 0, 0),
                    (0, 0, -depth / (n * dt), 0, 0, 0))
