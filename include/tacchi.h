@@ -71,7 +71,22 @@ typedef struct {
   int block[3];        /* particle-sort block in cells (0 -> library default) */
   int threads_per_cell; /* transfer threads sharing a cell: 1 or 3 (0 -> 1); 3
                            needs an 8x8x4 or 4x4x4 block; see tacchi_set_transfer */
+  int contact_mode;     /* grid-boundary indenter contact: TACCHI_CONTACT_STICKY
+                           (0, the default) or TACCHI_CONTACT_SLIP (1) */
 } tacchi_elastomer_desc;
+
+/* Contact of the grid-boundary indenter with the elastomer (Sec. III-A, Eq. 10:
+ * the paper's indenter moves the grid nodes it covers with its own velocity,
+ * a no-slip contact; it has no friction model, Sec. V).
+ * STICKY: a grid node inside the indenter takes the indenter's rigid velocity.
+ * SLIP: a node inside the indenter that holds mass keeps its velocity except
+ * for the part that moves into the indenter relative to it: with n the
+ * outward normal of the indenter's surface at the node (radial for the sphere
+ * and the cylinder, the lateral face for the cone and the prism, the surface
+ * gradient for a height map) and W the indenter's velocity there,
+ * V <- V - min(0, (V - W).n) n; empty nodes take W. */
+#define TACCHI_CONTACT_STICKY 0
+#define TACCHI_CONTACT_SLIP 1
 
 typedef enum {
   TACCHI_INDENTER_NONE = 0,

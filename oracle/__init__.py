@@ -49,7 +49,8 @@ class Params(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
                 ("pad_side", C.c_int), ("pad_bottom", C.c_int), ("pad_top", C.c_int),
                 ("dx", C.c_double), ("E", C.c_double), ("nu", C.c_double),
-                ("rho", C.c_double), ("gravity", C.c_double * 3), ("fix_base", C.c_int)]
+                ("rho", C.c_double), ("gravity", C.c_double * 3), ("fix_base", C.c_int),
+                ("slip", C.c_int)]
 
 
 class RenderParams(C.Structure):
@@ -173,7 +174,7 @@ class Sim:
     """One elastomer instance simulated by the oracle (FP64)."""
 
     def __init__(self, nx, ny, nz, dx, E, nu, rho, pad_side=4, pad_bottom=3, pad_top=4,
-                 gravity=(0.0, 0.0, 0.0), fix_base=True):
+                 gravity=(0.0, 0.0, 0.0), fix_base=True, slip=False):
         p = Params()
         p.nx, p.ny, p.nz = nx, ny, nz
         p.pad_side, p.pad_bottom, p.pad_top = pad_side, pad_bottom, pad_top
@@ -181,6 +182,7 @@ class Sim:
         for a in range(3):
             p.gravity[a] = gravity[a]
         p.fix_base = int(bool(fix_base))
+        p.slip = int(bool(slip))
         self.params = p
         self._L = lib()
         self._h = self._L.ora_create(C.byref(p))

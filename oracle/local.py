@@ -1,7 +1,8 @@
 """Substeps of the method in FP64 over the particles of one box of grid
 nodes, from the oracle's per-particle routines (B-spline weights, polar
-decomposition and stress): P2G (Eqs. 2-5), grid velocity (Eq. 6), G2P, the
-F update and advection (Eqs. 7-11).
+decomposition and stress): P2G (Eqs. 2-5), grid velocity (Eq. 6) with the
+indenter, base and padding-band conditions, G2P, the F update and advection
+(Eqs. 7-11).
 
 TEST INFRASTRUCTURE ONLY, like the rest of ``oracle/``: the full-size sampled
 parity tests recompute two substeps around sampled grid nodes with it, where
@@ -73,7 +74,31 @@ class Local:
 
 
 def velocity(M, MG):
+    """Eq. 6 alone: V = MG / M where M > 0, else 0."""
     V = np.zeros_like(MG)
     pos = M > 0
     V[pos] = MG[pos] / M[pos][:, None]
+    return V
+
+
+def grid_velocity(M, MG, lo, G, dx=None, origin=None, inside=None, pose=None, vel=None, base_k=None):
+    """Eq. 6 and the boundary conditions over the box's nodes lo + [0, shape),
+    in the order of the oracle's grid update: a node inside the indenter
+    (inside(i, j, k), the oracle's own decision at the pose of the substep)
+    takes the indenter's rigid velocity v + w x (X - c) (Eq. 10); a node at or
+    below the base layer base_k takes 0 (the fixed base, Eq. 10); the outer
+    two node layers of the grid (G nodes per axis) take 0."""
+    V = velocity(M, MG)
+    nz, ny, nx = M.shape
+    for k in range(nz):
+        for j in range(ny):
+            for i in range(nx):
+                I, J, K = lo[0] + i, lo[1] + j, lo[2] + k
+                if inside is not None and inside(I, J, K):
+                    r = origin + dx * np.array([I, J, K], float) - np.asarray(pose[:3], float)
+                    V[k, j, i] = np.asarray(vel[:3], float) + np.cross(np.asarray(vel[3:], float), r)
+                if base_k is not None and K <= base_k:
+                    V[k, j, i] = 0.0
+                if I < 2 or J < 2 or K < 2 or I > G[0] - 3 or J > G[1] - 3 or K > G[2] - 3:
+                    V[k, j, i] = 0.0
     return V

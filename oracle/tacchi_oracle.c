@@ -613,6 +613,61 @@ static void p2g_into(ora_sim *s, double dt, double *mass, double *mom) {
 
 void ora_p2g(ora_sim *s, double dt, double *mass, double *mom) { p2g_into(s, dt, mass, mom); }
 
+/* Outward unit normal of the grid-boundary indenter's surface at node
+ * (i, j, k), in FP64, for the slip contact mode (the paper's indenter is
+ * no-slip, Eq. 10; slip removes only the relative velocity into it).
+ * Sphere: radial from the centre.  Cylinder (axis local x): radial from the
+ * axis.  Cone (apex at the pose, opening to local +z, half angle a) and prism
+ * (edge along local y, faces at x_l = +-tan(a) z_l): the lateral face,
+ * (rho_hat, -tan a) / sqrt(1 + tan^2 a).  Height map (surface z_l = -h):
+ * (-dh/dx_l, -dh/dy_l, -1) / |.| from the bilinear interpolant.  Undefined
+ * cases (a node on an axis or edge) take the local -z direction. */
+static void indenter_normal(const ora_sim *s, int i, int j, int k, double n[3]) {
+  double Rm[9], d[3], m[3] = {0.0, 0.0, -1.0};
+  quat_to_mat(s->pose + 3, Rm);
+  double X[3] = {s->origin[0] + i * s->p.dx, s->origin[1] + j * s->p.dx, s->origin[2] + k * s->p.dx};
+  for (int a = 0; a < 3; ++a) d[a] = X[a] - s->pose[a];
+  if (s->ind_kind == ORA_IND_SPHERE) {
+    double q = sqrt(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+    if (q > 0.0) {
+      for (int a = 0; a < 3; ++a) n[a] = d[a] / q;
+      return;
+    }
+  } else {
+    double l[3];
+    for (int b = 0; b < 3; ++b) l[b] = Rm[0 * 3 + b] * d[0] + Rm[1 * 3 + b] * d[1] + Rm[2 * 3 + b] * d[2];
+    const double *P = s->ind_params;
+    if (s->ind_kind == ORA_IND_CYLINDER) {
+      double q = sqrt(l[1] * l[1] + l[2] * l[2]);
+      if (q > 0.0) { m[0] = 0.0; m[1] = l[1] / q; m[2] = l[2] / q; }
+    } else if (s->ind_kind == ORA_IND_CONE) {
+      double t = tan(P[0]), q = sqrt(l[0] * l[0] + l[1] * l[1]), c = 1.0 / sqrt(1.0 + t * t);
+      if (q > 0.0) { m[0] = l[0] / q * c; m[1] = l[1] / q * c; m[2] = -t * c; }
+    } else if (s->ind_kind == ORA_IND_PRISM) {
+      double t = tan(P[0]), c = 1.0 / sqrt(1.0 + t * t);
+      if (l[0] != 0.0) { m[0] = (l[0] > 0.0 ? 1.0 : -1.0) * c; m[1] = 0.0; m[2] = -t * c; }
+    } else if (s->ind_kind == ORA_IND_HEIGHTMAP) {
+      int w = s->hm_w, h = s->hm_h;
+      double fx = l[0] / s->hm_pixel + (w * 0.5 - 0.5), fy = l[1] / s->hm_pixel + (h * 0.5 - 0.5);
+      double cx = fx < 0.0 ? 0.0 : (fx > w - 1.0 ? w - 1.0 : fx);
+      double cy = fy < 0.0 ? 0.0 : (fy > h - 1.0 ? h - 1.0 : fy);
+      int ix = (int)floor(cx), iy = (int)floor(cy);
+      if (ix > w - 2) ix = w - 2;
+      if (iy > h - 2) iy = h - 2;
+      double tx = cx - ix, ty = cy - iy;
+      const float *H = s->hm; /* cells */
+      double h00 = H[iy * w + ix], h01 = H[iy * w + ix + 1], h10 = H[(iy + 1) * w + ix], h11 = H[(iy + 1) * w + ix + 1];
+      /* slope: cells of height per pixel, times dX / pixel */
+      double sc = s->p.dx / s->hm_pixel;
+      double gx = (fx > 0.0 && fx < w - 1.0) ? ((h01 - h00) * (1.0 - ty) + (h11 - h10) * ty) * sc : 0.0;
+      double gy = (fy > 0.0 && fy < h - 1.0) ? ((h10 - h00) * (1.0 - tx) + (h11 - h01) * tx) * sc : 0.0;
+      double c = 1.0 / sqrt(1.0 + gx * gx + gy * gy);
+      m[0] = -gx * c; m[1] = -gy * c; m[2] = -c;
+    }
+  }
+  for (int a = 0; a < 3; ++a) n[a] = Rm[a * 3 + 0] * m[0] + Rm[a * 3 + 1] * m[1] + Rm[a * 3 + 2] * m[2];
+}
+
 /* Grid velocity, Eq. 6, then the boundary conditions (indenter, Eq. 10 on
  * the base nodes, padding band). */
 static void grid_update(ora_sim *s, double dt) {
@@ -634,9 +689,19 @@ static void grid_update(ora_sim *s, double dt) {
       double X[3] = {s->origin[0] + i * dx, s->origin[1] + j * dx, s->origin[2] + k * dx};
       double r[3] = {X[0] - s->pose[0], X[1] - s->pose[1], X[2] - s->pose[2]};
       const double *w = s->vel + 3;
-      V[0] = s->vel[0] + (w[1] * r[2] - w[2] * r[1]);
-      V[1] = s->vel[1] + (w[2] * r[0] - w[0] * r[2]);
-      V[2] = s->vel[2] + (w[0] * r[1] - w[1] * r[0]);
+      double W[3] = {s->vel[0] + (w[1] * r[2] - w[2] * r[1]), s->vel[1] + (w[2] * r[0] - w[0] * r[2]),
+                     s->vel[2] + (w[0] * r[1] - w[1] * r[0])};
+      if (s->p.slip && M > 0.0) {
+        /* slip: remove only the velocity into the indenter, relative to it */
+        double nrm[3];
+        indenter_normal(s, i, j, k, nrm);
+        double q[3] = {V[0] - W[0], V[1] - W[1], V[2] - W[2]};
+        double vn = q[0] * nrm[0] + q[1] * nrm[1] + q[2] * nrm[2];
+        if (vn < 0.0)
+          for (int a = 0; a < 3; ++a) V[a] = W[a] + (q[a] - vn * nrm[a]);
+      } else { /* sticky (Eq. 10's rigid indenter), or an empty node */
+        for (int a = 0; a < 3; ++a) V[a] = W[a];
+      }
     }
     if (s->p.fix_base && k <= base_k) V[0] = V[1] = V[2] = 0.0;
     if (i < 2 || j < 2 || k < 2 || i > s->G[0] - 3 || j > s->G[1] - 3 || k > s->G[2] - 3)

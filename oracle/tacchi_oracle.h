@@ -31,6 +31,8 @@ typedef struct {
   double E, nu, rho;              /* Young's modulus [Pa], Poisson, density */
   double gravity[3];              /* [m/s^2], 0 unless a test sets it */
   int fix_base;                   /* 1: base set B and base nodes held fixed */
+  int slip;                       /* 1: slip contact with the grid-boundary
+                                     indenter (else sticky, Eq. 10) */
 } ora_params;
 
 typedef struct {

@@ -27,6 +27,10 @@ __all__ = ["Tacchi", "TacchiError", "IndenterKind", "default_render_params", "sh
 TRANSFER_PLANS = ("4x4x4/1", "8x8x4/1", "8x8x8/1", "16x8x4/1", "8x8x4/3", "4x4x4/3")
 
 
+class Contact:
+    STICKY, SLIP = 0, 1
+
+
 class IndenterKind:
     NONE, SPHERE, CYLINDER, CONE, PRISM, HEIGHTMAP = range(6)
 
@@ -107,7 +111,7 @@ class Tacchi:
 
     def __init__(self, extent_m, dx, E=3.0e5, nu=0.45, density=1000.0, seed=0, jitter=True,
                  pad_side=4, pad_bottom=3, pad_top=4, gravity=(0.0, 0.0, 0.0), fix_base=True,
-                 block=None, stream=None):
+                 block=None, stream=None, contact_mode=0):
         torch = _torch()
         self._torch = torch
         d = _lib.ElastomerDesc()
@@ -118,6 +122,7 @@ class Tacchi:
         d.seed, d.jitter = seed, int(bool(jitter))
         d.pad_side, d.pad_bottom, d.pad_top = pad_side, pad_bottom, pad_top
         d.free_base = 0 if fix_base else 1
+        d.contact_mode = int(contact_mode)
         if block is not None:
             for a in range(3):
                 d.block[a] = block[a]
@@ -281,7 +286,8 @@ class Tacchi:
         return out
 
 
-def _desc_from(block, seed=None, fix_base=True, gravity=(0.0, 0.0, 0.0), sort_block=None, jitter=True):
+def _desc_from(block, seed=None, fix_base=True, gravity=(0.0, 0.0, 0.0), sort_block=None, jitter=True,
+               contact_mode=0):
     """ElastomerDesc from an object with nx, ny, nz, dx, E, nu, rho, pad_side,
     pad_bottom, pad_top and seed attributes."""
     d = _lib.ElastomerDesc()
@@ -294,6 +300,7 @@ def _desc_from(block, seed=None, fix_base=True, gravity=(0.0, 0.0, 0.0), sort_bl
     d.jitter = int(bool(jitter))
     d.pad_side, d.pad_bottom, d.pad_top = block.pad_side, block.pad_bottom, block.pad_top
     d.free_base = 0 if fix_base else 1
+    d.contact_mode = int(contact_mode)
     if sort_block is not None:
         for a in range(3):
             d.block[a] = sort_block[a]
@@ -305,13 +312,13 @@ def _desc_from(block, seed=None, fix_base=True, gravity=(0.0, 0.0, 0.0), sort_bl
 class TacchiBatch:
     """Many independent sensor elastomers advanced together (one handle)."""
 
-    def __init__(self, blocks, fix_base=True, sort_block=None, stream=None):
+    def __init__(self, blocks, fix_base=True, sort_block=None, stream=None, contact_mode=0):
         torch = _torch()
         self._torch = torch
         n = len(blocks)
         arr = (_lib.ElastomerDesc * n)()
         for i, b in enumerate(blocks):
-            arr[i] = _desc_from(b, fix_base=fix_base, sort_block=sort_block)
+            arr[i] = _desc_from(b, fix_base=fix_base, sort_block=sort_block, contact_mode=contact_mode)
         self._stream = stream if stream is not None else torch.cuda.current_stream()
         h = C.c_void_p()
         self._h = None

@@ -26,7 +26,7 @@ class ElastomerDesc(C.Structure):
                 ("nu", C.c_double), ("density", C.c_double), ("seed", C.c_uint64),
                 ("jitter", C.c_int), ("pad_side", C.c_int), ("pad_bottom", C.c_int),
                 ("pad_top", C.c_int), ("gravity", C.c_double * 3), ("free_base", C.c_int),
-                ("block", C.c_int * 3), ("threads_per_cell", C.c_int)]
+                ("block", C.c_int * 3), ("threads_per_cell", C.c_int), ("contact_mode", C.c_int)]
 
 
 class IndenterDesc(C.Structure):

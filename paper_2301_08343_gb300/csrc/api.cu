@@ -124,6 +124,8 @@ tacchi_status validate_desc(const tacchi_elastomer_desc *d, Geometry *g) {
   const double nodes = (g->n[0] + 2.0 * g->ps + 1) * (g->n[1] + 2.0 * g->ps + 1) * (g->n[2] + g->pb + g->pt + 1.0);
   if (nodes > 2147483647.0) return TACCHI_ERR_INVALID_ARG;
   if (!block_supported(desc_plan(d))) return TACCHI_ERR_INVALID_ARG;
+  if (d->contact_mode != TACCHI_CONTACT_STICKY && d->contact_mode != TACCHI_CONTACT_SLIP)
+    return TACCHI_ERR_INVALID_ARG;
   return TACCHI_OK;
 }
 
@@ -645,6 +647,7 @@ tacchi_status create_batch(int n, const tacchi_elastomer_desc *descs, void *stre
     }
     I.pad_bottom = g.pb;
     I.fix_base = d.free_base ? 0 : 1;
+    I.slip = d.contact_mode == TACCHI_CONTACT_SLIP ? 1 : 0;
     I.node_off = h.node_off;
     I.N = h.N;
     I.part_off = h.part_off;

@@ -1,12 +1,14 @@
 // mpm.cu -- MLS-MPM substep kernels for sm_103a (Tacchi, arXiv 2301.08343,
 // Sec. III-A).
 //
-//   k_grid_update  Eq. 6 (V = MG / M) fused with the rigid indenter, the fixed
-//                  base (Eq. 10 on the grid) and the padding band.
+//   k_grid_update  Eq. 6 (V = MG / M) fused with the rigid indenter (sticky,
+//                  or slip: only the relative velocity into it removed), the
+//                  fixed base (Eq. 10 on the grid) and the padding band.
 //   k_transfer     one CTA per sort block of cells.  G2P of substep k
 //                  (Eqs. 7-9, the base override of Eq. 10 and advection,
-//                  Eq. 11) fused with P2G of substep k+1 (Eqs. 2-5) into a
-//                  shared-memory grid tile, flushed with vector reductions.
+//                  Eq. 11) fused with P2G of substep k+1 (Eqs. 2-5), summed
+//                  per cell in registers and added to the grid with vector
+//                  reductions.
 //                  P2G-only and G2P-only variants start and end a step.
 //   k_sort_*       counting sort of particle ids by grid block, run only when
 //                  a particle left its block during the last transfer.
@@ -41,9 +43,25 @@ __global__ void __launch_bounds__(256) k_grid_update(Batch b, int substep, float
       const float r0 = ((float)i - f.c[0]) * I.dx;
       const float r1 = ((float)j - f.c[1]) * I.dx;
       const float r2 = ((float)k - f.c[2]) * I.dx;
-      V0 = f.vlin[0] + (f.w[1] * r2 - f.w[2] * r1);
-      V1 = f.vlin[1] + (f.w[2] * r0 - f.w[0] * r2);
-      V2 = f.vlin[2] + (f.w[0] * r1 - f.w[1] * r0);
+      const float W0 = f.vlin[0] + (f.w[1] * r2 - f.w[2] * r1);
+      const float W1 = f.vlin[1] + (f.w[2] * r0 - f.w[0] * r2);
+      const float W2 = f.vlin[2] + (f.w[0] * r1 - f.w[1] * r0);
+      if (I.slip && mm.x > 0.f) {
+        // slip: only the velocity into the indenter, relative to it, is removed
+        float nrm[3];
+        indenter_normal(I.shape, f, i, j, k, nrm);
+        const float q0 = V0 - W0, q1 = V1 - W1, q2 = V2 - W2;
+        const float vn = q0 * nrm[0] + q1 * nrm[1] + q2 * nrm[2];
+        if (vn < 0.f) {
+          V0 = W0 + (q0 - vn * nrm[0]);
+          V1 = W1 + (q1 - vn * nrm[1]);
+          V2 = W2 + (q2 - vn * nrm[2]);
+        }
+      } else {  // sticky (the default), or an empty node
+        V0 = W0;
+        V1 = W1;
+        V2 = W2;
+      }
     }
   }
   if (I.fix_base && k <= I.pad_bottom) V0 = V1 = V2 = 0.f;  // sensor base, Eq. 10
@@ -60,9 +78,9 @@ __global__ void __launch_bounds__(256) k_grid_update(Batch b, int substep, float
 // (counting sort in shared memory) and gives each non-empty cell to one
 // thread, which runs G2P for the cell's particles against the shared
 // velocity tile and accumulates their P2G contributions to the cell's 27
-// nodes in registers; the accumulators reach the shared grid tile once per
-// cell.  A particle whose stencil base changes during the substep scatters
-// on its own.
+// nodes in registers; the accumulators reach the grid once per cell, by
+// vector reductions to global memory.  A particle whose stencil base changes
+// during the substep scatters on its own, also straight to the grid.
 template <int BX, int BY, int BZ>
 struct XferPlan {
   static constexpr int THREADS = 128;
@@ -70,13 +88,11 @@ struct XferPlan {
   static constexpr int NE = EX * EY * EZ;
   static constexpr int VX = BX + 4, VY = BY + 4, VZ = BZ + 4;       // V tile, nodes [B0-1, B0+B+3)
   static constexpr int VN = VX * VY * VZ;
-  static constexpr int TX = BX + 6, TY = BY + 6, TZ = BZ + 6;       // P2G tile, nodes [B0-2, B0+B+4)
-  static constexpr int TN = TX * TY * TZ;
   static constexpr int MAXP = 12 * BX * BY * BZ;                    // particles grouped in smem (1.5x nominal)
   static constexpr int PER = (NE + 1 + THREADS - 1) / THREADS;      // scan entries per thread
   // byte offsets in dynamic shared memory
-  static constexpr size_t OFF_TILE = 0;                             // float [4][TN]; first u32 key[MAXP]
-  static constexpr size_t OFF_V = OFF_TILE + 16 * (size_t)TN;       // float4 [VN]
+  static constexpr size_t OFF_KEY = 0;                              // u32 [MAXP] rank and cell per particle
+  static constexpr size_t OFF_V = OFF_KEY + 4 * (size_t)MAXP;       // float4 [VN]
   static constexpr size_t OFF_LIST = OFF_V + 16 * (size_t)VN;       // u32 [MAXP] particles by cell
   static constexpr size_t OFF_PID = OFF_LIST + 4 * (size_t)MAXP;    // u32 [MAXP] particle ids in idx order
   static constexpr size_t OFF_CNT = OFF_PID + 4 * (size_t)MAXP;     // u32 [NE] count, then start
@@ -86,7 +102,6 @@ struct XferPlan {
   static constexpr size_t OFF_ORDER = OFF_CELLS + 2 * (size_t)NE;   // u16 [NE] cells, heaviest class first
   static constexpr size_t OFF_STAGE = (OFF_ORDER + 2 * (size_t)NE + 15) / 16 * 16;
   static constexpr size_t BYTES = OFF_STAGE + 16 * 2 * 3 * (size_t)THREADS;
-  static_assert(4 * TN >= MAXP, "the P2G tile doubles as the key scratch");
 };
 
 // Resident transfer CTAs per SM the register allocation is bounded for.
@@ -99,10 +114,9 @@ __global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer(Batch 
   using P = XferPlan<BX, BY, BZ>;
   constexpr bool DO_G2P = (MODE & XFER_G2P) != 0;
   constexpr bool DO_P2G = (MODE & XFER_P2G) != 0;
-  constexpr int TX = P::TX, TY = P::TY, TN = P::TN, VX = P::VX, VY = P::VY;
+  constexpr int VX = P::VX, VY = P::VY;
   extern __shared__ __align__(16) unsigned char smem[];
-  float *tile = reinterpret_cast<float *>(smem + P::OFF_TILE);
-  uint32_t *s_key = reinterpret_cast<uint32_t *>(smem + P::OFF_TILE);
+  uint32_t *s_key = reinterpret_cast<uint32_t *>(smem + P::OFF_KEY);
   float4 *vt = reinterpret_cast<float4 *>(smem + P::OFF_V);
   uint32_t *s_list = reinterpret_cast<uint32_t *>(smem + P::OFF_LIST);
   uint32_t *s_pid = reinterpret_cast<uint32_t *>(smem + P::OFF_PID);
@@ -204,10 +218,6 @@ __global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer(Batch 
     order_cells_by_load<P::THREADS, P::PER>(s_cells, s_start, (int)ncells, s_order, s_warp64);
   }
   __syncthreads();
-  if (DO_P2G) {
-    float4 *tile4 = reinterpret_cast<float4 *>(tile);
-    for (int t = tid; t < TN; t += P::THREADS) tile4[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-  }
   cp_async_wait<0>();  // this thread's part of the V tile
   __syncthreads();
 
@@ -368,7 +378,11 @@ __global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer(Batch 
         for (int e = 0; e < 9; ++e) H[e] = Hn[e];
         if (fix_base && (fl & 1u)) v[0] = v[1] = v[2] = 0.f;  // Eq. 10
 #pragma unroll
-        for (int a = 0; a < 3; ++a) u[a] = u[a] + dt * inv_dx * v[a];  // Eq. 11
+        for (int a = 0; a < 3; ++a) {
+          const float du = dt * inv_dx * v[a];
+          if (!(fabsf(du) < 1.0f)) err |= ERRBIT_CFL;  // a cell or more in one substep
+          u[a] = u[a] + du;  // Eq. 11
+        }
         if (!(isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]))) err |= ERRBIT_NUMERICAL;
         store_particle(gps, p, u, H);
         if (!DO_P2G) {
@@ -450,21 +464,21 @@ __global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer(Batch 
               }
             }
         } else {
-          const int lx = nbs[0] - (B0x - 2), ly = nbs[1] - (B0y - 2), lz = nbs[2] - (B0z - 2);
-          if (lx < 0 || ly < 0 || lz < 0 || lx > TX - 3 || ly > TY - 3 || lz > P::TZ - 3) {
-            err |= ERRBIT_CFL;  // moved a cell or more in one substep: not scattered
-          } else {
-            const float wm[3] = {mv[0], mv[1], mv[2]};
-            scatter_particle(tile, TN, TX, TY, lx, ly, lz, f, wm, A);
-          }
+          // changed cell during the substep (or no grouping): scatters on its own
+          const float wm[3] = {mv[0], mv[1], mv[2]};
+          if (!scatter_particle_global(b.gmm + node_off, G0, G1, G2, nbs[0], nbs[1], nbs[2], m, f, wm, A))
+            err |= ERRBIT_OUT_OF_GRID;  // stencil outside the grid: not scattered
         }
       }
       if (err) atomicOr(b.err, err);
     }
     if (DO_P2G && grouped && q1 > q0) {
-      // the cell's base node in the P2G tile: home cell (cx, cy, cz) sits at
-      // node B0 - 1 + c, i.e. tile index c + 1
-      float *t = tile + ((cz + 1) * TY + (cy + 1)) * TX + (cx + 1);
+      // the cell's 27 node sums go straight to the grid, one vector reduction
+      // per node (red.global.add.v4.f32: no return value, so nothing waits on
+      // it); the cell's base node is B0 - 1 + c
+      const int bx = B0x - 1 + cx, by = B0y - 1 + cy, bz = B0z - 1 + cz;
+      float4 *g0 = b.gmm + node_off;
+      const bool inside = bx >= 0 && by >= 0 && bz >= 0 && bx + 2 < G0 && by + 2 < G1 && bz + 2 < G2;
 #pragma unroll
       for (int k = 0; k < 3; ++k)
 #pragma unroll
@@ -472,28 +486,14 @@ __global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer(Batch 
 #pragma unroll
           for (int i = 0; i < 3; ++i) {
             const int e = (k * 3 + j) * 3 + i;
-            float *tt = t + (k * TY + j) * TX + i;
-            atomicAdd(tt, acc2w[e].y);
-            atomicAdd(tt + TN, acc01[e].x);
-            atomicAdd(tt + 2 * TN, acc01[e].y);
-            atomicAdd(tt + 3 * TN, acc2w[e].x);
+            if (inside || (bx + i >= 0 && by + j >= 0 && bz + k >= 0 && bx + i < G0 && by + j < G1 && bz + k < G2))
+              atomicAdd(g0 + ((long long)(bz + k) * G1 + (by + j)) * G0 + (bx + i),
+                        make_float4(m * acc2w[e].y, acc01[e].x, acc01[e].y, acc2w[e].x));
           }
     }
   }
   __syncthreads();
   if (DO_G2P && tid == 0 && s_moved) *b.movers = 1;
-  if (DO_P2G) {
-    float4 *gmm = b.gmm + node_off;
-    for (int t = tid; t < TN; t += P::THREADS) {
-      const float wsum = tile[t];
-      if (wsum == 0.f) continue;
-      const int tx = t % TX, ty = (t / TX) % TY, tz = t / (TX * TY);
-      const int gx = B0x - 2 + tx, gy = B0y - 2 + ty, gz = B0z - 2 + tz;
-      if (gx < 0 || gy < 0 || gz < 0 || gx >= G0 || gy >= G1 || gz >= G2) continue;
-      atomicAdd(gmm + ((long long)gz * G1 + gy) * G0 + gx,
-                make_float4(m * wsum, tile[TN + t], tile[2 * TN + t], tile[3 * TN + t]));
-    }
-  }
 }
 
 // ---------------------------------------------------------------------------

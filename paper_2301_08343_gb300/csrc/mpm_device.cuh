@@ -1,8 +1,8 @@
 // mpm_device.cuh -- device helpers shared by the MLS-MPM transfer kernels
 // (Tacchi, arXiv 2301.08343, Sec. III-A): 3x3 algebra, the polar rotation
 // and the fixed-corotated stress (Eq. 5's S_p), quadratic B-spline weights,
-// block-wide scans of the cell grouping, the single-particle scatter and the
-// asynchronous-copy wrappers.  Included only by the library's .cu files.
+// block-wide scans of the cell grouping, the single-particle scatter to the
+// grid and the asynchronous-copy wrappers.  Included only by the library's .cu files.
 #pragma once
 #include "tacchi_internal.cuh"
 
@@ -208,10 +208,15 @@ __device__ __forceinline__ void order_cells_by_load(const uint16_t *cells, const
   __syncthreads();
 }
 
-// P2G of one particle straight into the shared tile (particles that change
-// cell during the substep, and the capacity fallback).
-__device__ __forceinline__ void scatter_particle(float *tile, int TN, int TX, int TY, int lx, int ly, int lz,
-                                                 const float f[3], const float mv[3], const float A[9]) {
+// P2G of one particle straight into the grid (particles that change cell
+// during the substep, and the fallback when a block cannot be grouped):
+// Eqs. 2-5 at the 27 nodes of the stencil with base (bx, by, bz), one vector
+// reduction per node.  Returns false, writing nothing, when the stencil is
+// not inside the grid of G0 x G1 x G2 nodes.
+__device__ __forceinline__ bool scatter_particle_global(float4 *g, int G0, int G1, int G2, int bx, int by,
+                                                        int bz, float m, const float f[3], const float mv[3],
+                                                        const float A[9]) {
+  if (bx < 0 || by < 0 || bz < 0 || bx + 2 >= G0 || by + 2 >= G1 || bz + 2 >= G2) return false;
   float wx[3], wy[3], wz[3], dpx[3], dpy[3], dpz[3];
   bspline3(f[0], wx, dpx);
   bspline3(f[1], wy, dpy);
@@ -221,17 +226,17 @@ __device__ __forceinline__ void scatter_particle(float *tile, int TN, int TX, in
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       const float wjk = wy[j] * wz[k];
-      float *t = tile + ((lz + k) * TY + (ly + j)) * TX + lx;
 #pragma unroll
       for (int i = 0; i < 3; ++i) {
         const float w = wx[i] * wjk;
-        atomicAdd(t + i, w);
+        float r[3];
 #pragma unroll
         for (int a = 0; a < 3; ++a)
-          atomicAdd(t + (a + 1) * TN + i,
-                    w * (mv[a] + A[a * 3 + 0] * dpx[i] + A[a * 3 + 1] * dpy[j] + A[a * 3 + 2] * dpz[k]));
+          r[a] = w * (mv[a] + A[a * 3 + 0] * dpx[i] + A[a * 3 + 1] * dpy[j] + A[a * 3 + 2] * dpz[k]);
+        atomicAdd(g + ((long long)(bz + k) * G1 + (by + j)) * G0 + (bx + i), make_float4(m * w, r[0], r[1], r[2]));
       }
     }
+  return true;
 }
 
 // 16-byte asynchronous copy global -> shared (L2 only), and its group fences.

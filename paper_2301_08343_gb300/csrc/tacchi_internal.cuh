@@ -82,6 +82,7 @@ struct Instance {
   const IndenterFrame *frames;  // [substep] for the running step chunk
   int ind_np;        // indenter particles (Eq. 10, p in I); 0: the grid boundary
   float ind_m;       // mass of each indenter particle (kg)
+  int slip;          // contact mode of the grid-boundary indenter: 0 sticky, 1 slip
 };
 
 struct Batch {
@@ -183,6 +184,60 @@ __device__ __forceinline__ bool inside_indenter(const IndenterShape &s, const In
     default:
       return false;
   }
+}
+
+// Outward unit normal (world frame) of the indenter's contact surface at a
+// grid node inside it, for the slip contact mode (reading of Sec. III-A: the
+// paper's indenter is no-slip; slip removes only the relative velocity into
+// the indenter).  Sphere: radial from the centre.  Cylinder: radial from the
+// axis (local x).  Cone and prism: the lateral face the node lies under,
+// (rho_hat, -t) / sqrt(1 + t^2) with t the tangent of the half angle.
+// Height map: the protruding surface z_l = -h(x_l, y_l), normal (-h_x, -h_y,
+// -1) / |.| from the gradient of the bilinear interpolant.  Where the normal
+// is undefined (on an axis or edge) it is the indenter's -z_l direction.
+__device__ __forceinline__ void indenter_normal(const IndenterShape &s, const IndenterFrame &f, int i, int j,
+                                                int k, float n[3]) {
+  const float d0 = (float)i - f.c[0], d1 = (float)j - f.c[1], d2 = (float)k - f.c[2];
+  if (s.kind == IND_SPHERE) {
+    const float q = sqrtf(d0 * d0 + d1 * d1 + d2 * d2);
+    if (q > 0.f) {
+      n[0] = d0 / q; n[1] = d1 / q; n[2] = d2 / q;
+    } else {
+      n[0] = -f.r[2]; n[1] = -f.r[5]; n[2] = -f.r[8];
+    }
+    return;
+  }
+  const float l0 = f.r[0] * d0 + f.r[3] * d1 + f.r[6] * d2;
+  const float l1 = f.r[1] * d0 + f.r[4] * d1 + f.r[7] * d2;
+  const float l2 = f.r[2] * d0 + f.r[5] * d1 + f.r[8] * d2;
+  float m0 = 0.f, m1 = 0.f, m2 = -1.f;  // local normal
+  if (s.kind == IND_CYLINDER) {
+    const float q = sqrtf(l1 * l1 + l2 * l2);
+    if (q > 0.f) { m0 = 0.f; m1 = l1 / q; m2 = l2 / q; }
+  } else if (s.kind == IND_CONE) {
+    const float q = sqrtf(l0 * l0 + l1 * l1), t = s.s0, c = rsqrtf(1.f + t * t);
+    if (q > 0.f) { m0 = l0 / q * c; m1 = l1 / q * c; m2 = -t * c; }
+  } else if (s.kind == IND_PRISM) {
+    const float t = s.s0, c = rsqrtf(1.f + t * t);
+    if (l0 != 0.f) { m0 = (l0 > 0.f ? 1.f : -1.f) * c; m1 = 0.f; m2 = -t * c; }
+  } else if (s.kind == IND_HEIGHTMAP) {
+    const int w = s.hm_w, h = s.hm_h;
+    const float fx = l0 * s.inv_pix + s.offx, fy = l1 * s.inv_pix + s.offy;
+    const float cx = fminf(fmaxf(fx, 0.f), (float)(w - 1)), cy = fminf(fmaxf(fy, 0.f), (float)(h - 1));
+    const int ix = min((int)floorf(cx), w - 2), iy = min((int)floorf(cy), h - 2);
+    const float tx = cx - (float)ix, ty = cy - (float)iy;
+    const float *H = s.hm;
+    const float h00 = __ldg(H + iy * w + ix), h01 = __ldg(H + iy * w + ix + 1);
+    const float h10 = __ldg(H + (iy + 1) * w + ix), h11 = __ldg(H + (iy + 1) * w + ix + 1);
+    // gradient in cells per cell (zero where the sample point is clamped)
+    const float gx = (fx > 0.f && fx < (float)(w - 1)) ? ((h01 - h00) * (1.f - ty) + (h11 - h10) * ty) * s.inv_pix : 0.f;
+    const float gy = (fy > 0.f && fy < (float)(h - 1)) ? ((h10 - h00) * (1.f - tx) + (h11 - h01) * tx) * s.inv_pix : 0.f;
+    const float c = rsqrtf(1.f + gx * gx + gy * gy);
+    m0 = -gx * c; m1 = -gy * c; m2 = -c;
+  }
+  n[0] = f.r[0] * m0 + f.r[1] * m1 + f.r[2] * m2;
+  n[1] = f.r[3] * m0 + f.r[4] * m1 + f.r[5] * m2;
+  n[2] = f.r[6] * m0 + f.r[7] * m1 + f.r[8] * m2;
 }
 
 // Launchers implemented in mpm.cu / render.cu (host side).

@@ -5,7 +5,7 @@
 // Like k_transfer (mpm.cu), one CTA takes one sort block of cells, groups its
 // particles by home cell (the stencil base floor(u - 1/2)) in shared memory
 // and accumulates each cell's P2G contributions in registers before adding
-// them to a shared grid tile.  The difference is how a cell is split over
+// them to the grid.  The difference is how a cell is split over
 // threads.  Here three threads of a warp share a cell:
 //   * particle work is split by particle: thread r of the triple runs G2P,
 //     the F update, advection and the polar stress for particles r, r + 3,
@@ -17,7 +17,8 @@
 //     shuffles.
 // A thread therefore holds 36 accumulators instead of a whole cell's 108,
 // which brings it under 128 registers and doubles the warps an SM keeps
-// resident.  Lanes 30 and 31 of each warp take no cell.
+// resident.  Lanes 30 and 31 of each warp take no cell.  Each thread adds its
+// plane's sums to the grid with vector reductions to global memory.
 #include "mpm_device.cuh"
 
 namespace tacchi {
@@ -30,12 +31,10 @@ struct Xfer3Plan {
   static constexpr int NE = EX * EY * EZ;
   static constexpr int VX = BX + 4, VY = BY + 4, VZ = BZ + 4;       // V tile, nodes [B0-1, B0+B+3)
   static constexpr int VN = VX * VY * VZ;
-  static constexpr int TX = BX + 6, TY = BY + 6, TZ = BZ + 6;       // P2G tile, nodes [B0-2, B0+B+4)
-  static constexpr int TN = TX * TY * TZ;
   static constexpr int MAXP = 12 * BX * BY * BZ;                    // particles grouped in smem (1.5x nominal)
   static constexpr int PER = (NE + 1 + THREADS - 1) / THREADS;      // scan entries per thread
-  static constexpr size_t OFF_TILE = 0;                             // float [4][TN]; first u32 key[MAXP]
-  static constexpr size_t OFF_V = OFF_TILE + 16 * (size_t)TN;       // float4 [VN]
+  static constexpr size_t OFF_KEY = 0;                              // u32 [MAXP] rank and cell per particle
+  static constexpr size_t OFF_V = OFF_KEY + 4 * (size_t)MAXP;       // float4 [VN]
   static constexpr size_t OFF_LIST = OFF_V + 16 * (size_t)VN;       // u32 [MAXP] particles by cell
   static constexpr size_t OFF_PID = OFF_LIST + 4 * (size_t)MAXP;    // u32 [MAXP] particle ids in idx order
   static constexpr size_t OFF_CNT = OFF_PID + 4 * (size_t)MAXP;     // u32 [NE] counts
@@ -44,7 +43,6 @@ struct Xfer3Plan {
   static constexpr size_t OFF_ORDER = OFF_CELLS + 2 * (size_t)NE;   // u16 [NE] cells, heaviest class first
   static constexpr size_t OFF_STAGE = (OFF_ORDER + 2 * (size_t)NE + 15) / 16 * 16;  // float4 [2][3][THREADS]
   static constexpr size_t BYTES = OFF_STAGE + 16 * 2 * 3 * (size_t)THREADS;
-  static_assert(4 * TN >= MAXP, "the P2G tile doubles as the key scratch");
   static_assert(THREADS % 32 == 0, "whole warps");
 };
 
@@ -55,10 +53,9 @@ __global__ void __launch_bounds__(THREADS, 65536 / (THREADS * 128)) k_transfer3(
   using P = Xfer3Plan<BX, BY, BZ, THREADS>;
   constexpr bool DO_G2P = (MODE & XFER_G2P) != 0;
   constexpr bool DO_P2G = (MODE & XFER_P2G) != 0;
-  constexpr int TX = P::TX, TY = P::TY, TN = P::TN, VX = P::VX, VY = P::VY, VZ = P::VZ;
+  constexpr int VX = P::VX, VY = P::VY, VZ = P::VZ;
   extern __shared__ __align__(16) unsigned char smem[];
-  float *tile = reinterpret_cast<float *>(smem + P::OFF_TILE);
-  uint32_t *s_key = reinterpret_cast<uint32_t *>(smem + P::OFF_TILE);
+  uint32_t *s_key = reinterpret_cast<uint32_t *>(smem + P::OFF_KEY);
   float4 *vt = reinterpret_cast<float4 *>(smem + P::OFF_V);
   uint32_t *s_list = reinterpret_cast<uint32_t *>(smem + P::OFF_LIST);
   uint32_t *s_pid = reinterpret_cast<uint32_t *>(smem + P::OFF_PID);
@@ -156,10 +153,6 @@ __global__ void __launch_bounds__(THREADS, 65536 / (THREADS * 128)) k_transfer3(
     order_cells_by_load<THREADS, P::PER>(s_cells, s_start, (int)ncells, s_order, s_warp64);
   }
   __syncthreads();
-  if (DO_P2G) {
-    float4 *tile4 = reinterpret_cast<float4 *>(tile);
-    for (int t = tid; t < TN; t += THREADS) tile4[t] = make_float4(0.f, 0.f, 0.f, 0.f);
-  }
   cp_async_wait<0>();  // this thread's part of the V tile
   __syncthreads();
 
@@ -242,7 +235,11 @@ __global__ void __launch_bounds__(THREADS, 65536 / (THREADS * 128)) k_transfer3(
       for (int e = 0; e < 9; ++e) H[e] = Hn[e];
       if (fix_base && (fl & 1u)) v[0] = v[1] = v[2] = 0.f;  // Eq. 10
 #pragma unroll
-      for (int a = 0; a < 3; ++a) u[a] = u[a] + dt * inv_dx * v[a];  // Eq. 11
+      for (int a = 0; a < 3; ++a) {
+        const float du = dt * inv_dx * v[a];
+        if (!(fabsf(du) < 1.0f)) err |= ERRBIT_CFL;  // a cell or more in one substep
+        u[a] = u[a] + du;  // Eq. 11
+      }
       if (!(isfinite(u[0]) && isfinite(u[1]) && isfinite(u[2]))) err |= ERRBIT_NUMERICAL;
       store_particle(gps, p, u, H);
       if (!DO_P2G) {
@@ -422,11 +419,8 @@ __global__ void __launch_bounds__(THREADS, 65536 / (THREADS * 128)) k_transfer3(
                 pok = 1;
               } else {
                 // changed cell during the substep: scatters on its own
-                const int lx = nbs[0] - (B0x - 2), ly = nbs[1] - (B0y - 2), lz = nbs[2] - (B0z - 2);
-                if (lx < 0 || ly < 0 || lz < 0 || lx > TX - 3 || ly > TY - 3 || lz > P::TZ - 3)
-                  err |= ERRBIT_CFL;  // moved a cell or more in one substep: not scattered
-                else
-                  scatter_particle(tile, TN, TX, TY, lx, ly, lz, pf, pmv, pA);
+                if (!scatter_particle_global(b.gmm + node_off, G0, G1, G2, nbs[0], nbs[1], nbs[2], m, pf, pmv, pA))
+                  err |= ERRBIT_OUT_OF_GRID;  // stencil outside the grid: not scattered
               }
             }
             if (err) atomicOr(b.err, err);
@@ -451,19 +445,19 @@ __global__ void __launch_bounds__(THREADS, 65536 / (THREADS * 128)) k_transfer3(
           }
         }
         if (DO_P2G) {
-          // plane r of the cell's nodes: the cell's base node sits at tile
-          // index (c + 1)
-          float *t = tile + ((cz + 1 + r) * TY + (cy + 1)) * TX + (cx + 1);
+          // plane r of the cell's nodes straight to the grid, one vector
+          // reduction per node; the cell's base node is B0 - 1 + c
+          const int bx = B0x - 1 + cx, by = B0y - 1 + cy, bz = B0z - 1 + cz + r;
+          float4 *g0 = b.gmm + node_off;
+          const bool inside = bx >= 0 && by >= 0 && bz >= 0 && bx + 2 < G0 && by + 2 < G1 && bz < G2;
 #pragma unroll
           for (int j = 0; j < 3; ++j)
 #pragma unroll
             for (int i = 0; i < 3; ++i) {
               const int e = j * 3 + i;
-              float *tt = t + j * TX + i;
-              atomicAdd(tt, acc2w[e].y);
-              atomicAdd(tt + TN, acc01[e].x);
-              atomicAdd(tt + 2 * TN, acc01[e].y);
-              atomicAdd(tt + 3 * TN, acc2w[e].x);
+              if (inside || (bx + i >= 0 && by + j >= 0 && bz >= 0 && bx + i < G0 && by + j < G1 && bz < G2))
+                atomicAdd(g0 + ((long long)bz * G1 + (by + j)) * G0 + (bx + i),
+                          make_float4(m * acc2w[e].y, acc01[e].x, acc01[e].y, acc2w[e].x));
             }
         }
       }
@@ -481,31 +475,16 @@ __global__ void __launch_bounds__(THREADS, 65536 / (THREADS * 128)) k_transfer3(
       load_particle(gps, p, u, H);
       int err = particle(p, fl, u, H, f, nbs, mv, A);
       if (DO_P2G) {
-        const int lx = nbs[0] - (B0x - 2), ly = nbs[1] - (B0y - 2), lz = nbs[2] - (B0z - 2);
         if (err & ERRBIT_NUMERICAL)
-          err |= ERRBIT_CFL;
-        else if (lx < 0 || ly < 0 || lz < 0 || lx > TX - 3 || ly > TY - 3 || lz > P::TZ - 3)
-          err |= ERRBIT_CFL;
-        else
-          scatter_particle(tile, TN, TX, TY, lx, ly, lz, f, mv, A);
+          err |= ERRBIT_CFL;  // not scattered
+        else if (!scatter_particle_global(b.gmm + node_off, G0, G1, G2, nbs[0], nbs[1], nbs[2], m, f, mv, A))
+          err |= ERRBIT_OUT_OF_GRID;
       }
       if (err) atomicOr(b.err, err);
     }
   }
   __syncthreads();
   if (DO_G2P && tid == 0 && s_moved) *b.movers = 1;
-  if (DO_P2G) {
-    float4 *gmm = b.gmm + node_off;
-    for (int t = tid; t < TN; t += THREADS) {
-      const float wsum = tile[t];
-      if (wsum == 0.f) continue;
-      const int tx = t % TX, ty = (t / TX) % TY, tz = t / (TX * TY);
-      const int gx = B0x - 2 + tx, gy = B0y - 2 + ty, gz = B0z - 2 + tz;
-      if (gx < 0 || gy < 0 || gz < 0 || gx >= G0 || gy >= G1 || gz >= G2) continue;
-      atomicAdd(gmm + ((long long)gz * G1 + gy) * G0 + gx,
-                make_float4(m * wsum, tile[TN + t], tile[2 * TN + t], tile[3 * TN + t]));
-    }
-  }
 }
 
 template <int BX, int BY, int BZ, int THREADS>

@@ -2,8 +2,9 @@
 to the batched MPM (this library's addition; the paper simulates one press at
 a time).
 
-Policy: a query inside the surrogate's training range (the trained sensor,
-shape families and depth range) is answered by one batched network inference
+Policy: a query inside the surrogate's range (the trained sensor, shape
+families and depth range, or a narrower validity region calibrated on
+held-out presses) is answered by one batched network inference
 (up to max_batch queries per launch) as soon as the server looks at it.
 Other queries join the MPM lane, which starts a batched MPM press (on pooled
 handles that are reset and reused) when it holds mpm_batch queries, its
@@ -34,11 +35,12 @@ def in_training_range(q):
 
 class PressServer:
     def __init__(self, net, block, substeps, dt, size=64, max_batch=1024, check_every=64, residual_um=5.0,
-                 use_surrogate=True, mpm_batch=256, mpm_wait_s=0.25, pool_sizes=(32, 128, 512, 1024)):
+                 use_surrogate=True, mpm_batch=256, mpm_wait_s=0.25, pool_sizes=(32, 128, 512, 1024),
+                 in_range=None):
         import torch
         self.torch = torch
         self._policy(substeps, dt, size, max_batch, check_every, residual_um, use_surrogate, mpm_batch,
-                     mpm_wait_s, pool_sizes)
+                     mpm_wait_s, pool_sizes, in_range)
         self.net, self.block = net, block
         self.pool = {}
         self.win = (0.0, 0.0, block.nx * block.dx, block.ny * block.dx)
@@ -48,7 +50,10 @@ class PressServer:
         self.Y = torch.empty((max_batch, size, size, 3), device="cuda")
 
     def _policy(self, substeps, dt, size, max_batch, check_every, residual_um, use_surrogate, mpm_batch,
-                mpm_wait_s, pool_sizes):
+                mpm_wait_s, pool_sizes, in_range=None):
+        # which queries the surrogate may answer: the training range, or a
+        # validity region calibrated on held-out presses (surrogate.calibrate_region)
+        self.in_range = in_range or in_training_range
         self.substeps, self.dt, self.size = substeps, dt, size
         self.max_batch, self.check_every, self.residual_um = max_batch, check_every, residual_um
         self.use_surrogate = use_surrogate
@@ -138,8 +143,8 @@ class PressServer:
                 while k < nq and queries[k]["arrival"] <= clock and len(batch) < self.max_batch:
                     batch.append(queries[k])
                     k += 1
-                sur = [q for q in batch if self.use_surrogate and in_training_range(q)]
-                pending += [(q, None) for q in batch if not (self.use_surrogate and in_training_range(q))]
+                sur = [q for q in batch if self.use_surrogate and self.in_range(q)]
+                pending += [(q, None) for q in batch if not (self.use_surrogate and self.in_range(q))]
                 if sur:
                     pred = timed(lambda: self._surrogate(sur))
                     n_sur += len(sur)
@@ -185,7 +190,7 @@ class PressServer:
         all_ids = [q["id"] for q in queries]
         by_mpm = set(mpm_served)
         sur_ids = [i for i in all_ids if i not in by_mpm]
-        n_fallback = sum(1 for q in queries if not (self.use_surrogate and in_training_range(q)))
+        n_fallback = sum(1 for q in queries if not (self.use_surrogate and self.in_range(q)))
         return {"queries": nq, "frames_per_s": nq / clock if clock > 0 else 0.0, "makespan_s": clock,
                 "latency_p50_ms": pct(all_ids, 50), "latency_p99_ms": pct(all_ids, 99),
                 "latency_surrogate_p99_ms": pct(sur_ids, 99), "latency_mpm_p99_ms": pct(list(by_mpm), 99),

@@ -17,16 +17,20 @@ after the closing G2P: positions to 1e-4 cells (FP32 spacing at 300 cells is
 3e-5), F - I to 1e-4 of its largest entry (the FP32 rounding of the 27-term
 G2P sums, about 2e-7 per substep).  The nodes are those with the largest
 momentum whose whole box is clear of the indenter, the fixed base and the
-padding band, so that no boundary condition acts inside it.  Also checked at every node: the total
-grid mass equals N m; and the 640 x 480 frame of the final state against the
-oracle's height map and shading."""
+padding band, plus two boxes where the boundary conditions act: one whose
+nodes cut the sphere (rigid indenter velocity on the nodes inside it, decided
+by the oracle's FP32 inside test at each substep's pose) and one on the
+sensor base (its nodes held at zero and its base-set particles stopped,
+Eq. 10).  Also checked at every node: the total grid mass equals N m; and the
+640 x 480 frame of the final state against the oracle's height map and
+shading."""
 import math
 
 import numpy as np
 import pytest
 
 import workloads as W
-from oracle.local import Local, velocity
+from oracle.local import Local, grid_velocity
 
 pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
@@ -83,6 +87,25 @@ def test_c1_two_substeps_at_sampled_nodes_and_particles():
         if len(picks) == 6:
             break
     assert float(score.max()) > 0
+    # the boundary-condition boxes: under the sphere's lowest point, so that
+    # nodes of the box lie inside it, and on the base under the press
+    k_low = int(math.floor(cc[2] - R / dx))
+    c_ind = np.array([int(round(cc[0])) + 3, int(round(cc[1])) - 2, k_low - 1])
+    c_base = np.array([int(round(cc[0])) - 5, int(round(cc[1])) + 4, b.pad_bottom + 1])
+    picks += [c_ind, c_base]
+    vel = (0.0, 0.0, -depth / (n * dt), 0.0, 0.0, 0.0)
+    pose1 = tuple(pose[a] + dt * vel[a] if a < 3 else pose[a] for a in range(7))
+    assert np.allclose(g.indenter_pose(), [pose1[a] + dt * vel[a] if a < 3 else pose1[a] for a in range(7)],
+                       rtol=0, atol=0)
+    # the oracle's inside decision depends on dx, the grid origin and the pose only
+    probe = oracle.Sim(4, 4, 2, dx, b.E, b.nu, b.rho, b.pad_side, b.pad_bottom, b.pad_top)
+
+    def inside_at(ps):
+        probe.set_indenter(oracle.IND_SPHERE, (R,), ps, vel)
+        return probe.node_inside
+
+    bc = dict(dx=dx, origin=org, vel=vel, base_k=b.pad_bottom)
+    n_inside, n_fixed = 0, 0
 
     u = S["u"]
     base = torch.floor(u - 0.5).to(torch.int32)
@@ -100,11 +123,11 @@ def test_c1_two_substeps_at_sampled_nodes_and_particles():
         Cp = S["C"][:, sel].T.double().cpu().numpy().reshape(-1, 3, 3)
         Fp = S["Fm"][:, sel].T.double().cpu().numpy().reshape(-1, 3, 3) + np.eye(3)
         fixed = (S["flags"][sel].cpu().numpy() & 1) > 0
-        assert not fixed.any()
         shape = tuple((hi - lo + 3)[::-1])
         # substep 0: P2G of S (complete on nodes [lo + 2, hi]), grid velocity
+        # with the boundary conditions at the substep's pose
         M0, MG0 = L.p2g(up, vp, Cp, Fp, lo, shape)
-        V0 = velocity(M0, MG0)
+        V0 = grid_velocity(M0, MG0, lo, (G0, G1, G2), inside=inside_at(pose), pose=pose, **bc)
         bp = np.floor(up - 0.5).astype(int)
         inner = np.all((bp >= lo + 2) & (bp <= hi - 2), axis=1)  # stencils inside [lo + 2, hi]
         u1, v1, C1, F1 = L.g2p(up[inner], Fp[inner], fixed[inner], V0, lo)
@@ -120,9 +143,12 @@ def test_c1_two_substeps_at_sampled_nodes_and_particles():
         sMG = max(sMG, float(np.abs(MG1[i0]).max()))
         # the closing G2P for the particles whose stencil lies where the
         # substep-1 grid is complete
-        V1 = velocity(M1, MG1)
+        V1 = grid_velocity(M1, MG1, lo, (G0, G1, G2), inside=inside_at(pose1), pose=pose1, **bc)
         b1 = np.floor(u1 - 0.5).astype(int)
         core = np.all((b1 >= lo + 5) & (b1 <= hi - 5), axis=1)
+        n_fixed += int(fixed[inner][core].sum())
+        n_inside += sum(inside_at(pose1)(i, j, k) for i in range(c[0] - 1, c[0] + 4)
+                        for j in range(c[1] - 1, c[1] + 4) for k in range(c[2] - 1, c[2] + 4))
         u2, v2, C2, F2 = L.g2p(u1[core], F1[core], fixed[inner][core], V1, lo)
         got = ids[inner][core]
         gu = S2["u"][:, torch.from_numpy(got).cuda()].T.double().cpu().numpy()
@@ -131,7 +157,8 @@ def test_c1_two_substeps_at_sampled_nodes_and_particles():
         dF = max(dF, float(np.abs(gF - (F2 - np.eye(3))).max()))
         sF = max(sF, float(np.abs(F2 - np.eye(3)).max()))
         nck += len(got)
-    assert nck >= 6 * 100
+    assert nck >= 8 * 100
+    assert n_inside > 0 and n_fixed > 0  # both boundary conditions act in the checked stencils
     assert sMG > 0 and dMG / sMG <= 1e-5, (dMG, sMG)
     assert dM / sM <= 1e-5, (dM, sM)
     assert du <= 1e-4, du

@@ -67,12 +67,13 @@ def test_cfl_violation_is_reported_and_the_handle_recovers():
     T, b, g = sensor()
     st = g.get_state()
     u0 = st["u"].clone()
-    # 150 m/s at dt = 1e-5 s and dx = 0.5 mm: three cells per substep
+    # 60 m/s at dt = 1e-5 s and dx = 0.5 mm: 1.2 cells in one substep (the
+    # particles stay inside the grid's padding, so no other error is raised)
     v = torch.zeros_like(u0)
-    v[0] = 150.0
+    v[0] = 60.0
     g.set_state(u0, v)
-    g.step(2, 1e-5)
-    assert g.status() != 0
+    g.step(1, 1e-5)
+    assert g.status() == -8  # TACCHI_ERR_CFL
     g.set_state(u0)
     g.step(20, 1e-5)
     s = g.get_state()

@@ -4,7 +4,18 @@ network (GPU, through the C ABI).
 Parameters and inputs are rounded to BF16 first, so both sides start from the
 same values; the GPU then rounds activations and activation gradients to BF16
 at every layer (8 bits of mantissa), so outputs must agree to a relative L2
-error of 3e-2 and parameter gradients to 6e-2 per tensor (cosine >= 0.995)."""
+error of 3e-2 and parameter gradients to 6e-2 per tensor (cosine >= 0.995).
+
+Every element is bounded too.  BF16's unit roundoff is u = 2^-8; an output
+passes through about nine such roundings (two per convolution of each level
+and the head), so an element's error is about 3 u = 0.012 of its tensor's RMS
+and the largest of some 10^4 elements about 4.5 times that, 0.05: outputs
+must stay within 0.10 of their tensor's RMS at every element.  Parameter
+gradients also carry the rounded activation gradients and the forward error
+entering the loss gradient (y - target), whose relative error grows where y
+and the target nearly cancel; their per-tensor L2 bound is 6e-2, and no
+element may exceed ten times that, 0.6 of the tensor's RMS (the largest
+measured is about 0.45)."""
 import numpy as np
 import pytest
 
@@ -71,6 +82,21 @@ def rel(a, b):
     return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30)
 
 
+def elementwise(a, b):
+    """Largest element error of a against b, in units of b's RMS."""
+    a, b = np.asarray(a, np.float64).ravel(), np.asarray(b, np.float64).ravel()
+    return float(np.abs(a - b).max() / max(np.sqrt(np.mean(b * b)), 1e-30))
+
+
+def check_gradients(G, Go):
+    for k in Go:
+        a, b = G[k].ravel(), Go[k].ravel()
+        cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-30))
+        assert rel(a, b) <= 6e-2, (k, rel(a, b))
+        assert cos >= 0.995, (k, cos)
+        assert elementwise(a, b) <= 0.6, (k, elementwise(a, b))
+
+
 def test_parameter_count_and_layout():
     import paper_2301_08343_gb300 as T
     net = T.SurrogateNet((32, 64, 128, 256), 2, 3, size=64, max_batch=2)
@@ -84,6 +110,7 @@ def test_forward_matches_oracle():
     y = net.forward(x).cpu().numpy()
     yo, _ = S.forward(P, x, WIDTHS)
     assert rel(y, yo) <= 3e-2
+    assert elementwise(y, yo) <= 0.10, elementwise(y, yo)
 
 
 def test_gradients_match_oracle():
@@ -92,11 +119,7 @@ def test_gradients_match_oracle():
     lo, Go = S.loss_and_grad(P, x, t, WIDTHS)
     assert abs(loss - lo) <= 3e-2 * lo
     G = unflatten(net.get_params(grads=True).astype(np.float64), WIDTHS, 2, 3)
-    for k in Go:
-        a, b = G[k].ravel(), Go[k].ravel()
-        cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-30))
-        assert rel(a, b) <= 6e-2, (k, rel(a, b))
-        assert cos >= 0.995, (k, cos)
+    check_gradients(G, Go)
 
 
 def test_four_levels_match_oracle():
@@ -109,14 +132,11 @@ def test_four_levels_match_oracle():
     y = net.forward(x).cpu().numpy()
     yo, _ = S.forward(P, x, widths)
     assert rel(y, yo) <= 3e-2
+    assert elementwise(y, yo) <= 0.10, elementwise(y, yo)
     net.gradients(x, t)
     _, Go = S.loss_and_grad(P, x, t, widths)
     G = unflatten(net.get_params(grads=True).astype(np.float64), widths, 2, 3)
-    for k in Go:
-        a, b = G[k].ravel(), Go[k].ravel()
-        cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-30))
-        assert rel(a, b) <= 6e-2, (k, rel(a, b))
-        assert cos >= 0.995, (k, cos)
+    check_gradients(G, Go)
 
 
 def test_full_size_matches_oracle():
@@ -128,14 +148,11 @@ def test_full_size_matches_oracle():
     y = net.forward(x).cpu().numpy()
     yo, _ = S.forward(P, x, widths)
     assert rel(y, yo) <= 3e-2
+    assert elementwise(y, yo) <= 0.10, elementwise(y, yo)
     net.gradients(x, t)
     _, Go = S.loss_and_grad(P, x, t, widths)
     G = unflatten(net.get_params(grads=True).astype(np.float64), widths, 2, 3)
-    for k in Go:
-        a, b = G[k].ravel(), Go[k].ravel()
-        cos = float(a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-30))
-        assert rel(a, b) <= 6e-2, (k, rel(a, b))
-        assert cos >= 0.995, (k, cos)
+    check_gradients(G, Go)
 
 
 def test_adam_steps_reduce_the_loss_and_match_the_oracle_step():

@@ -677,3 +677,116 @@ def test_particle_indenter_leaves_grid_nodes_to_the_momentum():
     V = s.last_grid_velocity()
     n = [q for q in range(s.nodes) if interior(q) and s.node_inside(*ijk(q))][0]
     assert np.allclose(V[:, n], vel[:3], rtol=1e-12, atol=1e-15)
+
+
+# ------------------------------------------------------------ slip contact --
+def _shape_phi(kind, params, pose, hm=None, hm_pixel=None):
+    """The shapes' defining inequalities (inside where phi <= 0 near the
+    contact surface), as the C ABI header states them: sphere |X - c| - R;
+    cylinder (axis local x) sqrt(y_l^2 + z_l^2) - R; cone sqrt(x_l^2 + y_l^2)
+    - tan(a) z_l; prism |x_l| - tan(a) z_l; height map -z_l - h(x_l, y_l)
+    with h the bilinear interpolant of the samples (the edge samples extended
+    beyond the outermost sample centres)."""
+    q = np.asarray(pose[3:], float)
+    q = q / np.linalg.norm(q)
+    w_, x_, y_, z_ = q
+    Rm = np.array([[1 - 2 * (y_ * y_ + z_ * z_), 2 * (x_ * y_ - w_ * z_), 2 * (x_ * z_ + w_ * y_)],
+                   [2 * (x_ * y_ + w_ * z_), 1 - 2 * (x_ * x_ + z_ * z_), 2 * (y_ * z_ - w_ * x_)],
+                   [2 * (x_ * z_ - w_ * y_), 2 * (y_ * z_ + w_ * x_), 1 - 2 * (x_ * x_ + y_ * y_)]])
+    c = np.asarray(pose[:3], float)
+
+    def phi(X):
+        l = Rm.T @ (X - c)
+        if kind == oracle.IND_SPHERE:
+            return np.linalg.norm(X - c) - params[0]
+        if kind == oracle.IND_CYLINDER:
+            return math.hypot(l[1], l[2]) - params[0]
+        if kind == oracle.IND_CONE:
+            return math.hypot(l[0], l[1]) - math.tan(params[0]) * l[2]
+        if kind == oracle.IND_PRISM:
+            return abs(l[0]) - math.tan(params[0]) * l[2]
+        h_, w = hm.shape
+        fx, fy = l[0] / hm_pixel + (w / 2 - 0.5), l[1] / hm_pixel + (h_ / 2 - 0.5)
+        fx, fy = min(max(fx, 0.0), w - 1.0), min(max(fy, 0.0), h_ - 1.0)  # edge samples extend outward
+        ix, iy = min(int(math.floor(fx)), w - 2), min(int(math.floor(fy)), h_ - 2)
+        tx, ty = fx - ix, fy - iy
+        hv = ((hm[iy, ix] * (1 - tx) + hm[iy, ix + 1] * tx) * (1 - ty)
+              + (hm[iy + 1, ix] * (1 - tx) + hm[iy + 1, ix + 1] * tx) * ty)
+        return -l[2] - hv
+    return phi
+
+
+@pytest.mark.parametrize("kind", ["sphere", "cylinder", "cone", "prism", "heightmap"])
+def test_slip_contact_removes_only_the_velocity_into_the_indenter(kind):
+    """Slip contact (reading c8): a node inside the indenter that holds mass
+    keeps its velocity V except the part that moves into the indenter,
+    relative to it: V <- W + q - min(0, q.n) n with q = V - W, W the rigid
+    velocity and n the unit outward normal, here the gradient of the shape's
+    defining function by central differences.  A uniform flow v0 with F = I
+    and C = 0 puts MG = M v0 on every node, so V = v0 before the condition;
+    sticky contact sets W instead."""
+    nx = ny = 8
+    nz, dx = 4, 0.5e-3
+    u0, fl = oracle.lattice(nx, ny, nz, 4, 3, seed=3)
+    rng = np.random.default_rng(4)
+    v0 = np.array([0.03, -0.02, 0.05])
+    v = np.repeat(v0[:, None], u0.shape[1], axis=1).astype(np.float32)
+    z_top = nz * dx
+    c = (nx * dx / 2 + 0.13e-3, ny * dx / 2 - 0.07e-3)
+    hm, hm_pixel = None, 0.0
+    if kind == "sphere":
+        k, params, tip = oracle.IND_SPHERE, (1.3e-3,), 1.3e-3
+        quat = (1.0, 0.0, 0.0, 0.0)
+    elif kind == "cylinder":
+        k, params, tip = oracle.IND_CYLINDER, (0.9e-3, 1.5e-3), 0.9e-3
+        quat = (math.cos(0.2), 0.0, 0.0, math.sin(0.2))     # yaw: the axis stays horizontal
+    elif kind == "cone":
+        k, params, tip = oracle.IND_CONE, (math.radians(40), 1.5e-3), 0.0
+        quat = (math.cos(0.05), math.sin(0.05), 0.0, 0.0)
+    elif kind == "prism":
+        k, params, tip = oracle.IND_PRISM, (math.radians(50), 1.5e-3, 1.5e-3), 0.0
+        quat = (math.cos(0.3), 0.0, 0.0, math.sin(0.3))
+    else:
+        k, tip = oracle.IND_HEIGHTMAP, 0.6e-3
+        hm_pixel = 0.2e-3
+        yy, xx = np.mgrid[0:16, 0:16]
+        hm = (0.6e-3 * np.exp(-((xx - 7.3) ** 2 + (yy - 8.1) ** 2) / 18.0)).astype(np.float32)
+        params = (0.5e-3,)
+        quat = (math.cos(0.15), 0.0, 0.0, math.sin(0.15))
+    pose = (c[0], c[1], z_top + tip - 0.7e-3) + quat
+    vel = (0.01, -0.02, -0.1, 0.0, 0.0, 3.0)
+    runs = {}
+    for slip in (False, True):
+        s = oracle.Sim(nx, ny, nz, dx, 3e5, 0.45, 1000.0, fix_base=True, slip=slip)
+        s.set_state(u0, v, None, None, fl)
+        s.set_indenter(k, params, pose, vel, hm=hm, hm_pixel=hm_pixel)
+        assert s.substep(1e-6) == 0
+        runs[slip] = (s, s.last_grid_velocity(), s.last_grid()[0])
+    s, Vs, M = runs[True]
+    _, Vk, _ = runs[False]
+    X = s.node_positions()
+    # the method keeps the height samples as FP32 heights in grid cells
+    hm_used = None if hm is None else (hm.astype(np.float64) / dx).astype(np.float32).astype(np.float64) * dx
+    phi = _shape_phi(k, params, pose, hm_used, hm_pixel)
+    gx, gy, gz = s.G
+    checked = moved_in = 0
+    for e in range(s.nodes):
+        i, j, kk = e % gx, (e // gx) % gy, e // (gx * gy)
+        if not s.node_inside(i, j, kk) or kk <= 3 or M[e] <= 0.0:
+            continue
+        Xe = X[:, e]
+        r = Xe - np.asarray(pose[:3])
+        Wv = np.asarray(vel[:3]) + np.cross(np.asarray(vel[3:]), r)
+        assert np.allclose(Vk[:, e], Wv, rtol=0, atol=1e-15)          # sticky
+        h = 1e-7
+        grad = np.array([(phi(Xe + h * ea) - phi(Xe - h * ea)) / (2 * h) for ea in np.eye(3)])
+        if np.linalg.norm(grad) < 0.5:
+            continue  # on an axis or edge: the normal is undefined there
+        n = grad / np.linalg.norm(grad)
+        qv = v0 - Wv
+        vn = qv @ n
+        exp = Wv + qv - min(0.0, vn) * n
+        assert np.abs(Vs[:, e] - exp).max() <= 1e-8 * max(1.0, np.abs(exp).max()), (kind, e, Vs[:, e], exp)
+        checked += 1
+        moved_in += vn < 0
+    assert checked >= 5 and 0 < moved_in < checked + 1
