@@ -218,6 +218,9 @@ def run_ours(args, rank, world, local_rank):
     if args.plan:
         shape, tpc = args.plan.split("/")
         sim.set_transfer(tuple(int(x) for x in shape.split("x")), int(tpc))
+    persistent = args.launch == "persistent"
+    if persistent:
+        sim.set_launch(True)
     rest = sim.get_state()
     assert rest["status"] == 0
     rest_u = rest["u"].clone()
@@ -291,13 +294,16 @@ def run_ours(args, rank, world, local_rank):
     peaks, src = measured_peaks()
     fp32 = fp32_peak()
     fused_avg_ms = prof["fused_ms"] / max(prof["fused_launches"], 1)
+    if persistent:  # no per-phase timing inside the persistent kernel: the whole substep
+        fused_avg_ms = ms / (args.steps * substeps)
     bytes_fused = BYTES_PER_PARTICLE * sim.N + BYTES_PER_NODE * sim.n_nodes
     flops_fused = FLOPS_PER_PARTICLE * sim.N
     gbs = bytes_fused / (fused_avg_ms * 1e-3) / 1e9
     tfl = flops_fused / (fused_avg_ms * 1e-3) / 1e12
     traffic = load_traffic(args.workload)
     roof = {
-        "kernel": "k_transfer (fused G2P+P2G)",
+        "kernel": ("k_persistent (whole substep: grid update, fused G2P+P2G, sort, and the step's frame)"
+                   if persistent else "k_transfer (fused G2P+P2G)"),
         "bound": "alu",
         "achieved": round(tfl, 3), "peak": round(fp32["tflops"], 2), "unit": "TFLOP/s",
         "frac": round(tfl / fp32["tflops"], 4),
@@ -313,7 +319,7 @@ def run_ours(args, rank, world, local_rank):
     share = {k: round(prof[k + "_ms"] / max(ms, 1e-9) / 1.0, 4) for k in ("grid", "fused", "edge", "sort")}
     # step graph (P2G, n x grid update, n - 1 fused, G2P, n x 3 sort kernels),
     # render (4 kernels), reset (state pack + 3 sort kernels)
-    launches = args.steps * ((5 * substeps + 1) + 4 + 4)
+    launches = args.steps * ((1 if persistent else 5 * substeps + 1) + 4 + 4)
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
@@ -323,7 +329,8 @@ def run_ours(args, rank, world, local_rank):
                                + ("3 mm sphere pressed 1 mm" if block is W.C0 else
                                   "nine procedural indenters cycled, depths 0.2-1.5 mm"),
                    "particles": sim.N, "grid_nodes": sim.n_nodes, "substeps_per_step": substeps,
-                   "image": [w, h], "sort_block": list(sim.block), "threads_per_cell": sim.threads_per_cell, "parallelism": f"replicas x{world}",
+                   "image": [w, h], "sort_block": list(sim.block), "threads_per_cell": sim.threads_per_cell,
+                   "launch": args.launch, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (particle state %.2f GB)" % (sim.N * 96 / 1e9)},
         "roofline": roof,
         "kernel_share_of_step": share,
@@ -353,15 +360,18 @@ def run_batch_bench(args, rank, world, local_rank):
     substeps = args.substeps or 200
     dt = W.C2_DT
     bt = T.TacchiBatch([b for b, _ in specs])
+    persistent = args.launch == "persistent"
     K = T.IndenterKind
     kinds = {"sphere": K.SPHERE, "cylinder": K.CYLINDER, "cone": K.CONE, "prism": K.PRISM}
     for i, (b, ind) in enumerate(specs):
         bt.set_indenter(i, kinds[ind["kind"]], ind["params"], ind["pose"], (0, 0, 0, 0, 0, 0))
     tuned = None
-    if not args.no_autotune:
+    if not args.no_autotune and not persistent:
         for i, (b, ind) in enumerate(specs):
             bt.set_indenter(i, vel=(0, 0, -ind["depth"] / (substeps * dt), 0, 0, 0))
         tuned = bt.autotune(min(32, substeps), dt)
+    if persistent:
+        bt.set_launch(True)
     hms = torch.empty((len(specs), 64, 64), device=dev)
 
     def one_step(s, host=None):
@@ -414,6 +424,8 @@ def run_batch_bench(args, rank, world, local_rank):
     e2e_value = whole_job_rate(units_all * e_steps, e2e_s)
     sizes = [b.n_particles for b, _ in all_specs]
     fused_avg = prof["fused_ms"] / max(prof["fused_launches"], 1)
+    if persistent:  # the whole substep
+        fused_avg = ms / (args.steps * substeps)
     peaks, src = measured_peaks()
     nodes = sum((b.nx + 2 * b.pad_side + 1) * (b.ny + 2 * b.pad_side + 1) * (b.nz + b.pad_bottom + b.pad_top + 1)
                 for b, _ in specs)
@@ -437,7 +449,9 @@ def run_batch_bench(args, rank, world, local_rank):
         "kernel_share_of_step": {k: round(prof[k + "_ms"] / max(ms, 1e-9), 4)
                                  for k in ("grid", "fused", "edge", "sort")},
         "fused_avg_launch_ms": fused_avg,
-        "roofline": {"kernel": "k_transfer (fused G2P+P2G)", "bound": "alu", "achieved": round(tfl, 3),
+        "launch": args.launch,
+        "roofline": {"kernel": "k_persistent (whole substep)" if persistent else "k_transfer (fused G2P+P2G)",
+                     "bound": "alu", "achieved": round(tfl, 3),
                      "peak": round(fp32["tflops"], 2), "unit": "TFLOP/s", "frac": round(tfl / fp32["tflops"], 4),
                      "peak_source": fp32["source"], "peak_nominal": fp32["nominal_tflops"], "traffic": None,
                      "hbm": {"achieved": round(gbs, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
@@ -446,7 +460,7 @@ def run_batch_bench(args, rank, world, local_rank):
                      "avg_launch_ms": round(fused_avg, 4)},
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 72 * substeps * len(specs) + 256 * len(specs),
                 "d2h_bytes_per_step": host.numel() * 4, "steps": e_steps},
-        "gpu_launches": args.steps * (5 * substeps + 1 + 3 * len(specs)),
+        "gpu_launches": args.steps * ((1 if persistent else 5 * substeps + 1) + 3 * len(specs)),
         "clocks": clk,
     }
 
@@ -833,6 +847,8 @@ def main():
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--instances", type=int, default=256, help="sensors of the batched workload")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--launch", choices=["graph", "persistent"], default="graph",
+                    help="step as CUDA graphs of kernels or as one persistent cooperative kernel per chunk")
     ap.add_argument("--plan", default="", help="transfer plan bx x by x bz / threads per cell, e.g. 8x8x4/3 "
                                                "(default: the library's)")
     args = ap.parse_args()

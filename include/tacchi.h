@@ -433,6 +433,28 @@ tacchi_status tacchi_set_block(tacchi_handle h, int bx, int by, int bz);
  * particles and drops cached graphs.  Errors: INVALID_ARG for other plans. */
 tacchi_status tacchi_set_transfer(tacchi_handle h, int bx, int by, int bz, int threads_per_cell);
 
+/* Launch form of tacchi_step (Sec. III-A's substep loop; the paper runs it
+ * as separate Taichi kernels).  GRAPH (the default): each chunk of up to 512
+ * substeps is one CUDA graph of five kernels per substep.  PERSISTENT: each
+ * chunk is one cooperative kernel that keeps every CTA resident and runs all
+ * phases (grid update, fused transfer, sort when needed) with grid-wide
+ * barriers between them; needs the 8x8x4 block with one thread per cell
+ * (INVALID_ARG otherwise; a later change of plan falls back to GRAPH).
+ * Every barrier wait is bounded (tacchi_set_barrier_wait): a CTA that gives
+ * up reports TACCHI_ERR_TIMEOUT at the next synchronising call and every CTA
+ * returns.  Synchronises.  Errors: INVALID_ARG, CUDA. */
+#define TACCHI_LAUNCH_GRAPH 0
+#define TACCHI_LAUNCH_PERSISTENT 1
+tacchi_status tacchi_set_launch(tacchi_handle h, int mode);
+
+/* Bound of the persistent step's grid-barrier waits: a CTA gives up after
+ * max_polls polls (about 0.1 us each; default 2^24), and a barrier waits for
+ * extra_arrivals CTAs beyond the grid (default 0).  A positive extra_arrivals
+ * makes every barrier wait for arrivals that never come: it exists to
+ * exercise the bounded wait, which then ends the step with
+ * TACCHI_ERR_TIMEOUT.  Errors: INVALID_ARG (max_polls < 1, extra_arrivals < 0). */
+tacchi_status tacchi_set_barrier_wait(tacchi_handle h, int64_t max_polls, int extra_arrivals);
+
 /* Number of transfer plans the autotuner tries, in this order:
  * 4x4x4/1, 8x8x4/1, 8x8x8/1, 16x8x4/1, 8x8x4/3, 4x4x4/3
  * (block shape / threads per cell). */

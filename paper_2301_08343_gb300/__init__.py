@@ -202,6 +202,14 @@ class Tacchi:
         check(lib().tacchi_set_transfer(self._h, *shape, int(threads_per_cell)), "tacchi_set_transfer")
         self.block, self.threads_per_cell = tuple(int(x) for x in shape), int(threads_per_cell)
 
+    def set_launch(self, persistent):
+        """Step as one persistent cooperative kernel per chunk (True) or as a
+        CUDA graph of kernels (False, the default)."""
+        check(lib().tacchi_set_launch(self._h, 1 if persistent else 0), "tacchi_set_launch")
+
+    def set_barrier_wait(self, max_polls, extra_arrivals=0):
+        check(lib().tacchi_set_barrier_wait(self._h, int(max_polls), int(extra_arrivals)), "tacchi_set_barrier_wait")
+
     def set_profiling(self, on=True):
         check(lib().tacchi_set_profiling(self._h, int(bool(on))), "tacchi_set_profiling")
 
@@ -401,6 +409,14 @@ class TacchiBatch:
     def set_transfer(self, shape, threads_per_cell):
         """Transfer plan: sort block (bx, by, bz) and threads sharing a cell (1 or 3)."""
         check(lib().tacchi_set_transfer(self._h, *shape, int(threads_per_cell)), "tacchi_set_transfer")
+
+    def set_launch(self, persistent):
+        """Step as one persistent cooperative kernel per chunk (True) or as a
+        CUDA graph of kernels (False, the default)."""
+        check(lib().tacchi_set_launch(self._h, 1 if persistent else 0), "tacchi_set_launch")
+
+    def set_barrier_wait(self, max_polls, extra_arrivals=0):
+        check(lib().tacchi_set_barrier_wait(self._h, int(max_polls), int(extra_arrivals)), "tacchi_set_barrier_wait")
 
     def transfer_plan(self):
         info = _lib.Info()

@@ -96,6 +96,8 @@ EXTRA_SIGNATURES = {
     "tacchi_batch_set_state": (C.c_int, [_vp, C.c_int, _vp, _vp, _vp, _vp]),
     "tacchi_set_block": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int]),
     "tacchi_set_transfer": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.c_int]),
+    "tacchi_set_launch": (C.c_int, [_vp, C.c_int]),
+    "tacchi_set_barrier_wait": (C.c_int, [_vp, C.c_int64, C.c_int]),
     "tacchi_batch_reset": (C.c_int, [_vp]),
     "tacchi_batch_displacement_map": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _dp, _vp]),
     "tacchi_batch_markers": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp]),

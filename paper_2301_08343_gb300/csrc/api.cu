@@ -209,6 +209,13 @@ struct tacchi_ctx {
   bool stepped = false;
   size_t device_bytes = 0;
 
+  // launch form of a step: a graph per chunk, or one persistent kernel
+  int launch = TACCHI_LAUNCH_GRAPH;
+  int persist_grid = 0;                 // co-resident CTAs of the persistent kernel
+  long long max_polls = 1ll << 24;      // polls of a grid barrier before TACCHI_ERR_TIMEOUT
+  unsigned extra_arrivals = 0;
+  unsigned *d_bar = nullptr;            // [4] barrier arrivals and generation, the abort word, the work counter
+
   int n_inst() const { return (int)in.size(); }
 };
 
@@ -543,6 +550,7 @@ tacchi_status apply_blocks(tacchi_ctx *c, SortBlock blk) {
   CK(cudaMemcpy(c->d_block_inst, bi.data(), sizeof(uint32_t) * bi.size(), cudaMemcpyHostToDevice));
   CK(cudaMemsetAsync(c->b.bcount, 0, sizeof(uint32_t) * c->Nblk_cap, c->stream));
   CK(prepare_transfer(blk));
+  if (c->launch == TACCHI_LAUNCH_PERSISTENT && !persistent_supported(blk)) c->launch = TACCHI_LAUNCH_GRAPH;
   CK(launch_sort(c->b, blk, 1, c->stream));
   CK(cudaMemsetAsync(c->b.movers, 0, sizeof(int), c->stream));
   CK(cudaStreamSynchronize(c->stream));
@@ -558,7 +566,7 @@ void release(tacchi_ctx *c) {
   cudaFree(c->d_ind_pts);
   cudaFree(c->d_ind_inst);
   void *bufs[] = {c->b.ps, c->b.v, c->b.C, (void *)c->b.flags, c->b.idx, c->b.key, c->b.bstart,
-                  c->b.bcount, c->b.cursor, c->b.gmm, c->b.gv, c->b.err, c->b.movers, c->d_inst,
+                  c->b.bcount, c->b.cursor, c->b.gmm, c->b.gv, c->b.err, c->b.movers, c->d_bar, c->d_inst,
                   c->d_node_offs, c->d_part_offs, c->d_block_inst, c->d_frames, c->d_surf, c->d_z0, c->d_srest,
                   c->d_u0,
                   c->d_cov, c->d_hbuf, c->d_rgb};
@@ -675,6 +683,7 @@ tacchi_status create_batch(int n, const tacchi_elastomer_desc *descs, void *stre
             dalloc(c, &c->b.bcount, blk_cap) == cudaSuccess && dalloc(c, &c->b.cursor, blk_cap) == cudaSuccess &&
             dalloc(c, &c->b.gmm, Nn) == cudaSuccess && dalloc(c, &c->b.gv, Nn) == cudaSuccess &&
             dalloc(c, &c->b.err, 1) == cudaSuccess && dalloc(c, &c->b.movers, 2) == cudaSuccess &&
+            dalloc(c, &c->d_bar, 4) == cudaSuccess &&
             dalloc(c, &c->d_inst, n) == cudaSuccess && dalloc(c, &c->d_node_offs, n) == cudaSuccess &&
             dalloc(c, &c->d_part_offs, n) == cudaSuccess && dalloc(c, &c->d_block_inst, blk_cap) == cudaSuccess &&
             dalloc(c, &c->d_frames, (size_t)n * kMaxChunk) == cudaSuccess &&
@@ -968,7 +977,7 @@ tacchi_status tacchi_step(tacchi_handle c, int n_substeps, double dt) {
   while (left > 0) {
     const int n = std::min(left, kMaxChunk);
     GraphEntry *ge = nullptr;
-    CK(graph_for(c, n, fdt, &ge));
+    if (c->launch == TACCHI_LAUNCH_GRAPH) CK(graph_for(c, n, fdt, &ge));
     // the previous upload must have left the pinned staging buffer
     CK(cudaEventSynchronize(c->stage_done));
     Instance *tab = reinterpret_cast<Instance *>(c->h_stage);
@@ -988,8 +997,14 @@ tacchi_status tacchi_step(tacchi_handle c, int n_substeps, double dt) {
     CK(cudaMemcpyAsync(c->d_frames, fr, sizeof(IndenterFrame) * (size_t)ni * n, cudaMemcpyHostToDevice,
                        c->stream));
     CK(cudaEventRecord(c->stage_done, c->stream));
-    CK(cudaGraphLaunch(ge->exec, c->stream));
-    if (ge->profiled) CK(collect_profile(c, ge));
+    if (c->launch == TACCHI_LAUNCH_PERSISTENT) {
+      CK(cudaMemsetAsync(c->d_bar, 0, sizeof(unsigned) * 4, c->stream));
+      PersistCtl ctl{c->d_bar, reinterpret_cast<int *>(c->d_bar + 2), c->max_polls, c->extra_arrivals};
+      CK(launch_persistent(c->b, c->blk, n, fdt, ctl, c->persist_grid, c->stream));
+    } else {
+      CK(cudaGraphLaunch(ge->exec, c->stream));
+      if (ge->profiled) CK(collect_profile(c, ge));
+    }
     left -= n;
   }
   c->stepped = true;
@@ -1310,6 +1325,26 @@ tacchi_status tacchi_set_transfer(tacchi_handle c, int bx, int by, int bz, int t
   return apply_blocks(c, SortBlock{bx, by, bz, threads_per_cell});
 }
 
+tacchi_status tacchi_set_launch(tacchi_handle c, int mode) {
+  if (!c || (mode != TACCHI_LAUNCH_GRAPH && mode != TACCHI_LAUNCH_PERSISTENT)) return TACCHI_ERR_INVALID_ARG;
+  if (mode == TACCHI_LAUNCH_PERSISTENT) {
+    if (!persistent_supported(c->blk)) return TACCHI_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(c->stream));
+    int grid = 0;
+    CK(prepare_persistent(c->blk, &grid));
+    c->persist_grid = grid;
+  }
+  c->launch = mode;
+  return TACCHI_OK;
+}
+
+tacchi_status tacchi_set_barrier_wait(tacchi_handle c, int64_t max_polls, int extra_arrivals) {
+  if (!c || max_polls < 1 || extra_arrivals < 0) return TACCHI_ERR_INVALID_ARG;
+  c->max_polls = max_polls;
+  c->extra_arrivals = (unsigned)extra_arrivals;
+  return TACCHI_OK;
+}
+
 tacchi_status tacchi_autotune(tacchi_handle c, int n_substeps, double dt, int best[4],
                               double ms_per_substep[TACCHI_NUM_TRANSFER_PLANS]) {
   NvtxRange range("tacchi_autotune");
@@ -1339,6 +1374,8 @@ tacchi_status tacchi_autotune(tacchi_handle c, int n_substeps, double dt, int be
   for (int i = 0; i < c->n_inst(); ++i) poses[i].assign(c->in[i].pose, c->in[i].pose + 7);
   const bool prof = c->profiling;
   c->profiling = false;
+  const int launch = c->launch;
+  c->launch = TACCHI_LAUNCH_GRAPH;  // the plans are timed in the graph form
   double best_ms = 1e300;
   int best_k = -1;
   for (int k = 0; k < TACCHI_NUM_TRANSFER_PLANS && st == TACCHI_OK; ++k) {
@@ -1364,6 +1401,7 @@ tacchi_status tacchi_autotune(tacchi_handle c, int n_substeps, double dt, int be
   }
   c->profiling = prof;
   if (st == TACCHI_OK) st = restore();
+  if (launch == TACCHI_LAUNCH_PERSISTENT && persistent_supported(c->blk)) c->launch = launch;
   for (int i = 0; i < c->n_inst(); ++i) std::copy(poses[i].begin(), poses[i].end(), c->in[i].pose);
   if (st == TACCHI_OK && best_k >= 0) st = apply_blocks(c, kPlans[best_k]);
   cudaFree(save);

@@ -17,10 +17,9 @@
 namespace tacchi {
 
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) k_grid_update(Batch b, int substep, float dt, int clear) {
-  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (n == 0) *b.movers = 0;  // the sort of the previous transfer has consumed it
-  if (n >= b.Nnodes) return;
+// Grid update of node n < Nnodes whose (M, MG) is mm.
+__device__ __forceinline__ void grid_update_node(const Batch &b, long long n, float4 mm, int substep, float dt,
+                                                 int clear) {
   const int ii = find_instance(b.node_offs, b.n_inst, n);
   const Instance &I = b.inst[ii];
   // an instance has fewer than 2^31 nodes: 32-bit index arithmetic
@@ -30,7 +29,6 @@ __global__ void __launch_bounds__(256) k_grid_update(Batch b, int substep, float
   const int i = (int)(loc - row * (unsigned)G0);
   const int k = (int)(row / (unsigned)G1);
   const int j = (int)(row - (unsigned)k * (unsigned)G1);
-  const float4 mm = b.gmm[n];
   float V0 = 0.f, V1 = 0.f, V2 = 0.f;
   if (mm.x > 0.f) {  // Eq. 6; empty nodes keep V = 0
     V0 = mm.y / mm.x + I.gdt[0] * dt;
@@ -68,6 +66,33 @@ __global__ void __launch_bounds__(256) k_grid_update(Batch b, int substep, float
   if (i < 2 || j < 2 || k < 2 || i > G0 - 3 || j > G1 - 3 || k > G2 - 3) V0 = V1 = V2 = 0.f;
   b.gv[n] = make_float4(V0, V1, V2, 0.f);
   if (clear) b.gmm[n] = make_float4(0.f, 0.f, 0.f, 0.f);
+}
+
+__global__ void __launch_bounds__(256) k_grid_update(Batch b, int substep, float dt, int clear) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n == 0) *b.movers = 0;  // the sort of the previous transfer has consumed it
+  if (n < b.Nnodes) grid_update_node(b, n, b.gmm[n], substep, dt, clear);
+}
+
+// The grid update over every node by all threads of a persistent grid, four
+// nodes' loads in flight per thread.
+__device__ __forceinline__ void grid_update_all(const Batch &b, int substep, float dt, int clear) {
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gt == 0) *b.movers = 0;
+  for (long long q0 = gt; q0 < b.Nnodes; q0 += 4 * nth) {
+    float4 mm[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long long q = q0 + u * nth;
+      mm[u] = q < b.Nnodes ? b.gmm[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const long long q = q0 + u * nth;
+      if (q < b.Nnodes) grid_update_node(b, q, mm[u], substep, dt, clear);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -109,13 +134,15 @@ struct XferPlan {
 #define TACCHI_XFER_MIN_BLOCKS 2
 #endif
 
+// The transfer of sort block gblk by the calling CTA (all its threads), in
+// dynamic shared memory smem of XferPlan::BYTES; the kernel below runs one
+// block per CTA, the persistent step one block after another.
 template <int BX, int BY, int BZ, int MODE>
-__global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer(Batch b, float dt) {
+__device__ __forceinline__ void transfer_block(const Batch &b, float dt, long long gblk, unsigned char *smem) {
   using P = XferPlan<BX, BY, BZ>;
   constexpr bool DO_G2P = (MODE & XFER_G2P) != 0;
   constexpr bool DO_P2G = (MODE & XFER_P2G) != 0;
   constexpr int VX = P::VX, VY = P::VY;
-  extern __shared__ __align__(16) unsigned char smem[];
   uint32_t *s_key = reinterpret_cast<uint32_t *>(smem + P::OFF_KEY);
   float4 *vt = reinterpret_cast<float4 *>(smem + P::OFF_V);
   uint32_t *s_list = reinterpret_cast<uint32_t *>(smem + P::OFF_LIST);
@@ -128,7 +155,6 @@ __global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer(Batch 
   __shared__ unsigned long long s_warp64[P::THREADS / 32];
   __shared__ int s_moved, s_overflow;
 
-  const long long gblk = blockIdx.x;
   const uint32_t start = b.bstart[gblk], end = b.bstart[gblk + 1];
   if (start == end) return;
   const uint32_t n = end - start;
@@ -496,6 +522,12 @@ __global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer(Batch 
   if (DO_G2P && tid == 0 && s_moved) *b.movers = 1;
 }
 
+template <int BX, int BY, int BZ, int MODE>
+__global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer(Batch b, float dt) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  transfer_block<BX, BY, BZ, MODE>(b, dt, blockIdx.x, smem);
+}
+
 // ---------------------------------------------------------------------------
 // Block of a particle: its stencil base cell floor(u - 1/2), divided by the
 // block size, clamped into the instance's block grid.
@@ -512,10 +544,11 @@ __device__ __forceinline__ uint32_t particle_block(const Batch &b, const Instanc
 // The sort kernels run on a small grid-stride grid: most substeps no particle
 // has left its block and they only read the flag and return, which must cost
 // a few microseconds, not a launch of one CTA per 256 particles.
-__global__ void __launch_bounds__(256) k_sort_keys(Batch b, SortBlock blk, int force) {
-  if (!force && *(volatile int *)b.movers == 0) return;
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long base = (long long)blockIdx.x * blockDim.x; base < b.Ntot; base += stride) {
+// The three sort passes, each run by CTAs cta, cta + ncta, ... of blockDim.x
+// threads (grid-stride over the particles; base is warp-uniform).
+__device__ __forceinline__ void sort_keys_pass(const Batch &b, SortBlock blk, long long cta, long long ncta) {
+  const long long stride = ncta * blockDim.x;
+  for (long long base = cta * blockDim.x; base < b.Ntot; base += stride) {
     const long long p = base + threadIdx.x;  // base is warp-uniform
     const bool valid = p < b.Ntot;
     uint32_t key = 0xFFFFFFFFu;
@@ -530,10 +563,15 @@ __global__ void __launch_bounds__(256) k_sort_keys(Batch b, SortBlock blk, int f
   }
 }
 
-// Exclusive scan of the block counts by one CTA of 1024 threads; also sets
-// the scatter cursors and clears the counts for the next sort.
-__global__ void __launch_bounds__(1024) k_sort_scan(Batch b, int force) {
+__global__ void __launch_bounds__(256) k_sort_keys(Batch b, SortBlock blk, int force) {
   if (!force && *(volatile int *)b.movers == 0) return;
+  sort_keys_pass(b, blk, blockIdx.x, gridDim.x);
+}
+
+// Exclusive scan of the block counts by one CTA (any size up to 1024
+// threads); also sets the scatter cursors and clears the counts for the next
+// sort.
+__device__ __forceinline__ void sort_scan_cta(const Batch &b) {
   __shared__ uint32_t warp_tot[32];
   const long long n = b.Nblk;
   const int T = blockDim.x;
@@ -576,11 +614,15 @@ __global__ void __launch_bounds__(1024) k_sort_scan(Batch b, int force) {
   }
 }
 
-__global__ void __launch_bounds__(256) k_sort_scatter(Batch b, int force) {
+__global__ void __launch_bounds__(1024) k_sort_scan(Batch b, int force) {
   if (!force && *(volatile int *)b.movers == 0) return;
-  const long long stride = (long long)gridDim.x * blockDim.x;
+  sort_scan_cta(b);
+}
+
+__device__ __forceinline__ void sort_scatter_pass(const Batch &b, long long cta, long long ncta) {
+  const long long stride = ncta * blockDim.x;
   const int lane = threadIdx.x & 31;
-  for (long long base = (long long)blockIdx.x * blockDim.x; base < b.Ntot; base += stride) {
+  for (long long base = cta * blockDim.x; base < b.Ntot; base += stride) {
     const long long p = base + threadIdx.x;
     const bool valid = p < b.Ntot;
     const uint32_t key = valid ? b.key[p] : 0xFFFFFFFFu;
@@ -593,6 +635,11 @@ __global__ void __launch_bounds__(256) k_sort_scatter(Batch b, int force) {
   }
 }
 
+__global__ void __launch_bounds__(256) k_sort_scatter(Batch b, int force) {
+  if (!force && *(volatile int *)b.movers == 0) return;
+  sort_scatter_pass(b, blockIdx.x, gridDim.x);
+}
+
 // ---------------------------------------------------------------------------
 // Indenter represented by particles (Eq. 10, p in I; Sec. III-C: initialised
 // from a point cloud of the object): each particle sits at x = c + R l on
@@ -600,8 +647,7 @@ __global__ void __launch_bounds__(256) k_sort_scatter(Batch b, int force) {
 // velocity (Eq. 4) is C = skew(w); a rigid particle carries no elastic
 // stress (Eq. 5 adds nothing).  It adds its mass and momentum to the grid
 // nodes of its stencil inside the grid (Eqs. 2-4) with vector reductions.
-__global__ void __launch_bounds__(256) k_indenter_p2g(Batch b, int substep) {
-  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+__device__ __forceinline__ void indenter_p2g_one(const Batch &b, long long q, int substep) {
   if (q >= b.Np) return;
   const Instance &I = b.inst[b.ind_inst[q]];
   const IndenterFrame f = I.frames[substep];
@@ -641,6 +687,10 @@ __global__ void __launch_bounds__(256) k_indenter_p2g(Batch b, int substep) {
                   make_float4(mw, mw * (v0 + (f.w[1] * d2 - f.w[2] * d1)), mw * (v1 + (f.w[2] * d0 - f.w[0] * d2)),
                               mw * (v2 + (f.w[0] * d1 - f.w[1] * d0))));
       }
+}
+
+__global__ void __launch_bounds__(256) k_indenter_p2g(Batch b, int substep) {
+  indenter_p2g_one(b, (long long)blockIdx.x * blockDim.x + threadIdx.x, substep);
 }
 
 cudaError_t launch_indenter_p2g(const Batch &b, int substep, cudaStream_t st) {
@@ -753,6 +803,131 @@ cudaError_t launch_transfer(const Batch &b, SortBlock blk, int mode, float dt, c
   if (blk.x == 8 && blk.y == 8 && blk.z == 8) return launch_transfer_t<8, 8, 8>(b, mode, dt, st);
   if (blk.x == 16 && blk.y == 8 && blk.z == 4) return launch_transfer_t<16, 8, 4>(b, mode, dt, st);
   return cudaErrorInvalidValue;
+}
+
+// ---------------------------------------------------------------------------
+// Persistent step: one cooperative launch runs a whole chunk of substeps
+// (grid clear, the opening P2G, then per substep the grid update, the fused
+// transfer or the closing G2P, and the sort when a particle left its block),
+// with a grid-wide barrier between phases instead of kernel boundaries.
+// Every CTA is co-resident (cooperative launch), so a barrier only waits for
+// CTAs that are running; each wait is still bounded: a CTA that polls
+// max_polls times gives up, records ERRBIT_TIMEOUT and sets the abort word,
+// and every CTA returns at its next barrier.  No asynchronous copy is in
+// flight at a barrier (each block's transfer waits for its own copies).
+__device__ __forceinline__ bool grid_barrier(const PersistCtl &c, int *err) {
+  __shared__ int s_ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    int ok = 1;
+    volatile unsigned *gen = c.bar + 1;
+    const unsigned g = *gen;
+    __threadfence();  // this CTA's writes before its arrival
+    if (atomicAdd(c.bar, 1u) == gridDim.x + c.extra - 1u) {
+      atomicExch(c.bar, 0u);
+      atomicExch(c.bar + 3, 0u);  // the next phase's blocks are taken from 0 again
+      __threadfence();
+      atomicAdd(c.bar + 1, 1u);  // release the others
+    } else {
+      long long polls = 0;
+      while (*gen == g) {
+        if (*(volatile int *)c.abort) {
+          ok = 0;
+          break;
+        }
+        if (++polls > c.max_polls) {
+          atomicOr(err, ERRBIT_TIMEOUT);
+          atomicExch(c.abort, 1);
+          ok = 0;
+          break;
+        }
+        __nanosleep(64);
+      }
+      __threadfence();
+    }
+    s_ok = ok;
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+// Transfer of every sort block by the persistent grid: each CTA takes the
+// next untaken block (an atomic counter, reset at every barrier), so that
+// blocks of uneven cost spread like the hardware scheduler would spread CTAs.
+template <int BX, int BY, int BZ, int MODE>
+__device__ __forceinline__ void transfer_all(const Batch &b, float dt, const PersistCtl &c, unsigned char *smem) {
+  __shared__ unsigned s_next;
+  for (;;) {
+    if (threadIdx.x == 0) s_next = atomicAdd(c.bar + 3, 1u);
+    __syncthreads();
+    const long long g = s_next;
+    __syncthreads();
+    if (g >= b.Nblk) break;
+    transfer_block<BX, BY, BZ, MODE>(b, dt, g, smem);
+  }
+}
+
+template <int BX, int BY, int BZ>
+__global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS)
+    k_persistent(Batch b, SortBlock blk, int n, float dt, PersistCtl c) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const long long nth = (long long)gridDim.x * blockDim.x;
+  const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  for (long long q = gt; q < b.Nnodes; q += nth) b.gmm[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (!grid_barrier(c, b.err)) return;
+  transfer_all<BX, BY, BZ, XFER_P2G>(b, dt, c, smem);
+  for (long long q = gt; q < b.Np; q += nth) indenter_p2g_one(b, q, 0);
+  if (!grid_barrier(c, b.err)) return;
+  for (int k = 0; k < n; ++k) {
+    const bool last = k + 1 == n;
+    grid_update_all(b, k, dt, last ? 0 : 1);
+    if (!grid_barrier(c, b.err)) return;
+    if (last) {
+      transfer_all<BX, BY, BZ, XFER_G2P>(b, dt, c, smem);
+    } else {
+      transfer_all<BX, BY, BZ, XFER_FUSED>(b, dt, c, smem);
+      for (long long q = gt; q < b.Np; q += nth) indenter_p2g_one(b, q, k + 1);
+    }
+    if (!grid_barrier(c, b.err)) return;
+    // every CTA reads the flag after the barrier and before anyone clears it
+    // (the next grid update, past the sort's barriers)
+    if (*(volatile int *)b.movers) {
+      sort_keys_pass(b, blk, blockIdx.x, gridDim.x);
+      if (!grid_barrier(c, b.err)) return;
+      if (blockIdx.x == 0) sort_scan_cta(b);
+      if (!grid_barrier(c, b.err)) return;
+      sort_scatter_pass(b, blockIdx.x, gridDim.x);
+      if (!grid_barrier(c, b.err)) return;
+    }
+  }
+}
+
+bool persistent_supported(SortBlock blk) { return blk.x == 8 && blk.y == 8 && blk.z == 4 && blk.t == 1; }
+
+cudaError_t prepare_persistent(SortBlock blk, int *grid) {
+  if (!persistent_supported(blk)) return cudaErrorInvalidValue;
+  const int smem = (int)XferPlan<8, 8, 4>::BYTES;
+  cudaError_t e = cudaFuncSetAttribute(k_persistent<8, 8, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  int dev = 0, sms = 0, per = 0;
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_persistent<8, 8, 4>, 128, smem);
+  if (e == cudaSuccess && (per < 1 || sms < 1)) e = cudaErrorInvalidConfiguration;
+  if (e == cudaSuccess) *grid = per * sms;
+  return e;
+}
+
+cudaError_t launch_persistent(const Batch &b, SortBlock blk, int n, float dt, const PersistCtl &ctl, int grid,
+                              cudaStream_t st) {
+  if (!persistent_supported(blk) || grid < 1 || n < 1) return cudaErrorInvalidValue;
+  Batch bb = b;
+  SortBlock sb = blk;
+  int nn = n;
+  float d = dt;
+  PersistCtl c = ctl;
+  void *args[] = {&bb, &sb, &nn, &d, &c};
+  return cudaLaunchCooperativeKernel((const void *)k_persistent<8, 8, 4>, dim3(grid), dim3(128), args,
+                                     XferPlan<8, 8, 4>::BYTES, st);
 }
 
 cudaError_t launch_sort(const Batch &b, SortBlock blk, int force, cudaStream_t st) {

@@ -252,6 +252,23 @@ cudaError_t launch_grid_update(const Batch &b, int substep, float dt, int clear,
 cudaError_t launch_transfer(const Batch &b, SortBlock blk, int mode, float dt, cudaStream_t st);
 cudaError_t launch_sort(const Batch &b, SortBlock blk, int force, cudaStream_t st);
 cudaError_t prepare_transfer(SortBlock blk);
+
+// Control words of the persistent step (device memory, cleared before each
+// launch) and its waiting policy.
+struct PersistCtl {
+  unsigned *bar;        // [0] arrivals at the current grid barrier, [1] its generation,
+                        // [3] the next sort block of the running transfer phase
+  int *abort;           // set by a CTA that gave up waiting; every CTA then returns
+  long long max_polls;  // polls of a barrier before giving up (ERRBIT_TIMEOUT)
+  unsigned extra;       // arrivals a barrier waits for beyond the grid: 0, except to
+                        // exercise the bounded wait (they never come)
+};
+bool persistent_supported(SortBlock blk);
+// Opts the persistent kernel into its shared memory and returns the number
+// of CTAs that can be co-resident on the device (the cooperative grid).
+cudaError_t prepare_persistent(SortBlock blk, int *grid);
+cudaError_t launch_persistent(const Batch &b, SortBlock blk, int n, float dt, const PersistCtl &ctl, int grid,
+                              cudaStream_t st);
 bool transfer3_supported(SortBlock blk);
 cudaError_t prepare_transfer3(SortBlock blk);
 cudaError_t launch_transfer3(const Batch &b, SortBlock blk, int mode, float dt, cudaStream_t st);

@@ -1,0 +1,122 @@
+"""The persistent step (one cooperative kernel per chunk of substeps, grid
+barriers between phases) against the graph form, and its bounded waits.
+
+The two forms run the same kernels' code in the same order, so their states
+differ only by the order of the floating-point reductions to the grid.  The
+waits: a barrier told to wait for an arrival that never comes gives up after
+the given number of polls in every CTA, the step reports TACCHI_ERR_TIMEOUT,
+and the handle steps normally again once the wait is restored (no fault, no
+hang: every poll loop is bounded and no asynchronous copy is in flight at a
+barrier)."""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def c0_sensor(persistent):
+    import paper_2301_08343_gb300 as T
+    b = W.C0
+    g = T.Tacchi(b.extent_m, b.dx, b.E, b.nu, b.rho, seed=b.seed, pad_side=b.pad_side,
+                 pad_bottom=b.pad_bottom, pad_top=b.pad_top)
+    g.set_launch(persistent)
+    g.set_indenter(T.IndenterKind.SPHERE, (W.C0_SPHERE_R,), W.c0_sphere_pose(), W.c0_sphere_vel())
+    return T, g
+
+
+def test_persistent_step_matches_the_graph_form():
+    _, a = c0_sensor(False)
+    _, p = c0_sensor(True)
+    a.profile(reset=True)
+    p.profile(reset=True)  # the sort at creation does not count
+    for _ in range(3):  # chunks: the press, with re-sorts as particles cross blocks
+        a.step(100, W.C0_DT)
+        p.step(100, W.C0_DT)
+    sa, sp = a.get_state(), p.get_state()
+    assert sa["status"] == 0 and sp["status"] == 0
+    assert np.abs(sa["u"].cpu().numpy() - sp["u"].cpu().numpy()).max() <= 1e-5
+    assert np.abs(sa["Fm"].cpu().numpy() - sp["Fm"].cpu().numpy()).max() <= 1e-5
+    assert np.abs(sa["u"].cpu().numpy() - a.get_state()["u"].cpu().numpy()).max() == 0.0
+    win = W.top_window(W.C0)
+    ha = a.heightmap(120, 120, win).cpu().numpy()
+    hp = p.heightmap(120, 120, win).cpu().numpy()
+    assert np.abs(ha - hp).max() <= 1e-3 * W.C0.dx
+
+
+def test_persistent_step_sorts_in_kernel():
+    """A drifting block (its particles cross sort blocks every few substeps):
+    the persistent kernel re-sorts in-kernel and stays with the graph form."""
+    import paper_2301_08343_gb300 as T
+    b = W.Block(24, 16, 6, 0.5e-3, seed=3, pad_side=12)
+    out = []
+    for persistent in (False, True):
+        g = T.Tacchi(b.extent_m, b.dx, b.E, b.nu, b.rho, seed=b.seed, pad_side=b.pad_side, fix_base=False)
+        g.set_launch(persistent)
+        u0 = g.get_state()["u"].clone()
+        v = torch.zeros_like(u0)
+        v[0], v[1] = 3.0, -1.5  # 0.06 and 0.03 cells per substep
+        g.set_state(u0, v)
+        g.profile(reset=True)
+        g.step(60, 1e-5)
+        s = g.get_state()
+        assert s["status"] == 0
+        out.append((s["u"].cpu().numpy(), g.profile()["sort_runs"]))
+    (ua, na), (up, np_) = out
+    assert na > 0 and np_ > 0
+    assert np.abs(ua - up).max() <= 1e-5
+
+
+def test_persistent_batch_matches_the_graph_form():
+    import paper_2301_08343_gb300 as T
+    specs = W.c2_instances(6, seed_base=1000)
+    out = []
+    for persistent in (False, True):
+        bt = T.TacchiBatch([b for b, _ in specs])
+        bt.set_launch(persistent)
+        K = T.IndenterKind
+        kinds = {"sphere": K.SPHERE, "cylinder": K.CYLINDER, "cone": K.CONE, "prism": K.PRISM}
+        for i, (b, ind) in enumerate(specs):
+            bt.set_indenter(i, kinds[ind["kind"]], ind["params"], ind["pose"],
+                            (0, 0, -ind["depth"] / (200 * W.C2_DT), 0, 0, 0))
+        bt.step(200, W.C2_DT)
+        assert bt.status() == 0
+        out.append([bt.get_state(i)["u"].cpu().numpy() for i in range(len(specs))])
+    for a, p in zip(*out):
+        assert np.abs(a - p).max() <= 1e-4  # 200 substeps of reordered FP32 reductions
+
+
+def test_persistent_barrier_wait_is_bounded_and_the_handle_recovers():
+    T, g = c0_sensor(True)
+    u0 = g.get_state()["u"].clone()
+    g.set_barrier_wait(1 << 14, extra_arrivals=1)  # an arrival that never comes
+    g.step(5, W.C0_DT)
+    assert g.status() == -6  # TACCHI_ERR_TIMEOUT
+    g.set_barrier_wait(1 << 24, extra_arrivals=0)
+    g.set_state(u0)
+    g.step(5, W.C0_DT)
+    s = g.get_state()
+    assert s["status"] == 0
+    assert math.isfinite(float(s["u"].abs().max()))
+
+
+def test_persistent_needs_its_plan():
+    import paper_2301_08343_gb300 as T
+    from paper_2301_08343_gb300 import _lib
+    b = W.Block(8, 8, 4, 0.5e-3, seed=6)
+    g = T.Tacchi(b.extent_m, b.dx, b.E, b.nu, b.rho, seed=b.seed)
+    g.set_transfer((4, 4, 4), 1)
+    with pytest.raises(_lib.TacchiError):
+        g.set_launch(True)
