@@ -74,21 +74,24 @@ __global__ void __launch_bounds__(256) k_grid_update(Batch b, int substep, float
   if (n < b.Nnodes) grid_update_node(b, n, b.gmm[n], substep, dt, clear);
 }
 
-// The grid update over every node by all threads of a persistent grid, four
-// nodes' loads in flight per thread.
+// The grid update over every node by all threads of a persistent grid, with
+// UNR nodes' loads in flight per thread (the persistent grid has far fewer
+// threads than nodes, and the pass is bound by HBM latency otherwise; eight
+// measured no better than four).
 __device__ __forceinline__ void grid_update_all(const Batch &b, int substep, float dt, int clear) {
+  constexpr int UNR = 4;
   const long long nth = (long long)gridDim.x * blockDim.x;
   const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (gt == 0) *b.movers = 0;
-  for (long long q0 = gt; q0 < b.Nnodes; q0 += 4 * nth) {
-    float4 mm[4];
+  for (long long q0 = gt; q0 < b.Nnodes; q0 += UNR * nth) {
+    float4 mm[UNR];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < UNR; ++u) {
       const long long q = q0 + u * nth;
       mm[u] = q < b.Nnodes ? b.gmm[q] : make_float4(0.f, 0.f, 0.f, 0.f);
     }
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
+    for (int u = 0; u < UNR; ++u) {
       const long long q = q0 + u * nth;
       if (q < b.Nnodes) grid_update_node(b, q, mm[u], substep, dt, clear);
     }
@@ -354,7 +357,10 @@ __device__ __forceinline__ void transfer_block(const Batch &b, float dt, long lo
         }
         const float2 z2 = make_float2(0.f, 0.f);
         float2 vxy = z2, b0xy = z2, b1xy = z2, b2xy = z2;  // v (Eq. 7), Bm columns (Eq. 8), rows x, y
-        float vz = 0.f, b0z = 0.f, b1z = 0.f, b2z = 0.f;    // row z
+        float2 vb0z = z2, b12z = z2;                        // row z: (v, Bm col 0), (Bm cols 1, 2)
+        float2 wst[3];
+#pragma unroll
+        for (int i = 0; i < 3; ++i) wst[i] = make_float2(wx[i], wdxd[i].x);
         // home cells lie inside the V tile; clamp only as a guard
         const int vx = clampi(bs[0] - (B0x - 1), 0, VX - 3), vy = clampi(bs[1] - (B0y - 1), 0, VY - 3),
                   vz0 = clampi(bs[2] - (B0z - 1), 0, P::VZ - 3);
@@ -372,23 +378,23 @@ __device__ __forceinline__ void transfer_block(const Batch &b, float dt, long lo
             txy = __ffma2_rn(wdxd[1], make_float2(V1.x, V1.y), txy);
             sxy = __ffma2_rn(wxd[2], make_float2(V2.x, V2.y), sxy);
             txy = __ffma2_rn(wdxd[2], make_float2(V2.x, V2.y), txy);
-            const float sz = wx[0] * V0.z + wx[1] * V1.z + wx[2] * V2.z;
-            const float tz = wdxd[0].x * V0.z + wdxd[1].x * V1.z + wdxd[2].x * V2.z;
+            // z component: (sum w_i V_i.z, sum w_i (i - f_x) V_i.z) as one pair
+            float2 st = __fmul2_rn(wst[0], make_float2(V0.z, V0.z));
+            st = __ffma2_rn(wst[1], make_float2(V1.z, V1.z), st);
+            st = __ffma2_rn(wst[2], make_float2(V2.z, V2.z), st);
             const float wjk = wy[j] * wz[k];
             const float wjy = wjk * dpy[j], wjz = wjk * dpz[k];
             vxy = __ffma2_rn(make_float2(wjk, wjk), sxy, vxy);      // Eq. 7
             b0xy = __ffma2_rn(make_float2(wjk, wjk), txy, b0xy);    // Eq. 8
             b1xy = __ffma2_rn(make_float2(wjy, wjy), sxy, b1xy);
             b2xy = __ffma2_rn(make_float2(wjz, wjz), sxy, b2xy);
-            vz += wjk * sz;
-            b0z += wjk * tz;
-            b1z += wjy * sz;
-            b2z += wjz * sz;
+            vb0z = __ffma2_rn(make_float2(wjk, wjk), st, vb0z);
+            b12z = __ffma2_rn(make_float2(wjy, wjz), make_float2(st.x, st.x), b12z);
           }
-        v[0] = vxy.x; v[1] = vxy.y; v[2] = vz;
+        v[0] = vxy.x; v[1] = vxy.y; v[2] = vb0z.x;
         Bm[0] = b0xy.x; Bm[1] = b1xy.x; Bm[2] = b2xy.x;
         Bm[3] = b0xy.y; Bm[4] = b1xy.y; Bm[5] = b2xy.y;
-        Bm[6] = b0z; Bm[7] = b1z; Bm[8] = b2z;
+        Bm[6] = vb0z.y; Bm[7] = b12z.x; Bm[8] = b12z.y;
         // Eq. 9: F <- (I + dt C) F, i.e. H <- H + dt C (I + H), C = 4/dx Bm
         float Hn[9];
 #pragma unroll
@@ -853,7 +859,8 @@ __device__ __forceinline__ bool grid_barrier(const PersistCtl &c, int *err) {
 
 // Transfer of every sort block by the persistent grid: each CTA takes the
 // next untaken block (an atomic counter, reset at every barrier), so that
-// blocks of uneven cost spread like the hardware scheduler would spread CTAs.
+// blocks of uneven cost spread like the hardware scheduler would spread CTAs
+// (taking two at a time starves small grids of parallelism: measured slower).
 template <int BX, int BY, int BZ, int MODE>
 __device__ __forceinline__ void transfer_all(const Batch &b, float dt, const PersistCtl &c, unsigned char *smem) {
   __shared__ unsigned s_next;
