@@ -841,7 +841,7 @@ def main():
                     default="c1")
     ap.add_argument("--stream-s", type=float, default=0.5, help="seconds of the served query stream")
     ap.add_argument("--samples", type=int, default=20000, help="surrogate training presses")
-    ap.add_argument("--train-steps", type=int, default=12000)
+    ap.add_argument("--train-steps", type=int, default=24000)
     ap.add_argument("--substeps", type=int, default=0, help="override substeps per step")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
