@@ -50,9 +50,10 @@ UNIT = "particle-substeps/s"
 BYTES_PER_PARTICLE = 96
 BYTES_PER_NODE = 32
 # FP32 operations per particle in the fused transfer (FMA = 2), tallied from
-# the kernel source with three Newton polar iterations: G2P 641, stress 420,
+# the kernel source with one Newton step of the left-stretch square root (the
+# count up to 5% strain): G2P 641, stress 242 (135 + 107 per further step),
 # P2G 385.
-FLOPS_PER_PARTICLE = 1446
+FLOPS_PER_PARTICLE = 1268
 
 WORKLOADS = {
     # name: (block, dt, substeps per step, image)

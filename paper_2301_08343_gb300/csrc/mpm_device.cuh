@@ -1,8 +1,8 @@
 // mpm_device.cuh -- device helpers shared by the MLS-MPM transfer kernels
-// (Tacchi, arXiv 2301.08343, Sec. III-A): 3x3 algebra, the polar rotation
-// and the fixed-corotated stress (Eq. 5's S_p), quadratic B-spline weights,
-// block-wide scans of the cell grouping, the single-particle scatter to the
-// grid and the asynchronous-copy wrappers.  Included only by the library's .cu files.
+// (Tacchi, arXiv 2301.08343, Sec. III-A): 3x3 algebra, the left stretch of
+// the polar decomposition and the fixed-corotated stress (Eq. 5's S_p),
+// quadratic B-spline weights, block-wide scans of the cell grouping, the
+// single-particle scatter to the grid and the asynchronous-copy wrappers.  Included only by the library's .cu files.
 #pragma once
 #include "tacchi_internal.cuh"
 
@@ -22,72 +22,105 @@ __device__ __forceinline__ void cofactor3(const float Y[9], float c[9]) {
   c[8] = Y[0] * Y[4] - Y[1] * Y[3];
 }
 
-// Rotation R of the polar decomposition F = R S by Newton's iteration
-// X <- (X + X^{-T}) / 2 (Higham 1986), carried in the form Y = X - I so that
-// R - I keeps its relative precision near the rest state.  With
-// X = I + Y:  det X = 1 + tr Y + m2(Y) + det Y  and
-// cof X = (1 + tr Y) I - Y^T + cof Y, hence
-// X^{-T} - I = [ -(m2 + det Y) I - Y^T + cof Y ] / det X.
-// Input H = F - I; output Y = R - I.
-__device__ __forceinline__ void polar_rotation_delta(const float H[9], float Y[9]) {
-  float hmag = 0.f;
+// Symmetric 3x3 matrices are held as their six entries (00, 11, 22, 01, 02, 12).
+__device__ __forceinline__ void cofactor_sym(const float Y[6], float c[6]) {
+  c[0] = Y[1] * Y[2] - Y[5] * Y[5];
+  c[1] = Y[0] * Y[2] - Y[4] * Y[4];
+  c[2] = Y[0] * Y[1] - Y[3] * Y[3];
+  c[3] = Y[4] * Y[5] - Y[3] * Y[2];
+  c[4] = Y[3] * Y[5] - Y[4] * Y[1];
+  c[5] = Y[3] * Y[4] - Y[0] * Y[5];
+}
+
+// Entries (00, 11, 22, 01, 02, 12) of S + P Z for symmetric P and Z that
+// commute (polynomials in one matrix), so that P Z is symmetric too.
+__device__ __forceinline__ void sym_mul_add(const float P[6], const float Z[6], const float S[6], float R[6]) {
+  R[0] = S[0] + P[0] * Z[0] + P[3] * Z[3] + P[4] * Z[4];
+  R[1] = S[1] + P[3] * Z[3] + P[1] * Z[1] + P[5] * Z[5];
+  R[2] = S[2] + P[4] * Z[4] + P[5] * Z[5] + P[2] * Z[2];
+  R[3] = S[3] + P[0] * Z[3] + P[3] * Z[1] + P[4] * Z[5];
+  R[4] = S[4] + P[0] * Z[4] + P[3] * Z[5] + P[4] * Z[2];
+  R[5] = S[5] + P[3] * Z[4] + P[1] * Z[5] + P[5] * Z[2];
+}
+
+// Left stretch V = (F F^T)^{1/2} of the polar decomposition F = V R, from
+// H = F - I, carried as Y = V - I with B = F F^T = I + P so that both keep
+// their relative precision near the rest state.  P = H + H^T + H H^T.
+// Start: the series I + P/2 - P^2/8 (error about |P|^3 / 16) while |P| is
+// small, else Newton's first iterate (I + B) / 2 (positive definite for any
+// nonsingular F).  Then Newton's iteration V <- (V + B V^{-1}) / 2 for the
+// square root of B (Higham, Functions of Matrices, Sec. 6.3): every iterate
+// is a polynomial in B, so the products stay symmetric, and the error in each
+// eigenvalue goes as e <- e^2 / (2 v).  With V = I + Y:
+// det V = 1 + tr Y + m2(Y) + det Y = 1 + d,  V^{-1} - I = [ -(m2 + det Y) I - Y + cof Y ] / (1 + d) = Z,
+// B V^{-1} = I + P + Z + P Z,  hence  Y <- (Y + P + Z + P Z) / 2.
+// Output P and Y; the stress needs no rotation.
+__device__ __forceinline__ void left_stretch_delta(const float H[9], float P[6], float Y[6]) {
+  P[0] = 2.0f * H[0] + (H[0] * H[0] + H[1] * H[1] + H[2] * H[2]);
+  P[1] = 2.0f * H[4] + (H[3] * H[3] + H[4] * H[4] + H[5] * H[5]);
+  P[2] = 2.0f * H[8] + (H[6] * H[6] + H[7] * H[7] + H[8] * H[8]);
+  P[3] = (H[1] + H[3]) + (H[0] * H[3] + H[1] * H[4] + H[2] * H[5]);
+  P[4] = (H[2] + H[6]) + (H[0] * H[6] + H[1] * H[7] + H[2] * H[8]);
+  P[5] = (H[5] + H[7]) + (H[3] * H[6] + H[4] * H[7] + H[5] * H[8]);
+  float pmag = 0.f;
 #pragma unroll
-  for (int e = 0; e < 9; ++e) {
-    Y[e] = H[e];
-    hmag = fmaxf(hmag, fabsf(H[e]));
-  }
+  for (int e = 0; e < 6; ++e) pmag = fmaxf(pmag, fabsf(P[e]));
+  float PP[6];
+  const float zero[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  sym_mul_add(P, P, zero, PP);
+  const bool series = pmag < 0.5f;
+#pragma unroll
+  for (int e = 0; e < 6; ++e) Y[e] = series ? fmaf(-0.125f, PP[e], 0.5f * P[e]) : 0.5f * P[e];
   // Newton converges quadratically: with |Y_{k+1} - Y_k| = e the next error is
-  // about e^2 / 2, below 1e-7 of the strain scale once e^2 <= 2e-7 |H|.
-  const float tol2 = 2e-7f * hmag;
+  // about e^2 / 2, below 5e-8 of the strain scale |P| once e^2 <= 1e-7 |P|.
+  // The series start alone is that close once (3 |P|)^3 / 16 <= 5e-8 |P|.
+  const float tol2 = 1e-7f * pmag;
+  if (series && pmag * pmag <= 2.9e-8f) return;
 #pragma unroll 1
   for (int it = 0; it < 12; ++it) {
-    float c[9];
-    cofactor3(Y, c);
-    const float m2 = c[0] + c[4] + c[8];
-    const float dY = Y[0] * c[0] + Y[1] * c[1] + Y[2] * c[2];
-    const float d = (Y[0] + Y[4] + Y[8]) + m2 + dY;
+    float c[6];
+    cofactor_sym(Y, c);
+    const float m2 = c[0] + c[1] + c[2];
+    const float dY = Y[0] * c[0] + Y[3] * c[3] + Y[4] * c[4];
+    const float d = (Y[0] + Y[1] + Y[2]) + m2 + dY;
     // approximate reciprocal: the iteration corrects its own rounding
     const float inv = __fdividef(1.0f, 1.0f + d);
     const float s = -(m2 + dY);
-    float Yn[9];
+    float Z[6], BZ[6];
+#pragma unroll
+    for (int e = 0; e < 6; ++e) Z[e] = ((e < 3 ? s : 0.f) + (c[e] - Y[e])) * inv;
+    sym_mul_add(P, Z, Z, BZ);  // B V^{-1} - I - P = Z + P Z
     float diff = 0.f;
 #pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        const float Z = ((r == q ? s : 0.f) - Y[q * 3 + r] + c[r * 3 + q]) * inv;
-        Yn[r * 3 + q] = 0.5f * (Y[r * 3 + q] + Z);
-        diff = fmaxf(diff, fabsf(Yn[r * 3 + q] - Y[r * 3 + q]));
-      }
-#pragma unroll
-    for (int e = 0; e < 9; ++e) Y[e] = Yn[e];
+    for (int e = 0; e < 6; ++e) {
+      const float yn = 0.5f * ((Y[e] + P[e]) + BZ[e]);
+      diff = fmaxf(diff, fabsf(yn - Y[e]));
+      Y[e] = yn;
+    }
     if (!(diff * diff > tol2)) break;
   }
 }
 
 // Elasticity term S_p of Eq. 5 as the fixed-corotated Kirchhoff stress
-// tau = 2 mu (F - R) F^T + lambda J (J - 1) I, from H = F - I.
+// tau = 2 mu (F - R) F^T + lambda J (J - 1) I, from H = F - I.  With
+// F = V R:  (F - R) F^T = F F^T - R R^T V = B - V, so
+// tau = 2 mu (P - Y) + lambda J (J - 1) I  (symmetric; no rotation needed).
 // Returns J - 1 (computed as tr H + m2(H) + det H).
 __device__ __forceinline__ float kirchhoff_stress(const float H[9], float mu, float la, float tau[9]) {
-  float Y[9];
-  polar_rotation_delta(H, Y);
+  float P[6], Y[6];
+  left_stretch_delta(H, P, Y);
   float c[9];
   cofactor3(H, c);
   const float Jm1 = (H[0] + H[4] + H[8]) + (c[0] + c[4] + c[8]) + (H[0] * c[0] + H[1] * c[1] + H[2] * c[2]);
   const float J = 1.0f + Jm1;
-  float D[9];
-#pragma unroll
-  for (int e = 0; e < 9; ++e) D[e] = H[e] - Y[e];  // F - R
   const float pr = la * J * Jm1;
   const float tm = 2.0f * mu;
-#pragma unroll
-  for (int r = 0; r < 3; ++r)
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      // (D (I + H)^T)_{rq} = D_rq + sum_k D_rk H_qk
-      float t = D[r * 3 + q] + D[r * 3 + 0] * H[q * 3 + 0] + D[r * 3 + 1] * H[q * 3 + 1] + D[r * 3 + 2] * H[q * 3 + 2];
-      tau[r * 3 + q] = tm * t + (r == q ? pr : 0.f);
-    }
+  tau[0] = tm * (P[0] - Y[0]) + pr;
+  tau[4] = tm * (P[1] - Y[1]) + pr;
+  tau[8] = tm * (P[2] - Y[2]) + pr;
+  tau[1] = tau[3] = tm * (P[3] - Y[3]);
+  tau[2] = tau[6] = tm * (P[4] - Y[4]);
+  tau[5] = tau[7] = tm * (P[5] - Y[5]);
   return Jm1;
 }
 
