@@ -249,7 +249,10 @@ __device__ __forceinline__ void order_cells_by_load(const uint16_t *cells, const
 __device__ __forceinline__ bool scatter_particle_global(float4 *g, int G0, int G1, int G2, int bx, int by,
                                                         int bz, float m, const float f[3], const float mv[3],
                                                         const float A[9]) {
-  if (bx < 0 || by < 0 || bz < 0 || bx + 2 >= G0 || by + 2 >= G1 || bz + 2 >= G2) return false;
+  // compared against G - 3, not as b + 2 >= G: a position far outside the grid
+  // (a run that has already failed its CFL check) saturates floor() at INT_MAX,
+  // where b + 2 would wrap negative and pass
+  if (bx < 0 || by < 0 || bz < 0 || bx > G0 - 3 || by > G1 - 3 || bz > G2 - 3) return false;
   float wx[3], wy[3], wz[3], dpx[3], dpy[3], dpz[3];
   bspline3(f[0], wx, dpx);
   bspline3(f[1], wy, dpy);

@@ -40,11 +40,17 @@ __global__ void __launch_bounds__(256) k_hm_splat(HeightmapArgs a) {
   // rest top plane plus the particle's vertical displacement (metres)
   const float h = a.z_top + a.dx * (uz - a.z0[s]);
   if (!(isfinite(ux) && isfinite(uy) && isfinite(h))) return;
-  // conservative pixel box of the disc of radius 1/2 cell; the exact test decides
-  int c0 = (int)floorf((ux - 0.5f - a.A0X) / a.SX) - 1;
-  int c1 = (int)ceilf((ux + 0.5f - a.A0X) / a.SX) + 1;
-  int r0 = (int)floorf((uy - 0.5f - a.A0Y) / a.SY) - 1;
-  int r1 = (int)ceilf((uy + 0.5f - a.A0Y) / a.SY) + 1;
+  // conservative pixel box of the disc of radius 1/2 cell; the exact test decides.
+  // The box edges are clamped just outside the image before they become
+  // integers, so a position far outside it cannot overflow them.
+  const float bx0 = fminf(fmaxf((ux - 0.5f - a.A0X) / a.SX, -2.f), (float)a.w + 1.f);
+  const float bx1 = fminf(fmaxf((ux + 0.5f - a.A0X) / a.SX, -2.f), (float)a.w + 1.f);
+  const float by0 = fminf(fmaxf((uy - 0.5f - a.A0Y) / a.SY, -2.f), (float)a.h + 1.f);
+  const float by1 = fminf(fmaxf((uy + 0.5f - a.A0Y) / a.SY, -2.f), (float)a.h + 1.f);
+  int c0 = (int)floorf(bx0) - 1;
+  int c1 = (int)ceilf(bx1) + 1;
+  int r0 = (int)floorf(by0) - 1;
+  int r1 = (int)ceilf(by1) + 1;
   c0 = max(c0, 0);
   r0 = max(r0, 0);
   c1 = min(c1, a.w - 1);
