@@ -116,20 +116,28 @@ struct XferPlan {
   static constexpr int NE = EX * EY * EZ;
   static constexpr int VX = BX + 4, VY = BY + 4, VZ = BZ + 4;       // V tile, nodes [B0-1, B0+B+3)
   static constexpr int VN = VX * VY * VZ;
-  static constexpr int MAXP = 12 * BX * BY * BZ;                    // particles grouped in smem (1.5x nominal)
+  // particles grouped in shared memory: 1.5x the nominal 8 per cell, 1.25x
+  // for blocks of 512 cells or more (a fuller block takes the ungrouped path)
+  static constexpr int MAXP = (BX * BY * BZ >= 512 ? 10 : 12) * BX * BY * BZ;
   static constexpr int PER = (NE + 1 + THREADS - 1) / THREADS;      // scan entries per thread
+  // per-thread staging of the next particle record: float4 [2 slots][3][THREADS]
+  static constexpr size_t STAGE_BYTES = 16 * 2 * 3 * (size_t)THREADS;
   // byte offsets in dynamic shared memory
   static constexpr size_t OFF_KEY = 0;                              // u32 [MAXP] rank and cell per particle
-  static constexpr size_t OFF_V = OFF_KEY + 4 * (size_t)MAXP;       // float4 [VN]
+  static constexpr size_t OFF_PID = OFF_KEY + 4 * (size_t)MAXP;     // u32 [MAXP] particle ids in idx order
+  static constexpr size_t OFF_V = (OFF_PID + 4 * (size_t)MAXP + 15) / 16 * 16;  // float4 [VN]
   static constexpr size_t OFF_LIST = OFF_V + 16 * (size_t)VN;       // u32 [MAXP] particles by cell
-  static constexpr size_t OFF_PID = OFF_LIST + 4 * (size_t)MAXP;    // u32 [MAXP] particle ids in idx order
-  static constexpr size_t OFF_CNT = OFF_PID + 4 * (size_t)MAXP;     // u32 [NE] count, then start
+  static constexpr size_t OFF_CNT = OFF_LIST + 4 * (size_t)MAXP;    // u32 [NE] count, then start
   static constexpr size_t OFF_START = OFF_CNT + 4 * (size_t)NE;     // u32 [NE + 1]
   static constexpr size_t OFF_CELLS = OFF_START + 4 * (size_t)(NE + 1);  // u16 [NE] non-empty cells
-  // per-thread staging of the next particle record: float4 [2 slots][3][THREADS]
   static constexpr size_t OFF_ORDER = OFF_CELLS + 2 * (size_t)NE;   // u16 [NE] cells, heaviest class first
-  static constexpr size_t OFF_STAGE = (OFF_ORDER + 2 * (size_t)NE + 15) / 16 * 16;
-  static constexpr size_t BYTES = OFF_STAGE + 16 * 2 * 3 * (size_t)THREADS;
+  static constexpr size_t END = (OFF_ORDER + 2 * (size_t)NE + 15) / 16 * 16;
+  // the keys and ids are dead once the cell lists are built, before the first
+  // record is staged: the staging slots reuse their space when it is large enough
+  // (61 KB instead of 75 KB for 8 x 8 x 4, leaving more of the SM's memory as L1)
+  static constexpr bool STAGE_IN_KEYS = 8 * (size_t)MAXP >= STAGE_BYTES;
+  static constexpr size_t OFF_STAGE = STAGE_IN_KEYS ? OFF_KEY : END;
+  static constexpr size_t BYTES = STAGE_IN_KEYS ? END : END + STAGE_BYTES;
 };
 
 // Resident transfer CTAs per SM the register allocation is bounded for.
