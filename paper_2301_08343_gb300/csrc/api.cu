@@ -565,7 +565,7 @@ void release(tacchi_ctx *c) {
     if (h.d_hm) cudaFree(h.d_hm);
   cudaFree(c->d_ind_pts);
   cudaFree(c->d_ind_inst);
-  void *bufs[] = {c->b.ps, c->b.v, c->b.C, (void *)c->b.flags, c->b.idx, c->b.key, c->b.bstart,
+  void *bufs[] = {c->b.ps, c->b.v, c->b.C, (void *)c->b.flags, c->b.idx, c->b.hcell, c->b.key, c->b.bstart,
                   c->b.bcount, c->b.cursor, c->b.gmm, c->b.gv, c->b.err, c->b.movers, c->d_bar, c->d_inst,
                   c->d_node_offs, c->d_part_offs, c->d_block_inst, c->d_frames, c->d_surf, c->d_z0, c->d_srest,
                   c->d_u0,
@@ -678,7 +678,8 @@ tacchi_status create_batch(int n, const tacchi_elastomer_desc *descs, void *stre
   const long long N = c->Ntot, Nn = c->Nnodes;
   bool ok = dalloc(c, &c->b.ps, 3 * N) == cudaSuccess &&
             dalloc(c, &c->b.v, 3 * N) == cudaSuccess && dalloc(c, &c->b.C, 9 * N) == cudaSuccess &&
-            dalloc(c, (uint8_t **)&c->b.flags, N) == cudaSuccess && dalloc(c, &c->b.idx, N) == cudaSuccess &&
+            dalloc(c, (uint8_t **)&c->b.flags, N) == cudaSuccess && dalloc(c, &c->b.idx, N + 4) == cudaSuccess &&
+            dalloc(c, &c->b.hcell, N + 8) == cudaSuccess &&
             dalloc(c, &c->b.key, N) == cudaSuccess && dalloc(c, &c->b.bstart, blk_cap + 1) == cudaSuccess &&
             dalloc(c, &c->b.bcount, blk_cap) == cudaSuccess && dalloc(c, &c->b.cursor, blk_cap) == cudaSuccess &&
             dalloc(c, &c->b.gmm, Nn) == cudaSuccess && dalloc(c, &c->b.gv, Nn) == cudaSuccess &&

@@ -208,34 +208,27 @@ __device__ __forceinline__ void transfer_block(const Batch &b, float dt, long lo
   }
   __syncthreads();
   if (n <= (uint32_t)P::MAXP) {
-    // GB particles per thread per round, so that their id and position loads
-    // are all in flight together
+    // GB slots per thread per round, so that their id and home-cell loads are
+    // all in flight together (two contiguous reads, no gather of positions)
     constexpr int GB = 16;
+    static_assert(P::NE < kNotHome, "home cells must fit below the not-home mark");
+    const uint16_t *__restrict__ ghc = b.hcell + start;
     for (uint32_t l0 = 0; l0 < n; l0 += GB * P::THREADS) {
-      uint32_t pp[GB];
-      float4 px[GB];
+      uint32_t pp[GB], hc[GB];
 #pragma unroll
       for (int g = 0; g < GB; ++g) {
         const uint32_t l = l0 + g * P::THREADS + tid;
         pp[g] = l < n ? b.idx[start + l] : 0u;
-      }
-#pragma unroll
-      for (int g = 0; g < GB; ++g) {
-        const uint32_t l = l0 + g * P::THREADS + tid;
-        px[g] = l < n ? load_position(gps, pp[g]) : make_float4(0.f, 0.f, 0.f, 0.f);
+        hc[g] = l < n ? (uint32_t)ghc[l] : (uint32_t)kNotHome;
       }
 #pragma unroll
       for (int g = 0; g < GB; ++g) {
         const uint32_t l = l0 + g * P::THREADS + tid;
         if (l >= n) continue;
         s_pid[l] = pp[g];
-        const int ex = (int)floorf(px[g].x - 0.5f) - (B0x - 1);
-        const int ey = (int)floorf(px[g].y - 0.5f) - (B0y - 1);
-        const int ez = (int)floorf(px[g].z - 0.5f) - (B0z - 1);
         uint32_t key = 0xFFFFFFFFu;
-        if (ex >= 0 && ey >= 0 && ez >= 0 && ex < P::EX && ey < P::EY && ez < P::EZ) {
-          const uint32_t c = (uint32_t)((ez * P::EY + ey) * P::EX + ex);
-          key = (atomicAdd(s_cnt + c, 1u) << 12) | c;  // rank, cell (< 4096)
+        if (hc[g] < (uint32_t)P::NE) {
+          key = (atomicAdd(s_cnt + hc[g], 1u) << 12) | hc[g];  // rank, cell (< 4096)
         } else {
           s_overflow = 1;  // not at home: the sort invariant is broken
         }
@@ -444,9 +437,18 @@ __device__ __forceinline__ void transfer_block(const Batch &b, float dt, long lo
       for (int a = 0; a < 3; ++a) nbs[a] = (int)floorf(u[a] - 0.5f);
       if (nbs[0] < 2 || nbs[1] < 2 || nbs[2] < 2 || nbs[0] > G0 - 5 || nbs[1] > G1 - 5 || nbs[2] > G2 - 5)
         err |= ERRBIT_OUT_OF_GRID;
-      if (DO_G2P && (nbs[0] < B0x - 1 || nbs[0] > B0x + BX || nbs[1] < B0y - 1 || nbs[1] > B0y + BY ||
-                     nbs[2] < B0z - 1 || nbs[2] > B0z + BZ))
-        s_moved = 1;  // left its home cells: re-sort after this transfer
+      const bool home = nbs[0] >= B0x - 1 && nbs[0] <= B0x + BX && nbs[1] >= B0y - 1 && nbs[1] <= B0y + BY &&
+                        nbs[2] >= B0z - 1 && nbs[2] <= B0z + BZ;
+      if (DO_G2P && !home) s_moved = 1;  // left its home cells: re-sort after this transfer
+      // the next transfer groups the block from these: slot q of the block's
+      // idx range (its cell order now, when grouped) and the new home cell
+      {
+        const uint16_t hc = home ? (uint16_t)(((nbs[2] - (B0z - 1)) * P::EY + (nbs[1] - (B0y - 1))) * P::EX +
+                                              (nbs[0] - (B0x - 1)))
+                                 : kNotHome;
+        if (grouped) b.idx[start + q] = p;
+        b.hcell[start + q] = hc;
+      }
 
       if (DO_P2G) {
         // Eqs. 2-5 with S_p = tau and the affine term of Eq. 4 carrying m_p:
@@ -633,7 +635,22 @@ __global__ void __launch_bounds__(1024) k_sort_scan(Batch b, int force) {
   sort_scan_cta(b);
 }
 
-__device__ __forceinline__ void sort_scatter_pass(const Batch &b, long long cta, long long ncta) {
+// Home cell of particle p in sort block key (see Batch::hcell), decided in
+// floats so that a position far outside the grid cannot overflow an integer.
+__device__ __forceinline__ uint16_t sort_home_cell(const Batch &b, SortBlock blk, uint32_t key, long long p) {
+  const Instance &I = b.inst[b.block_inst[key]];
+  const long long lb = (long long)key - I.block_off;
+  const int nb0 = I.nb[0], nb1 = I.nb[1];
+  const float o0 = (float)((int)(lb % nb0) * blk.x - 1), o1 = (float)((int)((lb / nb0) % nb1) * blk.y - 1),
+              o2 = (float)((int)(lb / ((long long)nb0 * nb1)) * blk.z - 1);
+  const float4 u = load_position(b.ps, p);
+  const float ex = floorf(u.x - 0.5f) - o0, ey = floorf(u.y - 0.5f) - o1, ez = floorf(u.z - 0.5f) - o2;
+  const int EX = blk.x + 2, EY = blk.y + 2, EZ = blk.z + 2;
+  if (!(ex >= 0.f && ey >= 0.f && ez >= 0.f && ex < (float)EX && ey < (float)EY && ez < (float)EZ)) return kNotHome;
+  return (uint16_t)(((int)ez * EY + (int)ey) * EX + (int)ex);
+}
+
+__device__ __forceinline__ void sort_scatter_pass(const Batch &b, SortBlock blk, long long cta, long long ncta) {
   const long long stride = ncta * blockDim.x;
   const int lane = threadIdx.x & 31;
   for (long long base = cta * blockDim.x; base < b.Ntot; base += stride) {
@@ -645,13 +662,17 @@ __device__ __forceinline__ void sort_scatter_pass(const Batch &b, long long cta,
     uint32_t base_slot = 0;
     if (valid && lane == leader) base_slot = atomicAdd(b.cursor + key, (uint32_t)__popc(peers));
     base_slot = __shfl_sync(0xFFFFFFFFu, base_slot, leader);
-    if (valid) b.idx[base_slot + __popc(peers & ((1u << lane) - 1u))] = (uint32_t)p;
+    if (valid) {
+      const uint32_t slot = base_slot + __popc(peers & ((1u << lane) - 1u));
+      b.idx[slot] = (uint32_t)p;
+      b.hcell[slot] = sort_home_cell(b, blk, key, p);
+    }
   }
 }
 
-__global__ void __launch_bounds__(256) k_sort_scatter(Batch b, int force) {
+__global__ void __launch_bounds__(256) k_sort_scatter(Batch b, SortBlock blk, int force) {
   if (!force && *(volatile int *)b.movers == 0) return;
-  sort_scatter_pass(b, blockIdx.x, gridDim.x);
+  sort_scatter_pass(b, blk, blockIdx.x, gridDim.x);
 }
 
 // ---------------------------------------------------------------------------
@@ -911,7 +932,7 @@ __global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS)
       if (!grid_barrier(c, b.err)) return;
       if (blockIdx.x == 0) sort_scan_cta(b);
       if (!grid_barrier(c, b.err)) return;
-      sort_scatter_pass(b, blockIdx.x, gridDim.x);
+      sort_scatter_pass(b, SortBlock{BX, BY, BZ, 1}, blockIdx.x, gridDim.x);
       if (!grid_barrier(c, b.err)) return;
     }
   }
@@ -958,7 +979,7 @@ cudaError_t launch_sort(const Batch &b, SortBlock blk, int force, cudaStream_t s
   const unsigned gp = (unsigned)(full < 8LL * sms ? full : 8LL * sms);  // 8 CTAs of 256 fill an SM
   k_sort_keys<<<gp, 256, 0, st>>>(b, blk, force);
   k_sort_scan<<<1, 1024, 0, st>>>(b, force);
-  k_sort_scatter<<<gp, 256, 0, st>>>(b, force);
+  k_sort_scatter<<<gp, 256, 0, st>>>(b, blk, force);
   return cudaGetLastError();
 }
 

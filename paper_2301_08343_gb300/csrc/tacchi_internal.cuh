@@ -96,6 +96,11 @@ struct Batch {
   float *v, *C;
   const uint8_t *flags;
   uint32_t *idx, *key, *bstart, *bcount, *cursor;
+  // home cell of the particle at each idx slot, within its sort block's cells
+  // grown by one on every side ((ez * (BY + 2) + ey) * (BX + 2) + ex), or
+  // kNotHome; written by the sort and by every transfer that groups its block,
+  // which also leaves the block's idx slots in cell order
+  uint16_t *hcell;
   float4 *gmm, *gv;
   // indenter particles of all instances: local positions (cells) and the
   // instance of each
@@ -105,6 +110,8 @@ struct Batch {
   int *err;
   int *movers;  // [0] a particle left its block in the last transfer; [1] sorts that did work
 };
+
+constexpr uint16_t kNotHome = 0xFFFF;
 
 // Particle records (see the layout above).
 __device__ __forceinline__ void load_particle(const float4 *ps, long long p, float u[3], float H[9]) {
