@@ -219,6 +219,8 @@ def run_ours(args, rank, world, local_rank):
     if args.plan:
         shape, tpc = args.plan.split("/")
         sim.set_transfer(tuple(int(x) for x in shape.split("x")), int(tpc))
+    if args.pipeline != "default":
+        sim.set_pipeline(args.pipeline == "on")
     persistent = args.launch == "persistent"
     if persistent:
         sim.set_launch(True)
@@ -331,7 +333,7 @@ def run_ours(args, rank, world, local_rank):
                                   "nine procedural indenters cycled, depths 0.2-1.5 mm"),
                    "particles": sim.N, "grid_nodes": sim.n_nodes, "substeps_per_step": substeps,
                    "image": [w, h], "sort_block": list(sim.block), "threads_per_cell": sim.threads_per_cell,
-                   "launch": args.launch, "parallelism": f"replicas x{world}",
+                   "launch": args.launch, "pipelined": sim.pipelined, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (particle state %.2f GB)" % (sim.N * 96 / 1e9)},
         "roofline": roof,
         "kernel_share_of_step": share,
@@ -361,6 +363,8 @@ def run_batch_bench(args, rank, world, local_rank):
     substeps = args.substeps or 200
     dt = W.C2_DT
     bt = T.TacchiBatch([b for b, _ in specs])
+    if args.pipeline != "default":
+        bt.set_pipeline(args.pipeline == "on")
     persistent = args.launch == "persistent"
     K = T.IndenterKind
     kinds = {"sphere": K.SPHERE, "cylinder": K.CYLINDER, "cone": K.CONE, "prism": K.PRISM}
@@ -450,7 +454,7 @@ def run_batch_bench(args, rank, world, local_rank):
         "kernel_share_of_step": {k: round(prof[k + "_ms"] / max(ms, 1e-9), 4)
                                  for k in ("grid", "fused", "edge", "sort")},
         "fused_avg_launch_ms": fused_avg,
-        "launch": args.launch,
+        "launch": args.launch, "pipelined": bt.pipelined,
         "roofline": {"kernel": "k_persistent (whole substep)" if persistent else "k_transfer (fused G2P+P2G)",
                      "bound": "alu", "achieved": round(tfl, 3),
                      "peak": round(fp32["tflops"], 2), "unit": "TFLOP/s", "frac": round(tfl / fp32["tflops"], 4),
@@ -850,6 +854,9 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--launch", choices=["graph", "persistent"], default="graph",
                     help="step as CUDA graphs of kernels or as one persistent cooperative kernel per chunk")
+    ap.add_argument("--pipeline", choices=["default", "on", "off"], default="default",
+                    help="fused transfers by the pipelined persistent kernel or one CTA per sort block "
+                         "(default: the library's)")
     ap.add_argument("--plan", default="", help="transfer plan bx x by x bz / threads per cell, e.g. 8x8x4/3 "
                                                "(default: the library's)")
     args = ap.parse_args()

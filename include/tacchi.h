@@ -134,6 +134,7 @@ typedef struct {
   int64_t n_blocks;
   size_t device_bytes;    /* device memory held by the context */
   int threads_per_cell;   /* transfer threads sharing a cell (1 or 3) */
+  int pipelined;          /* fused transfers run pipelined (tacchi_set_pipeline) */
 } tacchi_info_t;
 
 /* Create a simulator on the current CUDA device (Sec. III-A, Initialization;
@@ -447,6 +448,18 @@ tacchi_status tacchi_set_transfer(tacchi_handle h, int bx, int by, int bz, int t
 #define TACCHI_LAUNCH_PERSISTENT 1
 tacchi_status tacchi_set_launch(tacchi_handle h, int mode);
 
+/* Fused transfers of the graph form by the pipelined kernel (on = 1) or one
+ * CTA per sort block (on = 0, the default; tacchi_autotune turns it on when
+ * it times the pipelined form faster for the plan it picks).  The pipelined kernel
+ * (Sec. III-A, Eqs. 2-11, the same arithmetic) keeps two CTAs per SM resident
+ * over the sort's non-empty blocks: while a CTA runs one block's particles,
+ * bulk asynchronous copies bring the next block's particle slots, home cells
+ * and grid velocities into shared memory.  It exists for the 8x8x4 block with
+ * one thread per cell; other plans use the per-block kernel whatever the
+ * setting.  Its copy waits are bounded by tacchi_set_barrier_wait's max_polls
+ * (TACCHI_ERR_TIMEOUT).  Synchronises.  Errors: INVALID_ARG (on not 0 or 1). */
+tacchi_status tacchi_set_pipeline(tacchi_handle h, int on);
+
 /* Bound of the persistent step's grid-barrier waits: a CTA gives up after
  * max_polls polls (about 0.1 us each; default 2^24), and a barrier waits for
  * extra_arrivals CTAs beyond the grid (default 0).  A positive extra_arrivals
@@ -462,10 +475,11 @@ tacchi_status tacchi_set_barrier_wait(tacchi_handle h, int64_t max_polls, int ex
 
 /* Autotuner: times n_substeps substeps of length dt with each transfer plan
  * on the handle's current state (which it saves and restores, together with
- * the indenter poses), keeps the fastest plan and writes it to best[4]
+ * the indenter poses), a plan with a pipelined form both ways
+ * (tacchi_set_pipeline), keeps the fastest and writes its plan to best[4]
  * (host: bx, by, bz, threads per cell); ms_per_substep (host, optional,
  * TACCHI_NUM_TRANSFER_PLANS entries) receives the time per substep of each
- * plan in the order above.  Synchronises.  Errors: INVALID_ARG, CUDA, and
+ * plan in the order above (of its faster form, where both were timed).  Synchronises.  Errors: INVALID_ARG, CUDA, and
  * any device error raised while timing. */
 tacchi_status tacchi_autotune(tacchi_handle h, int n_substeps, double dt, int best[4],
                               double ms_per_substep[TACCHI_NUM_TRANSFER_PLANS]);

@@ -210,6 +210,17 @@ class Tacchi:
     def set_barrier_wait(self, max_polls, extra_arrivals=0):
         check(lib().tacchi_set_barrier_wait(self._h, int(max_polls), int(extra_arrivals)), "tacchi_set_barrier_wait")
 
+    def set_pipeline(self, on):
+        """Fused transfers by the pipelined kernel (True, the default where the
+        plan has one) or by one CTA per sort block (False)."""
+        check(lib().tacchi_set_pipeline(self._h, 1 if on else 0), "tacchi_set_pipeline")
+
+    @property
+    def pipelined(self):
+        info = _lib.Info()
+        check(lib().tacchi_info(self._h, C.byref(info)), "tacchi_info")
+        return bool(info.pipelined)
+
     def set_profiling(self, on=True):
         check(lib().tacchi_set_profiling(self._h, int(bool(on))), "tacchi_set_profiling")
 
@@ -417,6 +428,17 @@ class TacchiBatch:
 
     def set_barrier_wait(self, max_polls, extra_arrivals=0):
         check(lib().tacchi_set_barrier_wait(self._h, int(max_polls), int(extra_arrivals)), "tacchi_set_barrier_wait")
+
+    def set_pipeline(self, on):
+        """Fused transfers by the pipelined kernel (True, the default where the
+        plan has one) or by one CTA per sort block (False)."""
+        check(lib().tacchi_set_pipeline(self._h, 1 if on else 0), "tacchi_set_pipeline")
+
+    @property
+    def pipelined(self):
+        info = _lib.Info()
+        check(lib().tacchi_info(self._h, C.byref(info)), "tacchi_info")
+        return bool(info.pipelined)
 
     def transfer_plan(self):
         info = _lib.Info()

@@ -45,7 +45,7 @@ class Info(C.Structure):
     _fields_ = [("n_particles", C.c_int64), ("n_surface", C.c_int64), ("grid", C.c_int * 3),
                 ("n_nodes", C.c_int64), ("origin_m", C.c_double * 3), ("dx_m", C.c_double),
                 ("z_top_m", C.c_double), ("block", C.c_int * 3), ("n_blocks", C.c_int64),
-                ("device_bytes", C.c_size_t), ("threads_per_cell", C.c_int)]
+                ("device_bytes", C.c_size_t), ("threads_per_cell", C.c_int), ("pipelined", C.c_int)]
 
 
 class Profile(C.Structure):
@@ -98,6 +98,7 @@ EXTRA_SIGNATURES = {
     "tacchi_set_transfer": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, C.c_int]),
     "tacchi_set_launch": (C.c_int, [_vp, C.c_int]),
     "tacchi_set_barrier_wait": (C.c_int, [_vp, C.c_int64, C.c_int]),
+    "tacchi_set_pipeline": (C.c_int, [_vp, C.c_int]),
     "tacchi_batch_reset": (C.c_int, [_vp]),
     "tacchi_batch_displacement_map": (C.c_int, [_vp, C.c_int, C.c_int, C.c_int, _dp, _vp]),
     "tacchi_batch_markers": (C.c_int, [_vp, C.c_int, C.c_int, _vp, _vp]),

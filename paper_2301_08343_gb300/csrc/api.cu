@@ -212,6 +212,8 @@ struct tacchi_ctx {
   // launch form of a step: a graph per chunk, or one persistent kernel
   int launch = TACCHI_LAUNCH_GRAPH;
   int persist_grid = 0;                 // co-resident CTAs of the persistent kernel
+  int pipe = 0;                         // fused transfers by the pipelined kernel where the plan allows
+  int pipe_grid = 0;                    // its CTAs (0: the plan has no pipelined form)
   long long max_polls = 1ll << 24;      // polls of a grid barrier before TACCHI_ERR_TIMEOUT
   unsigned extra_arrivals = 0;
   unsigned *d_bar = nullptr;            // [4] barrier arrivals and generation, the abort word, the work counter
@@ -363,7 +365,11 @@ cudaError_t build_graph(tacchi_ctx *c, int n, float dt, GraphEntry *ge) {
   if (le == cudaSuccess && b.Np > 0) le = timed(c, pe, 2, [&] { return launch_indenter_p2g(b, 0, s); });
   for (int k = 0; k + 1 < n && le == cudaSuccess; ++k) {
     le = timed(c, pe, 0, [&] { return launch_grid_update(b, k, dt, 1, s); });
-    if (le == cudaSuccess) le = timed(c, pe, 1, [&] { return launch_transfer(b, blk, XFER_FUSED, dt, s); });
+    if (le == cudaSuccess)
+      le = timed(c, pe, 1, [&] {
+        return c->pipe && c->pipe_grid > 0 ? launch_transfer_pipe(b, blk, dt, c->pipe_grid, c->max_polls, s)
+                                           : launch_transfer(b, blk, XFER_FUSED, dt, s);
+      });
     if (le == cudaSuccess && b.Np > 0) le = timed(c, pe, 1, [&] { return launch_indenter_p2g(b, k + 1, s); });
     if (le == cudaSuccess) le = timed(c, pe, 3, [&] { return launch_sort(b, blk, 0, s); });
   }
@@ -550,6 +556,8 @@ tacchi_status apply_blocks(tacchi_ctx *c, SortBlock blk) {
   CK(cudaMemcpy(c->d_block_inst, bi.data(), sizeof(uint32_t) * bi.size(), cudaMemcpyHostToDevice));
   CK(cudaMemsetAsync(c->b.bcount, 0, sizeof(uint32_t) * c->Nblk_cap, c->stream));
   CK(prepare_transfer(blk));
+  c->pipe_grid = 0;
+  if (pipe_supported(blk)) CK(prepare_pipe(blk, &c->pipe_grid));
   if (c->launch == TACCHI_LAUNCH_PERSISTENT && !persistent_supported(blk)) c->launch = TACCHI_LAUNCH_GRAPH;
   CK(launch_sort(c->b, blk, 1, c->stream));
   CK(cudaMemsetAsync(c->b.movers, 0, sizeof(int), c->stream));
@@ -565,7 +573,7 @@ void release(tacchi_ctx *c) {
     if (h.d_hm) cudaFree(h.d_hm);
   cudaFree(c->d_ind_pts);
   cudaFree(c->d_ind_inst);
-  void *bufs[] = {c->b.ps, c->b.v, c->b.C, (void *)c->b.flags, c->b.idx, c->b.hcell, c->b.key, c->b.bstart,
+  void *bufs[] = {c->b.ps, c->b.v, c->b.C, (void *)c->b.flags, c->b.idx, c->b.hcell, c->b.brec, c->b.blkq, c->b.key, c->b.bstart,
                   c->b.bcount, c->b.cursor, c->b.gmm, c->b.gv, c->b.err, c->b.movers, c->d_bar, c->d_inst,
                   c->d_node_offs, c->d_part_offs, c->d_block_inst, c->d_frames, c->d_surf, c->d_z0, c->d_srest,
                   c->d_u0,
@@ -680,6 +688,7 @@ tacchi_status create_batch(int n, const tacchi_elastomer_desc *descs, void *stre
             dalloc(c, &c->b.v, 3 * N) == cudaSuccess && dalloc(c, &c->b.C, 9 * N) == cudaSuccess &&
             dalloc(c, (uint8_t **)&c->b.flags, N) == cudaSuccess && dalloc(c, &c->b.idx, N + 4) == cudaSuccess &&
             dalloc(c, &c->b.hcell, N + 8) == cudaSuccess &&
+            dalloc(c, &c->b.brec, blk_cap) == cudaSuccess && dalloc(c, &c->b.blkq, 4) == cudaSuccess &&
             dalloc(c, &c->b.key, N) == cudaSuccess && dalloc(c, &c->b.bstart, blk_cap + 1) == cudaSuccess &&
             dalloc(c, &c->b.bcount, blk_cap) == cudaSuccess && dalloc(c, &c->b.cursor, blk_cap) == cudaSuccess &&
             dalloc(c, &c->b.gmm, Nn) == cudaSuccess && dalloc(c, &c->b.gv, Nn) == cudaSuccess &&
@@ -694,7 +703,9 @@ tacchi_status create_batch(int n, const tacchi_elastomer_desc *descs, void *stre
     cudaGetLastError();
     return fail(TACCHI_ERR_OOM);
   }
-  if (cudaMemset(c->b.movers, 0, 2 * sizeof(int)) != cudaSuccess) return fail(TACCHI_ERR_CUDA);
+  if (cudaMemset(c->b.movers, 0, 2 * sizeof(int)) != cudaSuccess ||
+      cudaMemset(c->b.blkq, 0, 4 * sizeof(uint32_t)) != cudaSuccess)
+    return fail(TACCHI_ERR_CUDA);
   if (cudaMallocHost((void **)&c->h_stage, stage_bytes(n)) != cudaSuccess ||
       cudaMallocHost((void **)&c->h_err, sizeof(int)) != cudaSuccess)
     return fail(TACCHI_ERR_OOM);
@@ -835,6 +846,7 @@ tacchi_status tacchi_batch_info(tacchi_handle c, int i, tacchi_info_t *o) {
   o->block[1] = c->blk.y;
   o->block[2] = c->blk.z;
   o->threads_per_cell = c->blk.t;
+  o->pipelined = c->pipe && c->pipe_grid > 0 && c->launch == TACCHI_LAUNCH_GRAPH ? 1 : 0;
   o->n_blocks = h.dev.nblocks;
   o->device_bytes = c->device_bytes;
   return TACCHI_OK;
@@ -1339,6 +1351,14 @@ tacchi_status tacchi_set_launch(tacchi_handle c, int mode) {
   return TACCHI_OK;
 }
 
+tacchi_status tacchi_set_pipeline(tacchi_handle c, int on) {
+  if (!c || (on != 0 && on != 1)) return TACCHI_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  drop_graphs(c);
+  c->pipe = on;
+  return TACCHI_OK;
+}
+
 tacchi_status tacchi_set_barrier_wait(tacchi_handle c, int64_t max_polls, int extra_arrivals) {
   if (!c || max_polls < 1 || extra_arrivals < 0) return TACCHI_ERR_INVALID_ARG;
   c->max_polls = max_polls;
@@ -1377,29 +1397,40 @@ tacchi_status tacchi_autotune(tacchi_handle c, int n_substeps, double dt, int be
   c->profiling = false;
   const int launch = c->launch;
   c->launch = TACCHI_LAUNCH_GRAPH;  // the plans are timed in the graph form
+  const int pipe = c->pipe;
   double best_ms = 1e300;
-  int best_k = -1;
+  int best_k = -1, best_pipe = 0;
   for (int k = 0; k < TACCHI_NUM_TRANSFER_PLANS && st == TACCHI_OK; ++k) {
     st = apply_blocks(c, kPlans[k]);
     if (st != TACCHI_OK) break;
-    double ms = 0;
-    for (int rep = 0; rep < 2 && st == TACCHI_OK; ++rep) {  // the first run builds the graph
-      st = restore();
+    // a plan with a pipelined form is timed both ways and counts with the faster
+    double plan_ms = 1e300;
+    for (int pl = 0; pl < (c->pipe_grid > 0 ? 2 : 1) && st == TACCHI_OK; ++pl) {
+      c->pipe = pl;
+      drop_graphs(c);
+      double ms = 0;
+      for (int rep = 0; rep < 2 && st == TACCHI_OK; ++rep) {  // the first run builds the graph
+        st = restore();
+        if (st != TACCHI_OK) break;
+        for (int i = 0; i < c->n_inst(); ++i) std::copy(poses[i].begin(), poses[i].end(), c->in[i].pose);
+        st = cuda_status(cudaStreamSynchronize(c->stream));
+        const auto t0 = std::chrono::steady_clock::now();
+        if (st == TACCHI_OK) st = tacchi_step(c, n_substeps, dt);
+        if (st == TACCHI_OK) st = sync_and_check(c);
+        ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      }
       if (st != TACCHI_OK) break;
-      for (int i = 0; i < c->n_inst(); ++i) std::copy(poses[i].begin(), poses[i].end(), c->in[i].pose);
-      st = cuda_status(cudaStreamSynchronize(c->stream));
-      const auto t0 = std::chrono::steady_clock::now();
-      if (st == TACCHI_OK) st = tacchi_step(c, n_substeps, dt);
-      if (st == TACCHI_OK) st = sync_and_check(c);
-      ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+      if (ms < plan_ms) plan_ms = ms;
+      if (ms < best_ms) {
+        best_ms = ms;
+        best_k = k;
+        best_pipe = pl;
+      }
     }
     if (st != TACCHI_OK) break;
-    if (ms_per_substep) ms_per_substep[k] = ms / n_substeps;
-    if (ms < best_ms) {
-      best_ms = ms;
-      best_k = k;
-    }
+    if (ms_per_substep) ms_per_substep[k] = plan_ms / n_substeps;
   }
+  c->pipe = st == TACCHI_OK && best_k >= 0 ? best_pipe : pipe;
   c->profiling = prof;
   if (st == TACCHI_OK) st = restore();
   if (launch == TACCHI_LAUNCH_PERSISTENT && persistent_supported(c->blk)) c->launch = launch;

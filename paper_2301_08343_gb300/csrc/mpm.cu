@@ -124,8 +124,9 @@ struct XferPlan {
   static constexpr size_t STAGE_BYTES = 16 * 2 * 3 * (size_t)THREADS;
   // byte offsets in dynamic shared memory
   static constexpr size_t OFF_KEY = 0;                              // u32 [MAXP] rank and cell per particle
-  static constexpr size_t OFF_PID = OFF_KEY + 4 * (size_t)MAXP;     // u32 [MAXP] particle ids in idx order
-  static constexpr size_t OFF_V = (OFF_PID + 4 * (size_t)MAXP + 15) / 16 * 16;  // float4 [VN]
+  // u32 [MAXP + 8] particle ids in idx order (8 spare for a 16-byte-aligned copy)
+  static constexpr size_t OFF_PID = OFF_KEY + 4 * (size_t)MAXP;
+  static constexpr size_t OFF_V = (OFF_PID + 4 * (size_t)(MAXP + 8) + 15) / 16 * 16;  // float4 [VN]
   static constexpr size_t OFF_LIST = OFF_V + 16 * (size_t)VN;       // u32 [MAXP] particles by cell
   static constexpr size_t OFF_CNT = OFF_LIST + 4 * (size_t)MAXP;    // u32 [NE] count, then start
   static constexpr size_t OFF_START = OFF_CNT + 4 * (size_t)NE;     // u32 [NE + 1]
@@ -145,37 +146,46 @@ struct XferPlan {
 #define TACCHI_XFER_MIN_BLOCKS 2
 #endif
 
-// The transfer of sort block gblk by the calling CTA (all its threads), in
-// dynamic shared memory smem of XferPlan::BYTES; the kernel below runs one
-// block per CTA, the persistent step one block after another.
+// Block gblk's place: its particle range, instance and cell origin B0.
+struct XBlock {
+  uint32_t start, n;
+  int ii, B0x, B0y, B0z;
+};
+
+template <int BX, int BY, int BZ>
+__device__ __forceinline__ XBlock block_of(const Batch &b, long long gblk) {
+  XBlock x;
+  x.start = b.bstart[gblk];
+  x.n = b.bstart[gblk + 1] - x.start;
+  x.ii = (int)b.block_inst[gblk];
+  const Instance &I = b.inst[x.ii];
+  const long long lb = gblk - I.block_off;
+  const int nb0 = I.nb[0], nb1 = I.nb[1];
+  x.B0x = (int)(lb % nb0) * BX;
+  x.B0y = (int)((lb / nb0) % nb1) * BY;
+  x.B0z = (int)(lb / ((long long)nb0 * nb1)) * BZ;
+  return x;
+}
+
+// The particle loop of a grouped block (steps 2-3 of the transfer): cells
+// by thread, G2P against the V tile vt, F update, stress and P2G into the
+// cell's register accumulators, flushed to the grid per cell.  All threads
+// of the CTA call it after the grouping (s_list, s_start, s_order) is built;
+// it ends with a barrier.
 template <int BX, int BY, int BZ, int MODE>
-__device__ __forceinline__ void transfer_block(const Batch &b, float dt, long long gblk, unsigned char *smem) {
+__device__ __forceinline__ void transfer_cells(const Batch &b, float dt, const XBlock &xb, unsigned char *smem,
+                                               const float4 *vt, bool grouped, uint32_t ncells, int *s_moved) {
   using P = XferPlan<BX, BY, BZ>;
   constexpr bool DO_G2P = (MODE & XFER_G2P) != 0;
   constexpr bool DO_P2G = (MODE & XFER_P2G) != 0;
   constexpr int VX = P::VX, VY = P::VY;
-  uint32_t *s_key = reinterpret_cast<uint32_t *>(smem + P::OFF_KEY);
-  float4 *vt = reinterpret_cast<float4 *>(smem + P::OFF_V);
-  uint32_t *s_list = reinterpret_cast<uint32_t *>(smem + P::OFF_LIST);
-  uint32_t *s_pid = reinterpret_cast<uint32_t *>(smem + P::OFF_PID);
-  uint32_t *s_cnt = reinterpret_cast<uint32_t *>(smem + P::OFF_CNT);
-  uint32_t *s_start = reinterpret_cast<uint32_t *>(smem + P::OFF_START);
-  uint16_t *s_cells = reinterpret_cast<uint16_t *>(smem + P::OFF_CELLS);
-  uint16_t *s_order = reinterpret_cast<uint16_t *>(smem + P::OFF_ORDER);
-  __shared__ uint32_t s_warp[P::THREADS / 32];
-  __shared__ unsigned long long s_warp64[P::THREADS / 32];
-  __shared__ int s_moved, s_overflow;
-
-  const uint32_t start = b.bstart[gblk], end = b.bstart[gblk + 1];
-  if (start == end) return;
-  const uint32_t n = end - start;
-  const int ii = b.block_inst[gblk];
-  const Instance &I = b.inst[ii];
+  const uint32_t *s_list = reinterpret_cast<const uint32_t *>(smem + P::OFF_LIST);
+  const uint32_t *s_start = reinterpret_cast<const uint32_t *>(smem + P::OFF_START);
+  const uint16_t *s_order = reinterpret_cast<const uint16_t *>(smem + P::OFF_ORDER);
+  const uint32_t start = xb.start, n = xb.n;
+  const Instance &I = b.inst[xb.ii];
   const int G0 = I.G[0], G1 = I.G[1], G2 = I.G[2];
-  const long long lb = gblk - I.block_off;
-  const int nb0 = I.nb[0], nb1 = I.nb[1];
-  const int B0x = (int)(lb % nb0) * BX, B0y = (int)((lb / nb0) % nb1) * BY,
-            B0z = (int)(lb / ((long long)nb0 * nb1)) * BZ;
+  const int B0x = xb.B0x, B0y = xb.B0y, B0z = xb.B0z;
   const long long Ntot = b.Ntot;
   // the instance record is read once: stores to the particle arrays below
   // could otherwise alias it and force reloads inside the particle loop
@@ -187,69 +197,6 @@ __device__ __forceinline__ void transfer_block(const Batch &b, float dt, long lo
   const int tid = threadIdx.x;
   float4 *__restrict__ gps = b.ps;
   const uint8_t *__restrict__ gfl = b.flags;
-
-  // ---- grid velocities of nodes [B0-1, B0+B+3) into the V tile, copied
-  // asynchronously while the particles are grouped (zeros outside the grid)
-  if (DO_G2P) {
-    const float4 *gv = b.gv + node_off;
-    for (int t = tid; t < P::VN; t += P::THREADS) {
-      const int x = B0x - 1 + t % VX, y = B0y - 1 + (t / VX) % VY, z = B0z - 1 + t / (VX * VY);
-      const bool in = x >= 0 && y >= 0 && z >= 0 && x < G0 && y < G1 && z < G2;
-      cp_async16_zfill(vt + t, in ? gv + ((long long)z * G1 + y) * G0 + x : gv, in);
-    }
-  }
-  cp_async_commit();
-
-  // ---- group the block's particles by home cell
-  for (int c = tid; c < P::NE; c += P::THREADS) s_cnt[c] = 0;
-  if (tid == 0) {
-    s_moved = 0;
-    s_overflow = n > (uint32_t)P::MAXP;
-  }
-  __syncthreads();
-  if (n <= (uint32_t)P::MAXP) {
-    // GB slots per thread per round, so that their id and home-cell loads are
-    // all in flight together (two contiguous reads, no gather of positions)
-    constexpr int GB = 16;
-    static_assert(P::NE < kNotHome, "home cells must fit below the not-home mark");
-    const uint16_t *__restrict__ ghc = b.hcell + start;
-    for (uint32_t l0 = 0; l0 < n; l0 += GB * P::THREADS) {
-      uint32_t pp[GB], hc[GB];
-#pragma unroll
-      for (int g = 0; g < GB; ++g) {
-        const uint32_t l = l0 + g * P::THREADS + tid;
-        pp[g] = l < n ? b.idx[start + l] : 0u;
-        hc[g] = l < n ? (uint32_t)ghc[l] : (uint32_t)kNotHome;
-      }
-#pragma unroll
-      for (int g = 0; g < GB; ++g) {
-        const uint32_t l = l0 + g * P::THREADS + tid;
-        if (l >= n) continue;
-        s_pid[l] = pp[g];
-        uint32_t key = 0xFFFFFFFFu;
-        if (hc[g] < (uint32_t)P::NE) {
-          key = (atomicAdd(s_cnt + hc[g], 1u) << 12) | hc[g];  // rank, cell (< 4096)
-        } else {
-          s_overflow = 1;  // not at home: the sort invariant is broken
-        }
-        s_key[l] = key;
-      }
-    }
-  }
-  __syncthreads();
-  const bool grouped = !s_overflow;
-  uint32_t ncells = 0;
-  if (grouped) {
-    ncells = block_scan_compact<P::THREADS, P::PER>(s_cnt, s_start, s_cells, P::NE, s_warp);
-    for (uint32_t l = tid; l < n; l += P::THREADS) {
-      const uint32_t key = s_key[l];
-      s_list[s_start[key & 0xFFFu] + (key >> 12)] = s_pid[l];
-    }
-    order_cells_by_load<P::THREADS, P::PER>(s_cells, s_start, (int)ncells, s_order, s_warp64);
-  }
-  __syncthreads();
-  cp_async_wait<0>();  // this thread's part of the V tile
-  __syncthreads();
 
   // ---- one cell per thread (or, without grouping, one particle per thread)
   const uint32_t nwork = grouped ? ncells : n;
@@ -439,7 +386,7 @@ __device__ __forceinline__ void transfer_block(const Batch &b, float dt, long lo
         err |= ERRBIT_OUT_OF_GRID;
       const bool home = nbs[0] >= B0x - 1 && nbs[0] <= B0x + BX && nbs[1] >= B0y - 1 && nbs[1] <= B0y + BY &&
                         nbs[2] >= B0z - 1 && nbs[2] <= B0z + BZ;
-      if (DO_G2P && !home) s_moved = 1;  // left its home cells: re-sort after this transfer
+      if (DO_G2P && !home) *s_moved = 1;  // left its home cells: re-sort after this transfer
       // the next transfer groups the block from these: slot q of the block's
       // idx range (its cell order now, when grouped) and the new home cell
       {
@@ -535,13 +482,293 @@ __device__ __forceinline__ void transfer_block(const Batch &b, float dt, long lo
     }
   }
   __syncthreads();
-  if (DO_G2P && tid == 0 && s_moved) *b.movers = 1;
+  if (DO_G2P && tid == 0 && *s_moved) *b.movers = 1;
+}
+
+// The transfer of sort block gblk by the calling CTA (all its threads), in
+// dynamic shared memory smem of XferPlan::BYTES; the kernel below runs one
+// block per CTA, the persistent step one block after another.
+template <int BX, int BY, int BZ, int MODE>
+__device__ __forceinline__ void transfer_block(const Batch &b, float dt, long long gblk, unsigned char *smem) {
+  using P = XferPlan<BX, BY, BZ>;
+  constexpr bool DO_G2P = (MODE & XFER_G2P) != 0;
+  constexpr int VX = P::VX, VY = P::VY;
+  uint32_t *s_key = reinterpret_cast<uint32_t *>(smem + P::OFF_KEY);
+  float4 *vt = reinterpret_cast<float4 *>(smem + P::OFF_V);
+  uint32_t *s_list = reinterpret_cast<uint32_t *>(smem + P::OFF_LIST);
+  uint32_t *s_pid = reinterpret_cast<uint32_t *>(smem + P::OFF_PID);
+  uint32_t *s_cnt = reinterpret_cast<uint32_t *>(smem + P::OFF_CNT);
+  uint32_t *s_start = reinterpret_cast<uint32_t *>(smem + P::OFF_START);
+  uint16_t *s_cells = reinterpret_cast<uint16_t *>(smem + P::OFF_CELLS);
+  uint16_t *s_order = reinterpret_cast<uint16_t *>(smem + P::OFF_ORDER);
+  __shared__ uint32_t s_warp[P::THREADS / 32];
+  __shared__ unsigned long long s_warp64[P::THREADS / 32];
+  __shared__ int s_moved, s_overflow;
+
+  const XBlock xb = block_of<BX, BY, BZ>(b, gblk);
+  if (xb.n == 0) return;
+  const uint32_t start = xb.start, n = xb.n;
+  const Instance &I = b.inst[xb.ii];
+  const int G0 = I.G[0], G1 = I.G[1], G2 = I.G[2];
+  const int B0x = xb.B0x, B0y = xb.B0y, B0z = xb.B0z;
+  const long long node_off = I.node_off;
+  const int tid = threadIdx.x;
+
+  // ---- grid velocities of nodes [B0-1, B0+B+3) into the V tile, copied
+  // asynchronously while the particles are grouped (zeros outside the grid)
+  if (DO_G2P) {
+    const float4 *gv = b.gv + node_off;
+    for (int t = tid; t < P::VN; t += P::THREADS) {
+      const int x = B0x - 1 + t % VX, y = B0y - 1 + (t / VX) % VY, z = B0z - 1 + t / (VX * VY);
+      const bool in = x >= 0 && y >= 0 && z >= 0 && x < G0 && y < G1 && z < G2;
+      cp_async16_zfill(vt + t, in ? gv + ((long long)z * G1 + y) * G0 + x : gv, in);
+    }
+  }
+  cp_async_commit();
+
+  // ---- group the block's particles by home cell
+  for (int c = tid; c < P::NE; c += P::THREADS) s_cnt[c] = 0;
+  if (tid == 0) {
+    s_moved = 0;
+    s_overflow = n > (uint32_t)P::MAXP;
+  }
+  __syncthreads();
+  if (n <= (uint32_t)P::MAXP) {
+    // GB slots per thread per round, so that their id and home-cell loads are
+    // all in flight together (two contiguous reads, no gather of positions)
+    constexpr int GB = 16;
+    static_assert(P::NE < kNotHome, "home cells must fit below the not-home mark");
+    const uint16_t *__restrict__ ghc = b.hcell + start;
+    for (uint32_t l0 = 0; l0 < n; l0 += GB * P::THREADS) {
+      uint32_t pp[GB], hc[GB];
+#pragma unroll
+      for (int g = 0; g < GB; ++g) {
+        const uint32_t l = l0 + g * P::THREADS + tid;
+        pp[g] = l < n ? b.idx[start + l] : 0u;
+        hc[g] = l < n ? (uint32_t)ghc[l] : (uint32_t)kNotHome;
+      }
+#pragma unroll
+      for (int g = 0; g < GB; ++g) {
+        const uint32_t l = l0 + g * P::THREADS + tid;
+        if (l >= n) continue;
+        s_pid[l] = pp[g];
+        uint32_t key = 0xFFFFFFFFu;
+        if (hc[g] < (uint32_t)P::NE) {
+          key = (atomicAdd(s_cnt + hc[g], 1u) << 12) | hc[g];  // rank, cell (< 4096)
+        } else {
+          s_overflow = 1;  // not at home: the sort invariant is broken
+        }
+        s_key[l] = key;
+      }
+    }
+  }
+  __syncthreads();
+  const bool grouped = !s_overflow;
+  uint32_t ncells = 0;
+  if (grouped) {
+    ncells = block_scan_compact<P::THREADS, P::PER>(s_cnt, s_start, s_cells, P::NE, s_warp);
+    for (uint32_t l = tid; l < n; l += P::THREADS) {
+      const uint32_t key = s_key[l];
+      s_list[s_start[key & 0xFFFu] + (key >> 12)] = s_pid[l];
+    }
+    order_cells_by_load<P::THREADS, P::PER>(s_cells, s_start, (int)ncells, s_order, s_warp64);
+  }
+  __syncthreads();
+  cp_async_wait<0>();  // this thread's part of the V tile
+  __syncthreads();
+  transfer_cells<BX, BY, BZ, MODE>(b, dt, xb, smem, vt, grouped, ncells, &s_moved);
 }
 
 template <int BX, int BY, int BZ, int MODE>
 __global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer(Batch b, float dt) {
   extern __shared__ __align__(16) unsigned char smem[];
   transfer_block<BX, BY, BZ, MODE>(b, dt, blockIdx.x, smem);
+}
+
+// ---------------------------------------------------------------------------
+// Pipelined fused transfer.  A persistent grid (the transfer's resident CTAs,
+// two per SM) takes the sort's non-empty block records one after another.
+// While a CTA runs the particle loop of one block, the copy engine brings the
+// next block's idx slots, home cells and V tile into the other set of buffers
+// (bulk copies counted in bytes on one mbarrier), so that between two blocks
+// only the shared-memory grouping is left of the per-block prologue.  Records
+// are handed out by an atomic counter (brec order is block order, so CTAs
+// running at the same time work on neighbouring blocks); the last CTA to
+// finish resets the counters for the next launch.
+template <int BX, int BY, int BZ>
+struct PipePlan {
+  using X = XferPlan<BX, BY, BZ>;
+  // the XferPlan layout (its PID region holds the copied idx slots) plus a
+  // second V tile and the copied home cells
+  static constexpr size_t OFF_V2 = (X::BYTES + 15) / 16 * 16;                 // float4 [VN]
+  static constexpr size_t OFF_HC = OFF_V2 + 16 * (size_t)X::VN;              // u16 [MAXP + 16]
+  static constexpr size_t BYTES = (OFF_HC + 2 * (size_t)(X::MAXP + 16) + 15) / 16 * 16;
+};
+
+// Issue the copies of block r into V tile vb and the id / home-cell buffers
+// pid and hc (all threads; each arrives once on bar with the bytes of its own
+// copies).  The idx and home-cell copies start at the 16-byte boundary at or
+// below r.start: slot l of the block is then pid[(r.start & 3) + l] and
+// hc[(r.start & 7) + l].  They are skipped for a block too large to group.
+template <int BX, int BY, int BZ>
+__device__ __forceinline__ void pipe_prefetch(const Batch &b, const BlockRec &r, float4 *vb, uint32_t *pid,
+                                              uint16_t *hc, uint64_t *bar) {
+  using X = XferPlan<BX, BY, BZ>;
+  constexpr int VX = X::VX, VY = X::VY, VZ = X::VZ, T = X::THREADS;
+  const int tid = threadIdx.x;
+  // earlier generic accesses of these buffers (the last block's grouping and
+  // particle loop, behind a barrier) come before the copy engine's writes
+  fence_proxy_async_smem();
+  const bool groupable = r.n <= (uint32_t)X::MAXP;
+  const uint32_t a0 = r.start & ~3u, a1 = (r.start + r.n + 3u) & ~3u;  // idx, u32
+  const uint32_t h0 = r.start & ~7u, h1 = (r.start + r.n + 7u) & ~7u;  // hcell, u16
+  const float4 *gv = b.gv + r.node_off;
+  const int x0 = max(r.B0x - 1, 0), x1 = min(r.B0x - 1 + VX, r.G0);
+  uint32_t bytes = 0;
+  if (tid == 0 && groupable) bytes += 4u * (a1 - a0);
+  if (tid == 1 && groupable) bytes += 2u * (h1 - h0);
+  for (int rr = tid; rr < VY * VZ; rr += T) {
+    const int y = r.B0y - 1 + rr % VY, z = r.B0z - 1 + rr / VY;
+    if (y >= 0 && z >= 0 && y < r.G1 && z < r.G2 && x1 > x0) bytes += 16u * (uint32_t)(x1 - x0);
+  }
+  mbar_arrive_tx(bar, bytes);
+  if (tid == 0 && groupable) bulk_g2s(pid, b.idx + a0, 4u * (a1 - a0), bar);
+  if (tid == 1 && groupable) bulk_g2s(hc, b.hcell + h0, 2u * (h1 - h0), bar);
+  const float4 zero = make_float4(0.f, 0.f, 0.f, 0.f);
+  for (int rr = tid; rr < VY * VZ; rr += T) {
+    const int y = r.B0y - 1 + rr % VY, z = r.B0z - 1 + rr / VY;
+    float4 *row = vb + rr * VX;
+    if (y >= 0 && z >= 0 && y < r.G1 && z < r.G2 && x1 > x0) {
+      bulk_g2s(row + (x0 - (r.B0x - 1)), gv + ((long long)z * r.G1 + y) * r.G0 + x0, 16u * (uint32_t)(x1 - x0), bar);
+      for (int t = 0; t < x0 - (r.B0x - 1); ++t) row[t] = zero;     // nodes left of the grid
+      for (int t = x1 - (r.B0x - 1); t < VX; ++t) row[t] = zero;    // right of it
+    } else {
+      for (int t = 0; t < VX; ++t) row[t] = zero;                    // row outside the grid
+    }
+  }
+}
+
+template <int BX, int BY, int BZ>
+__global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer_pipe(Batch b, float dt, long long max_polls) {
+  using X = XferPlan<BX, BY, BZ>;
+  using Q = PipePlan<BX, BY, BZ>;
+  constexpr int T = X::THREADS;
+  extern __shared__ __align__(16) unsigned char smem[];
+  uint32_t *s_key = reinterpret_cast<uint32_t *>(smem + X::OFF_KEY);
+  uint32_t *s_pidbuf = reinterpret_cast<uint32_t *>(smem + X::OFF_PID);
+  uint16_t *s_hcbuf = reinterpret_cast<uint16_t *>(smem + Q::OFF_HC);
+  uint32_t *s_list = reinterpret_cast<uint32_t *>(smem + X::OFF_LIST);
+  uint32_t *s_cnt = reinterpret_cast<uint32_t *>(smem + X::OFF_CNT);
+  uint32_t *s_start = reinterpret_cast<uint32_t *>(smem + X::OFF_START);
+  uint16_t *s_cells = reinterpret_cast<uint16_t *>(smem + X::OFF_CELLS);
+  uint16_t *s_order = reinterpret_cast<uint16_t *>(smem + X::OFF_ORDER);
+  float4 *vcur = reinterpret_cast<float4 *>(smem + X::OFF_V);
+  float4 *vnext = reinterpret_cast<float4 *>(smem + Q::OFF_V2);
+  __shared__ __align__(8) uint64_t bar;
+  // ring of block records: the current block, the next (its copies in
+  // flight) and the one after (its record in flight)
+  __shared__ __align__(16) BlockRec s_rec[3];
+  __shared__ uint32_t s_warp[T / 32];
+  __shared__ unsigned long long s_warp64[T / 32];
+  __shared__ int s_moved, s_overflow, s_abort;
+  const int tid = threadIdx.x;
+  const uint32_t nrec = b.blkq[0];
+
+  if (tid == 0) {
+    mbar_init(&bar, T);
+    mbar_init_fence();
+    const uint32_t k0 = atomicAdd(b.blkq + 1, 1u), k1 = atomicAdd(b.blkq + 1, 1u);
+    BlockRec none{};
+    s_rec[0] = k0 < nrec ? b.brec[k0] : none;
+    s_rec[1] = k1 < nrec ? b.brec[k1] : none;
+    s_abort = 0;
+  }
+  __syncthreads();
+  uint32_t parity = 0;
+  if (s_rec[0].n > 0) pipe_prefetch<BX, BY, BZ>(b, s_rec[0], vcur, s_pidbuf, s_hcbuf, &bar);
+  for (int cur = 0;; cur = cur == 2 ? 0 : cur + 1) {
+    const int nxt = cur == 2 ? 0 : cur + 1, aft = nxt == 2 ? 0 : nxt + 1;
+    const BlockRec rc = s_rec[cur];
+    if (rc.n == 0) break;  // the records are used up (uniform: read from shared memory)
+    // the record after next: its index now, its copy once the grouping is done
+    uint32_t kk = 0;
+    if (tid == 0) kk = atomicAdd(b.blkq + 1, 1u);
+    // this block's copies
+    if (!mbar_wait_bounded(&bar, parity, max_polls)) s_abort = 1;
+    for (int c = tid; c < X::NE; c += T) s_cnt[c] = 0;
+    if (tid == 0) {
+      s_moved = 0;
+      s_overflow = rc.n > (uint32_t)X::MAXP;
+    }
+    __syncthreads();
+    if (s_abort) break;
+    parity ^= 1u;
+    // ---- grouping from the copied slots and home cells
+    const uint32_t n = rc.n;
+    const uint32_t *s_pid = s_pidbuf + (rc.start & 3u);
+    const uint16_t *s_hc = s_hcbuf + (rc.start & 7u);
+    if (n <= (uint32_t)X::MAXP) {
+      for (uint32_t l = tid; l < n; l += T) {
+        const uint32_t h = s_hc[l];
+        uint32_t key = 0xFFFFFFFFu;
+        if (h < (uint32_t)X::NE) {
+          key = (atomicAdd(s_cnt + h, 1u) << 12) | h;  // rank, cell (< 4096)
+        } else {
+          s_overflow = 1;  // not at home: the sort invariant is broken
+        }
+        s_key[l] = key;
+      }
+    }
+    __syncthreads();
+    const bool grouped = !s_overflow;
+    uint32_t ncells = 0;
+    if (grouped) {
+      ncells = block_scan_compact<T, X::PER>(s_cnt, s_start, s_cells, X::NE, s_warp);
+      for (uint32_t l = tid; l < n; l += T) {
+        const uint32_t key = s_key[l];
+        s_list[s_start[key & 0xFFFu] + (key >> 12)] = s_pid[l];
+      }
+      order_cells_by_load<T, X::PER>(s_cells, s_start, (int)ncells, s_order, s_warp64);
+    }
+    __syncthreads();
+    // ---- the next block's copies, into the buffers this one no longer needs,
+    // and the record after it
+    const BlockRec rn = s_rec[nxt];
+    if (rn.n > 0) pipe_prefetch<BX, BY, BZ>(b, rn, vnext, s_pidbuf, s_hcbuf, &bar);
+    if (tid == 0) {
+      if (kk < nrec) {
+        const float4 *src = reinterpret_cast<const float4 *>(b.brec + kk);
+        float4 *dst = reinterpret_cast<float4 *>(&s_rec[aft]);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) cp_async16(dst + j, src + j);
+      } else {
+        s_rec[aft].n = 0;
+      }
+      cp_async_commit();
+    }
+    // ---- the particle loop (ends with a barrier)
+    const XBlock xb{rc.start, rc.n, rc.ii, rc.B0x, rc.B0y, rc.B0z};
+    transfer_cells<BX, BY, BZ, XFER_FUSED>(b, dt, xb, smem, vcur, grouped, ncells, &s_moved);
+    cp_async_wait<0>();  // the record copy, where thread 0 had no particle to wait on
+    __syncthreads();
+    float4 *t = vcur;
+    vcur = vnext;
+    vnext = t;
+  }
+  // a wait that gave up: before the CTA leaves, wait again for the copies
+  // still in flight, with a bound of its own (2^26 polls) rather than the
+  // caller's, so that no copy lands in the shared memory of a finished CTA
+  if (s_abort) mbar_wait_bounded(&bar, parity, 1ll << 26);
+  __syncthreads();
+  if (tid == 0) {
+    if (s_abort) atomicOr(b.err, ERRBIT_TIMEOUT);
+    __threadfence();
+    if (atomicAdd(b.blkq + 2, 1u) == gridDim.x - 1) {  // last CTA: reset the hand-out
+      b.blkq[1] = 0u;
+      b.blkq[2] = 0u;
+      __threadfence();
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -587,52 +814,79 @@ __global__ void __launch_bounds__(256) k_sort_keys(Batch b, SortBlock blk, int f
 // Exclusive scan of the block counts by one CTA (any size up to 1024
 // threads); also sets the scatter cursors and clears the counts for the next
 // sort.
-__device__ __forceinline__ void sort_scan_cta(const Batch &b) {
-  __shared__ uint32_t warp_tot[32];
+__device__ __forceinline__ void sort_scan_cta(const Batch &b, SortBlock blk) {
+  __shared__ unsigned long long warp_tot[32];
   const long long n = b.Nblk;
   const int T = blockDim.x;
   const long long per = (n + T - 1) / T;
   const long long lo = threadIdx.x * per;
   const long long hi = lo + per < n ? lo + per : n;
-  uint32_t local = 0;
-  for (long long i = lo; i < hi; ++i) local += b.bcount[i];
+  // particles (low word) and non-empty blocks (high word) of this thread's
+  // range, scanned together
+  uint32_t local = 0, nz = 0;
+  for (long long i = lo; i < hi; ++i) {
+    const uint32_t c = b.bcount[i];
+    local += c;
+    nz += c > 0u;
+  }
+  const unsigned long long mine = (unsigned long long)local | ((unsigned long long)nz << 32);
   // inclusive scan of the per-thread totals
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  uint32_t x = local;
+  unsigned long long x = mine;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x, o);
     if (lane >= o) x += y;
   }
   if (lane == 31) warp_tot[wid] = x;
   __syncthreads();
   if (wid == 0) {
-    uint32_t t = lane < (T >> 5) ? warp_tot[lane] : 0u;
+    unsigned long long t = lane < (T >> 5) ? warp_tot[lane] : 0ull;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, t, o);
+      const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, t, o);
       if (lane >= o) t += y;
     }
     warp_tot[lane] = t;
   }
   __syncthreads();
-  uint32_t run = x - local + (wid > 0 ? warp_tot[wid - 1] : 0u);
+  const unsigned long long pre = x - mine + (wid > 0 ? warp_tot[wid - 1] : 0ull);
+  uint32_t run = (uint32_t)pre, arun = (uint32_t)(pre >> 32);
   for (long long i = lo; i < hi; ++i) {
     const uint32_t c = b.bcount[i];
     b.bstart[i] = run;
     b.cursor[i] = run;
     b.bcount[i] = 0u;
+    if (c > 0u) {
+      BlockRec r;
+      r.start = run;
+      r.n = c;
+      r.ii = (int)b.block_inst[i];
+      const Instance &I = b.inst[r.ii];
+      const long long lb = i - I.block_off;
+      const int nb0 = I.nb[0], nb1 = I.nb[1];
+      r.B0x = (int)(lb % nb0) * blk.x;
+      r.B0y = (int)((lb / nb0) % nb1) * blk.y;
+      r.B0z = (int)(lb / ((long long)nb0 * nb1)) * blk.z;
+      r.G0 = I.G[0];
+      r.G1 = I.G[1];
+      r.G2 = I.G[2];
+      r.pad = 0;
+      r.node_off = I.node_off;
+      b.brec[arun++] = r;
+    }
     run += c;
   }
   if (threadIdx.x == T - 1) {
     b.bstart[n] = run;
+    b.blkq[0] = arun;
     b.movers[1] += 1;  // sorts that did work, read by the profile
   }
 }
 
-__global__ void __launch_bounds__(1024) k_sort_scan(Batch b, int force) {
+__global__ void __launch_bounds__(1024) k_sort_scan(Batch b, SortBlock blk, int force) {
   if (!force && *(volatile int *)b.movers == 0) return;
-  sort_scan_cta(b);
+  sort_scan_cta(b, blk);
 }
 
 // Home cell of particle p in sort block key (see Batch::hcell), decided in
@@ -840,6 +1094,36 @@ cudaError_t launch_transfer(const Batch &b, SortBlock blk, int mode, float dt, c
   return cudaErrorInvalidValue;
 }
 
+template <int BX, int BY, int BZ>
+static cudaError_t prepare_pipe_t(int *grid) {
+  const int smem = (int)PipePlan<BX, BY, BZ>::BYTES;
+  cudaError_t e = cudaFuncSetAttribute(k_transfer_pipe<BX, BY, BZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int per_sm = 0, dev = 0, sms = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_transfer_pipe<BX, BY, BZ>, XferPlan<BX, BY, BZ>::THREADS,
+                                                    smem);
+  if (e == cudaSuccess) e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  *grid = per_sm * sms;
+  return cudaSuccess;
+}
+
+bool pipe_supported(SortBlock blk) { return blk.t == 1 && blk.x == 8 && blk.y == 8 && blk.z == 4; }
+
+cudaError_t prepare_pipe(SortBlock blk, int *grid) {
+  if (!pipe_supported(blk)) return cudaErrorInvalidValue;
+  return prepare_pipe_t<8, 8, 4>(grid);
+}
+
+cudaError_t launch_transfer_pipe(const Batch &b, SortBlock blk, float dt, int grid, long long max_polls,
+                                 cudaStream_t st) {
+  if (!pipe_supported(blk) || grid < 1) return cudaErrorInvalidValue;
+  k_transfer_pipe<8, 8, 4><<<grid, XferPlan<8, 8, 4>::THREADS, PipePlan<8, 8, 4>::BYTES, st>>>(b, dt, max_polls);
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------
 // Persistent step: one cooperative launch runs a whole chunk of substeps
 // (grid clear, the opening P2G, then per substep the grid update, the fused
@@ -930,7 +1214,7 @@ __global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS)
     if (*(volatile int *)b.movers) {
       sort_keys_pass(b, blk, blockIdx.x, gridDim.x);
       if (!grid_barrier(c, b.err)) return;
-      if (blockIdx.x == 0) sort_scan_cta(b);
+      if (blockIdx.x == 0) sort_scan_cta(b, SortBlock{BX, BY, BZ, 1});
       if (!grid_barrier(c, b.err)) return;
       sort_scatter_pass(b, SortBlock{BX, BY, BZ, 1}, blockIdx.x, gridDim.x);
       if (!grid_barrier(c, b.err)) return;
@@ -978,7 +1262,7 @@ cudaError_t launch_sort(const Batch &b, SortBlock blk, int force, cudaStream_t s
   const long long full = (b.Ntot + 255) / 256;
   const unsigned gp = (unsigned)(full < 8LL * sms ? full : 8LL * sms);  // 8 CTAs of 256 fill an SM
   k_sort_keys<<<gp, 256, 0, st>>>(b, blk, force);
-  k_sort_scan<<<1, 1024, 0, st>>>(b, force);
+  k_sort_scan<<<1, 1024, 0, st>>>(b, blk, force);
   k_sort_scatter<<<gp, 256, 0, st>>>(b, blk, force);
   return cudaGetLastError();
 }

@@ -85,6 +85,17 @@ struct Instance {
   int slip;          // contact mode of the grid-boundary indenter: 0 sticky, 1 slip
 };
 
+// A non-empty sort block as the pipelined transfer takes it, written by the
+// sort in block order: particle range, instance, cell origin B0, and the
+// instance's grid extent and first node (so that one 48-byte read places it).
+struct BlockRec {
+  uint32_t start, n;
+  int ii, B0x, B0y, B0z;
+  int G0, G1, G2, pad;
+  long long node_off;
+};
+static_assert(sizeof(BlockRec) == 48, "block records are three 16-byte words");
+
 struct Batch {
   const Instance *inst;       // [n_inst]
   const long long *node_offs; // [n_inst] first global node of each instance
@@ -101,6 +112,8 @@ struct Batch {
   // kNotHome; written by the sort and by every transfer that groups its block,
   // which also leaves the block's idx slots in cell order
   uint16_t *hcell;
+  BlockRec *brec;   // [Nblk] non-empty blocks, in block order
+  uint32_t *blkq;   // [0] records in brec, [1] next record to hand out, [2] CTAs finished
   float4 *gmm, *gv;
   // indenter particles of all instances: local positions (cells) and the
   // instance of each
@@ -257,6 +270,12 @@ struct SortBlock {
 };
 cudaError_t launch_grid_update(const Batch &b, int substep, float dt, int clear, cudaStream_t st);
 cudaError_t launch_transfer(const Batch &b, SortBlock blk, int mode, float dt, cudaStream_t st);
+// The pipelined fused transfer (a persistent grid of grid CTAs over the
+// sort's block records; see mpm.cu), for the plans pipe_supported accepts.
+bool pipe_supported(SortBlock blk);
+cudaError_t prepare_pipe(SortBlock blk, int *grid);
+cudaError_t launch_transfer_pipe(const Batch &b, SortBlock blk, float dt, int grid, long long max_polls,
+                                 cudaStream_t st);
 cudaError_t launch_sort(const Batch &b, SortBlock blk, int force, cudaStream_t st);
 cudaError_t prepare_transfer(SortBlock blk);
 

@@ -1,0 +1,107 @@
+"""The pipelined fused transfer (a persistent grid over the sort's block
+records, bulk copies of the next block's slots, home cells and grid velocities
+while a block's particles run) against the per-block transfer kernel.
+
+Both run the same particle loop in the same cell order, so their states differ
+only by the order in which cells' node sums reach the grid (vector reductions
+to global memory from CTAs running at different times): within the bounds of
+reordered FP32 sums."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def c0_sensor(pipelined):
+    import paper_2301_08343_gb300 as T
+    b = W.C0
+    g = T.Tacchi(b.extent_m, b.dx, b.E, b.nu, b.rho, seed=b.seed, pad_side=b.pad_side,
+                 pad_bottom=b.pad_bottom, pad_top=b.pad_top)
+    g.set_pipeline(pipelined)
+    g.set_indenter(T.IndenterKind.SPHERE, (W.C0_SPHERE_R,), W.c0_sphere_pose(), W.c0_sphere_vel())
+    return T, g
+
+
+def test_pipeline_switch_and_its_plan():
+    _, g = c0_sensor(False)
+    assert g.block == (8, 8, 4) and g.threads_per_cell == 1
+    assert not g.pipelined  # the per-block kernel is the default
+    g.set_pipeline(True)
+    assert g.pipelined
+    g.set_transfer((4, 4, 4), 1)  # no pipelined form: the per-block kernel runs
+    assert not g.pipelined
+    g.set_transfer((8, 8, 4), 1)
+    assert g.pipelined
+    g.set_launch(True)  # the persistent step has its own transfer
+    assert not g.pipelined
+
+
+def test_pipelined_press_matches_the_per_block_kernel():
+    _, a = c0_sensor(False)
+    _, p = c0_sensor(True)
+    for _ in range(3):
+        a.step(100, W.C0_DT)
+        p.step(100, W.C0_DT)
+    sa, sp = a.get_state(), p.get_state()
+    assert sa["status"] == 0 and sp["status"] == 0
+    assert np.abs(sa["u"].cpu().numpy() - sp["u"].cpu().numpy()).max() <= 1e-5
+    assert np.abs(sa["Fm"].cpu().numpy() - sp["Fm"].cpu().numpy()).max() <= 1e-5
+    win = W.top_window(W.C0)
+    ha = a.heightmap(120, 120, win).cpu().numpy()
+    hp = p.heightmap(120, 120, win).cpu().numpy()
+    assert np.abs(ha - hp).max() <= 1e-3 * W.C0.dx
+
+
+def test_pipelined_step_follows_the_sorts():
+    """A drifting block: its particles cross sort blocks every few substeps,
+    so the block records and home cells are rebuilt by the sort between
+    pipelined transfers."""
+    import paper_2301_08343_gb300 as T
+    b = W.Block(24, 16, 6, 0.5e-3, seed=3, pad_side=12)
+    out = []
+    for pipelined in (False, True):
+        g = T.Tacchi(b.extent_m, b.dx, b.E, b.nu, b.rho, seed=b.seed, pad_side=b.pad_side, fix_base=False)
+        g.set_pipeline(pipelined)
+        u0 = g.get_state()["u"].clone()
+        v = torch.zeros_like(u0)
+        v[0], v[1] = 3.0, -1.5  # 0.06 and 0.03 cells per substep
+        g.set_state(u0, v)
+        g.profile(reset=True)
+        g.step(60, 1e-5)
+        s = g.get_state()
+        assert s["status"] == 0
+        out.append((s["u"].cpu().numpy(), g.profile()["sort_runs"]))
+    (ua, na), (up, np_) = out
+    assert na > 0 and np_ > 0
+    assert np.abs(ua - up).max() <= 1e-5
+
+
+def test_pipelined_batch_matches_the_per_block_kernel():
+    import paper_2301_08343_gb300 as T
+    specs = W.c2_instances(6, seed_base=1000)
+    K = T.IndenterKind
+    kinds = {"sphere": K.SPHERE, "cylinder": K.CYLINDER, "cone": K.CONE, "prism": K.PRISM}
+    out = []
+    for pipelined in (False, True):
+        bt = T.TacchiBatch([b for b, _ in specs])
+        bt.set_pipeline(pipelined)
+        assert bt.pipelined == pipelined
+        for i, (b, ind) in enumerate(specs):
+            bt.set_indenter(i, kinds[ind["kind"]], ind["params"], ind["pose"],
+                            (0, 0, -ind["depth"] / (200 * W.C2_DT), 0, 0, 0))
+        bt.step(200, W.C2_DT)
+        assert bt.status() == 0
+        out.append([bt.get_state(i)["u"].cpu().numpy() for i in range(len(specs))])
+    for a, p in zip(*out):
+        assert np.abs(a - p).max() <= 1e-4  # 200 substeps of reordered FP32 reductions
