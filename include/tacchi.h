@@ -460,12 +460,15 @@ tacchi_status tacchi_set_launch(tacchi_handle h, int mode);
  * (TACCHI_ERR_TIMEOUT).  Synchronises.  Errors: INVALID_ARG (on not 0 or 1). */
 tacchi_status tacchi_set_pipeline(tacchi_handle h, int on);
 
-/* Bound of the persistent step's grid-barrier waits: a CTA gives up after
- * max_polls polls (about 0.1 us each; default 2^24), and a barrier waits for
- * extra_arrivals CTAs beyond the grid (default 0).  A positive extra_arrivals
- * makes every barrier wait for arrivals that never come: it exists to
- * exercise the bounded wait, which then ends the step with
- * TACCHI_ERR_TIMEOUT.  Errors: INVALID_ARG (max_polls < 1, extra_arrivals < 0). */
+/* Bound of the persistent step's grid-barrier waits and of the pipelined
+ * transfer's copy waits: a CTA gives up after max_polls polls (about 0.1 us
+ * each; default 2^24), and a barrier waits for extra_arrivals arrivals beyond
+ * its own (default 0).  A positive extra_arrivals makes every such wait wait
+ * for arrivals that never come: it exists to exercise the bounded wait, which
+ * then ends the step with TACCHI_ERR_TIMEOUT (a pipelined CTA that gives up
+ * supplies the missing arrivals itself and waits for its copies in flight
+ * before it leaves).  Errors: INVALID_ARG (max_polls < 1, extra_arrivals < 0
+ * or > 65536). */
 tacchi_status tacchi_set_barrier_wait(tacchi_handle h, int64_t max_polls, int extra_arrivals);
 
 /* Number of transfer plans the autotuner tries, in this order:

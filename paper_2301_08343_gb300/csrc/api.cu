@@ -367,7 +367,7 @@ cudaError_t build_graph(tacchi_ctx *c, int n, float dt, GraphEntry *ge) {
     le = timed(c, pe, 0, [&] { return launch_grid_update(b, k, dt, 1, s); });
     if (le == cudaSuccess)
       le = timed(c, pe, 1, [&] {
-        return c->pipe && c->pipe_grid > 0 ? launch_transfer_pipe(b, blk, dt, c->pipe_grid, c->max_polls, s)
+        return c->pipe && c->pipe_grid > 0 ? launch_transfer_pipe(b, blk, dt, c->pipe_grid, c->max_polls, c->extra_arrivals, s)
                                            : launch_transfer(b, blk, XFER_FUSED, dt, s);
       });
     if (le == cudaSuccess && b.Np > 0) le = timed(c, pe, 1, [&] { return launch_indenter_p2g(b, k + 1, s); });
@@ -1360,7 +1360,9 @@ tacchi_status tacchi_set_pipeline(tacchi_handle c, int on) {
 }
 
 tacchi_status tacchi_set_barrier_wait(tacchi_handle c, int64_t max_polls, int extra_arrivals) {
-  if (!c || max_polls < 1 || extra_arrivals < 0) return TACCHI_ERR_INVALID_ARG;
+  if (!c || max_polls < 1 || extra_arrivals < 0 || extra_arrivals > 65536) return TACCHI_ERR_INVALID_ARG;
+  CK(cudaStreamSynchronize(c->stream));
+  drop_graphs(c);  // the graphs hold the pipelined transfer's arguments
   c->max_polls = max_polls;
   c->extra_arrivals = (unsigned)extra_arrivals;
   return TACCHI_OK;

@@ -649,7 +649,8 @@ __device__ __forceinline__ void pipe_prefetch(const Batch &b, const BlockRec &r,
 }
 
 template <int BX, int BY, int BZ>
-__global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer_pipe(Batch b, float dt, long long max_polls) {
+__global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer_pipe(Batch b, float dt, long long max_polls,
+                                                                               int extra) {
   using X = XferPlan<BX, BY, BZ>;
   using Q = PipePlan<BX, BY, BZ>;
   constexpr int T = X::THREADS;
@@ -675,7 +676,7 @@ __global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer_pipe(B
   const uint32_t nrec = b.blkq[0];
 
   if (tid == 0) {
-    mbar_init(&bar, T);
+    mbar_init(&bar, T + extra);  // extra > 0: arrivals that never come (tests the bounded wait)
     mbar_init_fence();
     const uint32_t k0 = atomicAdd(b.blkq + 1, 1u), k1 = atomicAdd(b.blkq + 1, 1u);
     BlockRec none{};
@@ -755,10 +756,15 @@ __global__ void __launch_bounds__(128, TACCHI_XFER_MIN_BLOCKS) k_transfer_pipe(B
     vcur = vnext;
     vnext = t;
   }
-  // a wait that gave up: before the CTA leaves, wait again for the copies
-  // still in flight, with a bound of its own (2^26 polls) rather than the
-  // caller's, so that no copy lands in the shared memory of a finished CTA
-  if (s_abort) mbar_wait_bounded(&bar, parity, 1ll << 26);
+  // a wait that gave up: before the CTA leaves, give the phase its missing
+  // arrivals and wait again for the copies still in flight, with a bound of
+  // its own (2^26 polls) rather than the caller's, so that no copy lands in
+  // the shared memory of a finished CTA
+  if (s_abort) {
+    if (tid == 0)
+      for (int e = 0; e < extra; ++e) mbar_arrive(&bar);
+    mbar_wait_bounded(&bar, parity, 1ll << 26);
+  }
   __syncthreads();
   if (tid == 0) {
     if (s_abort) atomicOr(b.err, ERRBIT_TIMEOUT);
@@ -1117,10 +1123,10 @@ cudaError_t prepare_pipe(SortBlock blk, int *grid) {
   return prepare_pipe_t<8, 8, 4>(grid);
 }
 
-cudaError_t launch_transfer_pipe(const Batch &b, SortBlock blk, float dt, int grid, long long max_polls,
+cudaError_t launch_transfer_pipe(const Batch &b, SortBlock blk, float dt, int grid, long long max_polls, int extra,
                                  cudaStream_t st) {
   if (!pipe_supported(blk) || grid < 1) return cudaErrorInvalidValue;
-  k_transfer_pipe<8, 8, 4><<<grid, XferPlan<8, 8, 4>::THREADS, PipePlan<8, 8, 4>::BYTES, st>>>(b, dt, max_polls);
+  k_transfer_pipe<8, 8, 4><<<grid, XferPlan<8, 8, 4>::THREADS, PipePlan<8, 8, 4>::BYTES, st>>>(b, dt, max_polls, extra);
   return cudaGetLastError();
 }
 

@@ -274,7 +274,7 @@ cudaError_t launch_transfer(const Batch &b, SortBlock blk, int mode, float dt, c
 // sort's block records; see mpm.cu), for the plans pipe_supported accepts.
 bool pipe_supported(SortBlock blk);
 cudaError_t prepare_pipe(SortBlock blk, int *grid);
-cudaError_t launch_transfer_pipe(const Batch &b, SortBlock blk, float dt, int grid, long long max_polls,
+cudaError_t launch_transfer_pipe(const Batch &b, SortBlock blk, float dt, int grid, long long max_polls, int extra,
                                  cudaStream_t st);
 cudaError_t launch_sort(const Batch &b, SortBlock blk, int force, cudaStream_t st);
 cudaError_t prepare_transfer(SortBlock blk);

@@ -105,3 +105,26 @@ def test_pipelined_batch_matches_the_per_block_kernel():
         out.append([bt.get_state(i)["u"].cpu().numpy() for i in range(len(specs))])
     for a, p in zip(*out):
         assert np.abs(a - p).max() <= 1e-4  # 200 substeps of reordered FP32 reductions
+
+
+def test_pipelined_copy_wait_is_bounded_and_the_handle_recovers():
+    """Every copy wait is told to wait for an arrival that never comes: each
+    CTA gives up, supplies the missing arrival itself, waits for its copies
+    in flight and leaves; the step reports TACCHI_ERR_TIMEOUT and the handle
+    steps normally once the wait is restored."""
+    import math
+    from paper_2301_08343_gb300 import _lib
+    _, g = c0_sensor(True)
+    u0 = g.get_state()["u"].clone()
+    with pytest.raises(_lib.TacchiError):
+        g.set_barrier_wait(1 << 24, extra_arrivals=70000)
+    g.set_barrier_wait(1 << 14, extra_arrivals=1)
+    g.step(5, W.C0_DT)
+    assert g.status() == -6  # TACCHI_ERR_TIMEOUT
+    g.set_barrier_wait(1 << 24, extra_arrivals=0)
+    g.set_state(u0)
+    g.step(5, W.C0_DT)
+    s = g.get_state()
+    assert s["status"] == 0
+    assert math.isfinite(float(s["u"].abs().max()))
+
