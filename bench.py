@@ -764,18 +764,25 @@ def run_smoothed_bench(args):
     }
 
 
+def kernel_sources_sha1():
+    """First 12 hex digits of the SHA-1 of the transfer kernel's sources
+    (mpm.cu, mpm_device.cuh, tacchi_internal.cuh, in that order)."""
+    import hashlib
+    h = hashlib.sha1()
+    for name in ("mpm.cu", "mpm_device.cuh", "tacchi_internal.cuh"):
+        with open(os.path.join(ROOT, "paper_2301_08343_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:12]
+
+
 def load_traffic(workload):
     """DRAM bytes per fused launch from the committed ncu summary; null when
     the kernel source changed since the counters were taken."""
-    import hashlib
     p = os.path.join(ROOT, "profiles", "k_transfer_fused_traffic.json")
-    src = os.path.join(ROOT, "paper_2301_08343_gb300", "csrc", "mpm.cu")
     try:
         with open(p) as f:
             d = json.load(f)
-        with open(src, "rb") as f:
-            fp = hashlib.sha1(f.read()).hexdigest()[:12]
-        if d.get("mpm_cu_sha1") != fp or workload not in d:
+        if d.get("kernel_sources_sha1") != kernel_sources_sha1() or workload not in d:
             return None
         return d[workload]["dram_bytes_per_launch"]
     except Exception:
