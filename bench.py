@@ -363,8 +363,6 @@ def run_batch_bench(args, rank, world, local_rank):
     substeps = args.substeps or 200
     dt = W.C2_DT
     bt = T.TacchiBatch([b for b, _ in specs])
-    if args.pipeline != "default":
-        bt.set_pipeline(args.pipeline == "on")
     persistent = args.launch == "persistent"
     K = T.IndenterKind
     kinds = {"sphere": K.SPHERE, "cylinder": K.CYLINDER, "cone": K.CONE, "prism": K.PRISM}
@@ -375,6 +373,8 @@ def run_batch_bench(args, rank, world, local_rank):
         for i, (b, ind) in enumerate(specs):
             bt.set_indenter(i, vel=(0, 0, -ind["depth"] / (substeps * dt), 0, 0, 0))
         tuned = bt.autotune(min(32, substeps), dt)
+    if args.pipeline != "default":  # an explicit choice overrides the autotuner's
+        bt.set_pipeline(args.pipeline == "on")
     if persistent:
         bt.set_launch(True)
     hms = torch.empty((len(specs), 64, 64), device=dev)
