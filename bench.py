@@ -373,6 +373,9 @@ def run_batch_bench(args, rank, world, local_rank):
         for i, (b, ind) in enumerate(specs):
             bt.set_indenter(i, vel=(0, 0, -ind["depth"] / (substeps * dt), 0, 0, 0))
         tuned = bt.autotune(min(32, substeps), dt)
+    if args.plan:  # an explicit plan overrides the autotuner's
+        shape, tpc = args.plan.split("/")
+        bt.set_transfer(tuple(int(x) for x in shape.split("x")), int(tpc))
     if args.pipeline != "default":  # an explicit choice overrides the autotuner's
         bt.set_pipeline(args.pipeline == "on")
     if persistent:
@@ -447,6 +450,7 @@ def run_batch_bench(args, rank, world, local_rank):
                                f"{substeps} substeps dt={dt:g} s + 64x64 map per sensor per step",
                    "instances": len(all_specs), "instances_rank0": len(specs), "particles": bt.N_total,
                    "particles_all_ranks": int(units_all // substeps), "autotune": tuned,
+                   "plan": "x".join(map(str, bt.transfer_plan()[0])) + "/%d" % bt.transfer_plan()[1],
                    "rank_particle_loads": loads,
                    "parallelism": f"sensors split over {world} rank(s) by particle count (longest first), "
                                   "no collective in the step",
