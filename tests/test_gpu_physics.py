@@ -122,6 +122,8 @@ def test_hertz_press_matches_the_oracle_profile():
         assert cur == pytest.approx(prof["depth_m"], rel=0, abs=1e-15)
         worst = max(worst, float(np.abs(wb - np.array(prof["w_m"])).max()))
         fits.append((cur,) + fit_profile(rb, wb, math.sqrt(R * cur)))
+    print(f"oracle press on the GPU: worst binned height difference {worst / dx:.2e} dX, "
+          f"k/R = {k_over_R(fits, R):.4f}")
     # 5,000 FP32 substeps against FP64: binned surface heights within 1e-2 dX
     assert worst <= 1e-2 * dx, worst / dx
     assert abs(k_over_R(fits, R) - 1.0) <= 0.05, (k_over_R(fits, R), fits)
