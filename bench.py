@@ -474,17 +474,28 @@ def run_batch_bench(args, rank, world, local_rank):
     }
 
 
-def unet_flops_per_image(widths, size, cin_pad=32, cout=3):
-    """FLOPs (2 per multiply-add) of one forward pass of the surrogate U-Net."""
+def unet_flops_per_image(widths, size, cin=2, cout=3):
+    """FLOPs (2 per multiply-add) of one forward pass of the surrogate U-Net on
+    its cin real input channels (the kernels pad the first layer's input to 32
+    channels; the padded products are not work and are not counted)."""
     L = len(widths)
     f = 0
     hw = size * size
     for l in range(L):
-        ci = cin_pad if l == 0 else widths[l - 1]
+        ci = cin if l == 0 else widths[l - 1]
         f += 2 * (hw >> (2 * l)) * 9 * (ci * widths[l] + widths[l] * widths[l])
     for l in range(L - 2, -1, -1):
         f += 2 * (hw >> (2 * l)) * 9 * ((widths[l + 1] + widths[l]) * widths[l] + widths[l] * widths[l])
     return f + 2 * hw * widths[0] * cout
+
+
+def unet_train_flops_per_image(widths, size, cin=2, cout=3):
+    """FLOPs of one training sample: the forward pass, the weight gradients
+    (as many products as the forward) and the data gradients, which every
+    layer needs except the first (the input takes no gradient)."""
+    fwd = unet_flops_per_image(widths, size, cin, cout)
+    first = 2 * size * size * 9 * cin * widths[0]
+    return 3 * fwd - first
 
 
 def single_mpm_fps(block, substeps, dt, presses=3):
@@ -572,7 +583,7 @@ def run_surrogate_bench(args):
     img_err_region = SG.image_errors(img_pred[mask], img_mpm[mask]) if inreg.any() else None
     fps = {b: SG.inference_rate(net, Xte.repeat(max(1, 1024 // len(ste) + 1), 1, 1, 1), b) for b in (1, 256, 1024)}
     single_fps = single_mpm_fps(W.C3_BLOCK, W.C3_SUBSTEPS, W.C3_DT)
-    step_flops = 3 * 256 * unet_flops_per_image(widths, W.C3_SIZE)
+    step_flops = 256 * unet_train_flops_per_image(widths, W.C3_SIZE)
     tflops = step_flops * args.train_steps / (train_ms * 1e-3) / 1e12
     peaks, src = measured_peaks()
     sustained = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
