@@ -1,4 +1,4 @@
-"""The Hertz contact law on the oracle (spec: a = sqrt(R d) within 5%).
+"""The Hertz contact law on the oracle: a = sqrt(R d), required within 5%.
 
 oracle/hertz.py presses a rigid sphere (R = 6 mm) quasi-statically into a
 14 x 14 x 7 mm block at dX = 0.1 mm with every step of the oracle's method
