@@ -128,3 +128,28 @@ def test_pipelined_copy_wait_is_bounded_and_the_handle_recovers():
     assert s["status"] == 0
     assert math.isfinite(float(s["u"].abs().max()))
 
+
+
+def test_block_beyond_the_grouping_capacity():
+    """4,000 particles packed into one 8 x 8 x 4 block (capacity 3,072): that
+    block takes the ungrouped path, one particle per thread with its own
+    scatter, in both kernels (the pipelined one then copies no slots or home
+    cells for it); the step reports no error and the two agree."""
+    out = []
+    for pipelined in (False, True):
+        _, g = c0_sensor(pipelined)
+        g.set_indenter(vel=(0, 0, 0, 0, 0, 0))
+        u = g.get_state()["u"].clone()
+        rng = np.random.default_rng(4)
+        k = 4000
+        b0 = np.array([8.0, 8.0, 4.0])
+        ext = np.array([8.0, 8.0, 4.0])
+        # home cells floor(u - 1/2) inside the block [b0, b0 + ext)
+        pts = b0 + 0.5 + rng.random((k, 3)) * ext
+        u[:, :k] = torch.as_tensor(pts.T, dtype=torch.float32, device=u.device)
+        g.set_state(u)
+        g.step(5, W.C0_DT)
+        s = g.get_state()
+        assert s["status"] == 0
+        out.append(s["u"].cpu().numpy())
+    assert np.abs(out[0] - out[1]).max() <= 1e-5
