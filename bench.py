@@ -216,12 +216,18 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream(dev)
     sim = T.Tacchi(block.extent_m, block.dx, block.E, block.nu, block.rho, seed=block.seed + rank,
                    pad_side=block.pad_side, pad_bottom=block.pad_bottom, pad_top=block.pad_top)
+    persistent = args.launch == "persistent"
+    tuned = None
     if args.plan:
         shape, tpc = args.plan.split("/")
         sim.set_transfer(tuple(int(x) for x in shape.split("x")), int(tpc))
-    if args.pipeline != "default":
+    elif not args.no_autotune and not persistent:
+        # the library's autotuner picks the plan on the first press
+        name, params, hm, pose, vel, depth = indenter_for_step(block, 0, substeps, dt)
+        sim.set_indenter(kind_of(name, T.IndenterKind), params, pose, vel, hm=hm, hm_pixel=0.1e-3)
+        tuned = sim.autotune(min(32, substeps), dt)
+    if args.pipeline != "default":  # an explicit choice overrides the autotuner's
         sim.set_pipeline(args.pipeline == "on")
-    persistent = args.launch == "persistent"
     if persistent:
         sim.set_launch(True)
     rest = sim.get_state()
@@ -303,10 +309,18 @@ def run_ours(args, rank, world, local_rank):
     flops_fused = FLOPS_PER_PARTICLE * sim.N
     gbs = bytes_fused / (fused_avg_ms * 1e-3) / 1e9
     tfl = flops_fused / (fused_avg_ms * 1e-3) / 1e12
-    traffic = load_traffic(args.workload)
+    # the committed DRAM traffic holds for the per-block kernel of the plan it was taken on
+    plan = "x".join(map(str, sim.block)) + "/%d" % sim.threads_per_cell
+    traffic = None if persistent or sim.pipelined else load_traffic(args.workload, plan)
+    if persistent:
+        kernel = "k_persistent (whole substep: grid update, fused G2P+P2G, sort, and the step's frame)"
+    elif sim.pipelined:
+        kernel = "k_transfer_pipe (fused G2P+P2G, pipelined)"
+    else:
+        kernel = "k_transfer%s (fused G2P+P2G, plan %s/%d)" % (
+            "3" if sim.threads_per_cell == 3 else "", "x".join(map(str, sim.block)), sim.threads_per_cell)
     roof = {
-        "kernel": ("k_persistent (whole substep: grid update, fused G2P+P2G, sort, and the step's frame)"
-                   if persistent else "k_transfer (fused G2P+P2G)"),
+        "kernel": kernel,
         "bound": "alu",
         "achieved": round(tfl, 3), "peak": round(fp32["tflops"], 2), "unit": "TFLOP/s",
         "frac": round(tfl / fp32["tflops"], 4),
@@ -333,6 +347,7 @@ def run_ours(args, rank, world, local_rank):
                                   "nine procedural indenters cycled, depths 0.2-1.5 mm"),
                    "particles": sim.N, "grid_nodes": sim.n_nodes, "substeps_per_step": substeps,
                    "image": [w, h], "sort_block": list(sim.block), "threads_per_cell": sim.threads_per_cell,
+                   "autotune": tuned,
                    "launch": args.launch, "pipelined": sim.pipelined, "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (particle state %.2f GB)" % (sim.N * 96 / 1e9)},
         "roofline": roof,
@@ -790,14 +805,15 @@ def kernel_sources_sha1():
     return h.hexdigest()[:12]
 
 
-def load_traffic(workload):
+def load_traffic(workload, plan):
     """DRAM bytes per fused launch from the committed ncu summary; null when
-    the kernel source changed since the counters were taken."""
+    the kernel source changed since the counters were taken, or when they were
+    taken on another transfer plan."""
     p = os.path.join(ROOT, "profiles", "k_transfer_fused_traffic.json")
     try:
         with open(p) as f:
             d = json.load(f)
-        if d.get("kernel_sources_sha1") != kernel_sources_sha1() or workload not in d:
+        if d.get("kernel_sources_sha1") != kernel_sources_sha1() or d.get("plan") != plan or workload not in d:
             return None
         return d[workload]["dram_bytes_per_launch"]
     except Exception:

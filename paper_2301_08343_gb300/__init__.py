@@ -202,6 +202,16 @@ class Tacchi:
         check(lib().tacchi_set_transfer(self._h, *shape, int(threads_per_cell)), "tacchi_set_transfer")
         self.block, self.threads_per_cell = tuple(int(x) for x in shape), int(threads_per_cell)
 
+    def autotune(self, n_substeps, dt):
+        """Times every transfer plan on the current state (restored after);
+        keeps the fastest and returns ((bx, by, bz, threads per cell),
+        {plan name: ms per substep})."""
+        best = (C.c_int * 4)()
+        ms = (C.c_double * len(TRANSFER_PLANS))()
+        check(lib().tacchi_autotune(self._h, int(n_substeps), float(dt), best, ms), "tacchi_autotune")
+        self.block, self.threads_per_cell = tuple(best[:3]), int(best[3])
+        return tuple(best), dict(zip(TRANSFER_PLANS, list(ms)))
+
     def set_launch(self, persistent):
         """Step as one persistent cooperative kernel per chunk (True) or as a
         CUDA graph of kernels (False, the default)."""
