@@ -153,3 +153,16 @@ def test_block_beyond_the_grouping_capacity():
         assert s["status"] == 0
         out.append(s["u"].cpu().numpy())
     assert np.abs(out[0] - out[1]).max() <= 1e-5
+
+
+def test_single_handle_autotune_keeps_the_state_and_reports_its_plan():
+    _, g = c0_sensor(False)
+    g.step(10, W.C0_DT)
+    before = g.get_state()["u"].clone()
+    best, ms = g.autotune(8, W.C0_DT)
+    assert best in [(4, 4, 4, 1), (8, 8, 4, 1), (8, 8, 8, 1), (16, 8, 4, 1), (8, 8, 4, 3), (4, 4, 4, 3)]
+    assert g.block == tuple(best[:3]) and g.threads_per_cell == best[3]
+    assert len(ms) == 6 and all(v > 0 for v in ms.values())
+    assert torch.equal(g.get_state()["u"], before)
+    g.step(10, W.C0_DT)
+    assert g.get_state()["status"] == 0
